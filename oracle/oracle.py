@@ -1,0 +1,205 @@
+"""ctypes wrapper of the FP64 CPU oracle (``lbm3_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: tests/, ``__graft_entry__.smoke()`` and bench.py's CPU-baseline
+and reference legs are the only users.  The product package never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lbm3_oracle.c")
+_LIB = os.path.join(_HERE, "liblbm3_oracle.so")
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_U8 = ctypes.POINTER(ctypes.c_uint8)
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (portable flags only: it must build on x86 and Arm)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        L.ora_create.restype = ctypes.c_void_p
+        L.ora_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_double, ctypes.c_double, _U8, _D, _D, _D,
+                                 ctypes.c_double]
+        for name in ("ora_destroy",):
+            getattr(L, name).argtypes = [ctypes.c_void_p]
+        L.ora_check.argtypes = [ctypes.c_void_p]
+        L.ora_check.restype = ctypes.c_int
+        L.ora_set_fields.argtypes = [ctypes.c_void_p, _D]
+        L.ora_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.ora_fields.argtypes = [ctypes.c_void_p, _D, _D]
+        L.ora_diag.argtypes = [ctypes.c_void_p, _D]
+        for name in ("ora_get_f", "ora_set_f", "ora_get_normals", "ora_get_wallC",
+                     "ora_get_force"):
+            getattr(L, name).argtypes = [ctypes.c_void_p, _D]
+        L.ora_get_classes.argtypes = [ctypes.c_void_p, _U8]
+        L.ora_lattice.argtypes = [ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                  _D, _D, _D]
+        L.ora_collide.argtypes = [_D, _D, ctypes.c_double, _D, _D]
+        L.ora_gfun.argtypes = [ctypes.c_double]
+        L.ora_gfun.restype = ctypes.c_double
+        L.ora_gradient_periodic.argtypes = [ctypes.c_int, ctypes.c_int, _D, _D]
+        L.ora_beta.argtypes = [ctypes.c_void_p, _D, _D]
+        L.ora_wet_probe.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_double, _D, _D]
+        L.ora_local_angles.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D]
+        _lib = L
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _c(a, dtype=np.float64):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Oracle:
+    """One oracle simulation: geometry, parameters and FP64 state."""
+
+    def __init__(self, nx, ny, periodic_y, bc_x, solid, angles, sigma, nu, beta0=0.7,
+                 u_in=0.0, rho_out=1.0):
+        L = lib()
+        self.nx, self.ny = int(nx), int(ny)
+        self.n = self.nx * self.ny
+        self._solid = _c(solid, np.uint8).reshape(-1)
+        self._angles = _c(angles).reshape(-1)
+        assert self._solid.size == self.n and self._angles.size == 3 * self.n
+        sig = _c(sigma)
+        nus = _c(nu)
+        self._h = L.ora_create(self.nx, self.ny, int(periodic_y), int(bc_x), float(u_in),
+                               float(rho_out), self._solid.ctypes.data_as(_U8),
+                               _dp(self._angles), _dp(sig), _dp(nus), float(beta0))
+        code = L.ora_check(self._h)
+        if code != 0:
+            L.ora_destroy(self._h)
+            self._h = None
+            raise ValueError(f"oracle: invalid configuration (code {code})")
+
+    @classmethod
+    def from_workload(cls, w):
+        o = cls(w.nx, w.ny, w.periodic_y, w.bc_x, w.solid, w.angles, w.sigma, w.nu, w.beta0,
+                w.u_in, w.rho_out)
+        o.set_fields(w.rho)
+        return o
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            lib().ora_destroy(self._h)
+            self._h = None
+
+    def set_fields(self, rho):
+        r = _c(rho).reshape(-1)
+        assert r.size == 3 * self.n
+        lib().ora_set_fields(self._h, _dp(r))
+
+    def step(self, n=1):
+        lib().ora_step(self._h, int(n))
+
+    def fields(self):
+        rho = np.empty(3 * self.n)
+        u = np.empty(2 * self.n)
+        lib().ora_fields(self._h, _dp(rho), _dp(u))
+        return rho.reshape(3, self.ny, self.nx), u.reshape(2, self.ny, self.nx)
+
+    def diag(self):
+        out = np.empty(8)
+        lib().ora_diag(self._h, _dp(out))
+        return out
+
+    def get_f(self):
+        f = np.empty(27 * self.n)
+        lib().ora_get_f(self._h, _dp(f))
+        return f.reshape(3, 9, self.ny, self.nx)
+
+    def set_f(self, f):
+        f = _c(f).reshape(-1)
+        assert f.size == 27 * self.n
+        lib().ora_set_f(self._h, _dp(f))
+
+    def classes(self):
+        c = np.empty(self.n, np.uint8)
+        lib().ora_get_classes(self._h, c.ctypes.data_as(_U8))
+        return c.reshape(self.ny, self.nx)
+
+    def normals(self):
+        a = np.empty(2 * self.n)
+        lib().ora_get_normals(self._h, _dp(a))
+        return a.reshape(self.ny, self.nx, 2)
+
+    def wall_C(self):
+        a = np.empty(3 * self.n)
+        lib().ora_get_wallC(self._h, _dp(a))
+        return a.reshape(3, self.ny, self.nx)
+
+    def force(self):
+        a = np.empty(2 * self.n)
+        lib().ora_get_force(self._h, _dp(a))
+        return a.reshape(2, self.ny, self.nx)
+
+    def beta(self, rho_k):
+        out = np.empty(9)
+        lib().ora_beta(self._h, _dp(_c(rho_k)), _dp(out))
+        return out.reshape(3, 3)
+
+    def wet_probe(self, node, k, theta_k, C):
+        C = _c(C).reshape(-1)
+        assert C.size == 3 * self.n
+        out = np.empty(3)
+        lib().ora_wet_probe(self._h, int(node), int(k), float(theta_k), _dp(C), _dp(out))
+        return out
+
+    def local_angles(self, node, Cp):
+        out = np.empty(2)
+        lib().ora_local_angles(self._h, int(node), _dp(_c(Cp)), _dp(out))
+        return out
+
+
+def lattice():
+    ex = (ctypes.c_int * 9)()
+    ey = (ctypes.c_int * 9)()
+    w = np.empty(9)
+    M = np.empty(81)
+    Mi = np.empty(81)
+    lib().ora_lattice(ex, ey, _dp(w), _dp(M), _dp(Mi))
+    return np.array(ex[:]), np.array(ey[:]), w, M.reshape(9, 9), Mi.reshape(9, 9)
+
+
+def collide(f, Fs, tau):
+    f = _c(f)
+    Fs = _c(Fs)
+    out = np.empty(9)
+    u = np.empty(2)
+    lib().ora_collide(_dp(f), _dp(Fs), float(tau), _dp(out), _dp(u))
+    return out, u
+
+
+def gfun(X):
+    return lib().ora_gfun(float(X))
+
+
+def gradient_periodic(psi):
+    psi = _c(psi)
+    ny, nx = psi.shape
+    out = np.empty(2 * nx * ny)
+    lib().ora_gradient_periodic(nx, ny, _dp(psi), _dp(out))
+    return out.reshape(2, ny, nx)
