@@ -33,8 +33,11 @@
  *   - "in contact with" means any of the 8 D2Q9 neighbours
  *   - n_s of Eq.(19) points into the solid; the characteristic lines use -n_s
  *   - Eq.(21) uses the C_SB values of the previous step (initially the w-weighted mean
- *     of the fluid neighbours); when 1 - C_k < 1e-12 theta_k is the mean of its two angles
- *   - ray march: crossings within 1e-9 of a node are node hits; search stops at t > 16;
+ *     of the fluid neighbours), evaluated with 1 - C_r = C_b + C_g as the convex combination
+ *     theta_r = theta_rg + C_b/(C_b + C_g) (theta_rb - theta_rg) (and likewise for green);
+ *     when both weights are below 1e-12 theta_k is the mean of its two angles
+ *   - |pi/2 - theta_k| below 1e-6 deg is taken as 0 (both lines along n_s)
+ *   - ray march: crossings within 1e-6 of a node are node hits; search stops at t > 16;
  *     if no valid crossing exists, C_D is the w-weighted mean of the fluid neighbours
  *   - Eq.(22) tie theta_k = 90 deg takes the max branch; if C_r + C_g > 1 both are
  *     rescaled to sum to 1, and C_b = max(0, 1 - C_r - C_g)
@@ -75,7 +78,8 @@ enum { LOC_IN = 0, LOC_SOLID = 1, LOC_GHOST = 2 };
 
 #define G2_EPS 1e-24
 #define RAY_TMAX 16.0
-#define RAY_EPS 1e-9
+#define RAY_EPS 1e-6
+#define PHI_SNAP 1e-6
 
 typedef struct ora {
     int nx, ny, n;
@@ -414,7 +418,8 @@ static double wet_value(const ora_t* o, int p, int k, double theta_k, double* CD
     int px = p % o->nx, py = p / o->nx;
     double nx = o->ns[2 * (size_t)p], ny = o->ns[2 * (size_t)p + 1];
     double tx = -ny, ty = nx; /* tangent */
-    double phi = fabs(90.0 - theta_k) * (M_PI / 180.0);
+    /* |pi/2 - theta_k|; within 1e-6 deg of 90 both lines run along n_s */
+    double phi = fabs(90.0 - theta_k) < PHI_SNAP ? 0.0 : fabs(90.0 - theta_k) * (M_PI / 180.0);
     double cphi = cos(phi), sphi = sin(phi);
     double d1x = cphi * nx + sphi * tx, d1y = cphi * ny + sphi * ty;
     double d2x = cphi * nx - sphi * tx, d2y = cphi * ny - sphi * ty;
@@ -435,14 +440,17 @@ static void local_angles(const ora_t* o, int p, double th[2])
     double t_br = o->theta[3 * (size_t)p + 1];
     double t_gb = o->theta[3 * (size_t)p + 2];
     double t_rb = 180.0 - t_br, t_gr = 180.0 - t_rg; /* theta_lk = pi - theta_kl */
-    if (1.0 - Cr < 1e-12)
+    /* Eq.(21) with 1 - C_r = C_b + C_g (the fractions sum to 1), written as a convex combination
+     * so that it is exact when one of the two weights vanishes; both weights below 1e-12 (the
+     * 0/0 of a wall node filled by fluid k): the mean of the two angles */
+    if (Cb + Cg < 1e-12)
         th[0] = 0.5 * (t_rb + t_rg);
     else
-        th[0] = Cb / (1.0 - Cr) * t_rb + Cg / (1.0 - Cr) * t_rg;
-    if (1.0 - Cg < 1e-12)
+        th[0] = t_rg + Cb / (Cb + Cg) * (t_rb - t_rg);
+    if (Cb + Cr < 1e-12)
         th[1] = 0.5 * (t_gb + t_gr);
     else
-        th[1] = Cb / (1.0 - Cg) * t_gb + Cr / (1.0 - Cg) * t_gr;
+        th[1] = t_gr + Cb / (Cb + Cr) * (t_gb - t_gr);
 }
 
 /* O2-O4 for every C_SB node */
@@ -623,7 +631,11 @@ static void densities(ora_t* o)
     }
 }
 
-/* rest equilibrium f_ak = w_a rho_k; lagged C_SB values = w-weighted fluid-neighbour mean */
+static void zou_he(ora_t* o, double* F);
+
+/* rest equilibrium f_ak = w_a rho_k, taken as a post-streaming state (so the open-boundary
+ * populations are completed by Zou-He as after any streaming step); lagged C_SB values =
+ * w-weighted fluid-neighbour mean */
 void ora_set_fields(ora_t* o, const double* rho_in)
 {
     size_t n = o->n;
@@ -634,6 +646,7 @@ void ora_set_fields(ora_t* o, const double* rho_in)
         for (int k = 0; k < NF; k++)
             for (int a = 0; a < Q; a++) o->f[((size_t)k * Q + a) * n + i] = WQ[a] * rho_in[k * n + i];
     }
+    if (o->bc_x == BC_ZOUHE) zou_he(o, o->f);
     densities(o);
     for (int p = 0; p < o->n; p++) {
         if (o->cls[p] != CL_SB) continue;
@@ -645,11 +658,11 @@ void ora_set_fields(ora_t* o, const double* rho_in)
     o->steps = 0;
 }
 
-/* O10 tail: Zou-He non-equilibrium bounce-back on the open columns */
-static void zou_he(ora_t* o)
+/* O10 tail: Zou-He non-equilibrium bounce-back on the open columns of the post-streaming
+ * populations F */
+static void zou_he(ora_t* o, double* F)
 {
     size_t n = o->n;
-    double* F = o->fnew;
     for (int y = 0; y < o->ny; y++) {
         /* velocity inlet, x = 0: unknown a = 1, 5, 8 */
         size_t i = (size_t)y * o->nx;
@@ -798,7 +811,7 @@ static void one_step(ora_t* o)
                 }
             }
         }
-    if (o->bc_x == BC_ZOUHE) zou_he(o);
+    if (o->bc_x == BC_ZOUHE) zou_he(o, o->fnew);
     free(fdd);
     double* t = o->f;
     o->f = o->fnew;
