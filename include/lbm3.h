@@ -1,0 +1,147 @@
+/*
+ * lbm3.h -- C ABI of the GB300 (sm_103a) three-phase MRT colour-gradient lattice Boltzmann
+ * step with the characteristic-line wetting condition on curved walls
+ * (arXiv:2102.04709, Section II).
+ *
+ * One handle owns one D2Q9 simulation on one GPU.  Every call that touches the GPU is
+ * enqueued on the handle's CUDA stream; calls that return host data synchronise that
+ * stream.  Plain pointers and sizes only.  All functions return an int status:
+ *   0 = OK, > 0 = warning (the call did its work), < 0 = error (see lbm3_last_error).
+ *
+ * Layout conventions (all host arrays, row-major, node index i = y * nx + x):
+ *   solid mask       uint8  [ny][nx]            1 = solid node (the paper's C_S), 0 = fluid (C_F)
+ *   wall angles      double [ny][nx][3]         (theta_01, theta_20, theta_12) in degrees, i.e.
+ *                                               the paper's (theta_rg, theta_br, theta_gb) of Eq.(17);
+ *                                               theta_kl is measured inside fluid k; only values at
+ *                                               solid nodes that touch fluid (C_SB) are read
+ *   densities        double [3][ny][nx]         rho_k of fluids 0, 1, 2 (the paper's red, green, blue)
+ *   velocity         double [2][ny][nx]         (u_x, u_y)
+ * Fluid indices 0, 1, 2 are the paper's r, g, b.  Pure-fluid densities are 1 (the method is
+ * limited to equal densities, Section II.A).
+ */
+#ifndef LBM3_H
+#define LBM3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm3 lbm3;
+
+/* status codes */
+#define LBM3_OK 0
+#define LBM3_WARN_YOUNG 1        /* wall angles violate Eq.(18) by more than 1e-6 (work done) */
+#define LBM3_ERR_INVALID (-1)    /* bad argument or unsupported geometry */
+#define LBM3_ERR_CUDA (-2)       /* a CUDA call failed */
+#define LBM3_ERR_OOM (-3)        /* device allocation failed */
+#define LBM3_ERR_DIVERGED (-4)   /* non-finite or non-positive density found by lbm3_diag */
+#define LBM3_ERR_STATE (-5)      /* call out of order (e.g. lbm3_step before lbm3_set_fields) */
+
+/* x boundary (bc_x) */
+#define LBM3_BC_PERIODIC 0       /* periodic */
+#define LBM3_BC_MODPER 1         /* modified periodic, Section III.C: populations and phase
+                                    fields crossing the x seam swap fluids 0 and 2;
+                                    requires sigma_01 == sigma_12 */
+#define LBM3_BC_ZOUHE 2          /* Zou-He velocity inlet (u_in, 0) at x = 0 and pressure outlet
+                                    rho = rho_out at x = nx-1, Section III.D; requires periodic y
+                                    and no solid node in the first/last 4 columns */
+#define LBM3_BC_WALLS 3          /* columns 0 and nx-1 must be solid */
+
+/* population storage (precision) */
+#define LBM3_FP32 0              /* 27 FP32 populations per node */
+#define LBM3_FP16 1              /* per fluid: FP32 rho_k + 8 FP16 offsets f_ak - w_a rho_k */
+#define LBM3_BF16 2              /* per fluid: FP32 rho_k + 8 BF16 offsets f_ak - w_a rho_k */
+
+typedef struct lbm3_grid {
+    int32_t nx, ny;        /* grid size, nx >= 8, ny >= 8, nx * ny < 2^31 */
+    int32_t periodic_y;    /* 1: periodic in y; 0: rows 0 and ny-1 must be solid */
+    int32_t bc_x;          /* LBM3_BC_* */
+    double u_in;           /* inlet velocity for LBM3_BC_ZOUHE (|u_in| < 0.3) */
+    double rho_out;        /* outlet density for LBM3_BC_ZOUHE (> 0) */
+    int32_t precision;     /* LBM3_FP32 / LBM3_FP16 / LBM3_BF16 */
+} lbm3_grid;
+
+/* Create a simulation.  Classifies nodes into C_FI, C_FB, C_SB, C_SI (Section II.B, any of the
+ * 8 D2Q9 neighbours counts as contact), computes the outward solid normal at every C_SB node
+ * with the eighth-order isotropic stencil of Eq.(19)-(20), builds the compact wall list and
+ * allocates device memory (owned by the handle).  All host inputs are copied.
+ *   sigma  = (sigma_01, sigma_02, sigma_12), interfacial tensions of Eq.(10), > 0
+ *   nu     = kinematic viscosity of each pure fluid, > 0 (mixture by Eq.(7))
+ *   beta0  = reference segregation parameter of Eq.(14) (the paper uses 0.7)
+ *   stream = cudaStream_t (NULL = legacy default stream) on which all work is enqueued
+ * Returns LBM3_WARN_YOUNG if an angle triple at a C_SB node violates Eq.(18); *out is valid
+ * for any status >= 0 and NULL otherwise. */
+int lbm3_create(lbm3** out, const lbm3_grid* grid, const uint8_t* solid_mask,
+                const double* wall_angles_deg, const double sigma[3], const double nu[3],
+                double beta0, void* stream);
+
+/* Initialise every fluid node at rest: f_ak = w_a rho_k (Eq.3 with u = 0), as a post-streaming
+ * state (open boundaries completed by Zou-He).  The wall values that Eq.(21) reads in the first
+ * step are the w-weighted means of each C_SB node's fluid neighbours.  rho: host [3][ny][nx]. */
+int lbm3_set_fields(lbm3* h, const double* rho);
+
+/* Advance nsteps >= 0 timesteps (Eq.1-22), asynchronously on the handle's stream.  Each step is
+ * the wetting pass over the C_SB list (Eq.21-22) followed by the fused step kernel
+ * (Eq.1-16: densities, gradients, interfacial force, MRT collision, recolouring, streaming with
+ * halfway bounce-back and the x boundary).  The velocity of the last collision of the call is
+ * recorded for lbm3_fields / lbm3_diag. */
+int lbm3_step(lbm3* h, int32_t nsteps);
+
+/* lbm3_step with per-launch timing: CUDA events are recorded on the handle's stream around every
+ * wetting launch and every fused step launch; after the last step the call synchronises and
+ * writes ms_out[0] = summed wetting-kernel time, ms_out[1] = summed step-kernel time (ms). */
+int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[2]);
+
+/* Copy the current post-streaming densities rho_k (host [3][ny][nx], 0 at solid nodes) and the
+ * velocity of the most recent collision, Eq.(11) (host [2][ny][nx], may be NULL).  Synchronises. */
+int lbm3_fields(lbm3* h, double* rho_out, double* u_out);
+
+/* Diagnostics of the current state, accumulated in FP64 on the GPU:
+ * out[0..2] = sum of rho_k over fluid nodes, out[3] = sum x rho_0, out[4] = sum y rho_0,
+ * out[5] = max |u| of the last collision, out[6] = min rho, out[7] = count of non-finite rho_k.
+ * Returns LBM3_ERR_DIVERGED (with out filled) if out[7] > 0 or out[6] <= 0.  Synchronises. */
+int lbm3_diag(lbm3* h, double out[8]);
+
+/* Number of C_SB nodes (the wall list) and their node indices, in increasing order
+ * (cap = capacity of idx; returns the count or a negative status). */
+int lbm3_n_wall(const lbm3* h);
+int lbm3_wall_nodes(const lbm3* h, int32_t* idx, int32_t cap);
+
+/* Wall values C_0, C_1, C_2 at the C_SB nodes (in lbm3_wall_nodes order) as of the last wetting
+ * pass (before any step: the initial fluid-neighbour means); c: host [cap][3].  Returns the
+ * number of wall nodes or a negative status.  Synchronises. */
+int lbm3_wall_values(lbm3* h, double* c, int32_t cap);
+
+/* Checkpoint / resume.  The state of a simulation is its post-streaming populations
+ * f_post [3][9][ny][nx] (fluid k, direction a; 0 at solid nodes) and the wall values
+ * wall_c [3][ny][nx] that the next wetting pass reads in Eq.(21) (used at C_SB nodes only).
+ * lbm3_get_state copies both to host memory (synchronises); lbm3_set_state replaces the state
+ * (the populations of directions entering from an open side are recomputed by Zou-He). */
+int lbm3_get_state(lbm3* h, double* f_post, double* wall_c);
+int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c);
+
+/* Size facts: out[0] = fluid nodes, out[1] = C_SB nodes, out[2] = algorithmic HBM bytes of one
+ * step-kernel launch, out[3] = step kernels launched per timestep, out[4] = wetting kernels per
+ * timestep, out[5] = device bytes held by the handle. */
+int lbm3_info(const lbm3* h, int64_t out[8]);
+
+/* Change the stream used by later calls (cudaStream_t). */
+int lbm3_set_stream(lbm3* h, void* stream);
+
+/* Block until all work enqueued by the handle is done. */
+int lbm3_sync(lbm3* h);
+
+/* Release all device memory of the handle (NULL is ignored). */
+void lbm3_destroy(lbm3* h);
+
+/* Text of the last error or warning of the handle (or of the last failed lbm3_create when
+ * h == NULL). Valid until the next call on the same handle. */
+const char* lbm3_last_error(const lbm3* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM3_H */

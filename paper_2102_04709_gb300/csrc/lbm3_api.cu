@@ -1,0 +1,487 @@
+// lbm3_api.cu -- host side of the C ABI declared in include/lbm3.h: argument checks, node
+// classification (Section II.B), eighth-order solid normals (Eq.19-20), the compact wall list,
+// device buffers and the per-step launch sequence.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm3.h"
+#include "lbm3_common.cuh"
+
+using namespace lbm3k;
+
+struct lbm3 {
+    Params P{};
+    int precision = 0;
+    cudaStream_t stream = nullptr;
+    // device buffers
+    float* f[2] = {nullptr, nullptr};
+    uint8_t* type = nullptr;
+    double* Cw = nullptr;          // [3][N] wall values (written at C_SB nodes only)
+    float* u = nullptr;
+    float* scratch = nullptr;      // 3N floats for fields
+    double* partials = nullptr;    // diagnostics block partials
+    double* dout = nullptr;        // 8 doubles
+    int* widx = nullptr;
+    double* wnrm = nullptr;
+    float* wang = nullptr;
+    int nw = 0;
+    long long n_fluid = 0;
+    size_t bytes = 0;
+    int cur = 0;
+    bool ready = false;
+    std::vector<int> wall_host;
+    std::string err;
+};
+
+namespace {
+
+std::string g_create_error;
+
+int fail(lbm3* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg; else g_create_error = msg;
+    return code;
+}
+
+#define CUDA_TRY(h, call)                                                              \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess)                                                         \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? LBM3_ERR_OOM : LBM3_ERR_CUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));           \
+    } while (0)
+
+// Solid indicator s(x) of Eq.(19) at an unwrapped position: periodic sides wrap, wall sides
+// are solid beyond the domain, open sides are fluid beyond the domain.
+struct Indicator {
+    int nx, ny, per_y, bc_x;
+    const uint8_t* m;
+    int operator()(int X, int Y) const
+    {
+        if (Y < 0 || Y >= ny) {
+            if (!per_y) return 1;
+            Y = ((Y % ny) + ny) % ny;
+        }
+        if (X < 0 || X >= nx) {
+            if (bc_x == kWalls) return 1;
+            if (bc_x == kZouHe) return 0;
+            X = ((X % nx) + nx) % nx;
+        }
+        return m[(size_t)Y * nx + X] ? 1 : 0;
+    }
+    bool outside_solid(int X, int Y) const
+    {
+        if ((Y < 0 || Y >= ny) && !per_y) return true;
+        if ((X < 0 || X >= nx) && bc_x == kWalls) return true;
+        return false;
+    }
+};
+
+// g(X) of Eq.(15)
+double seg_g(double X)
+{
+    if (X < -1.0) return 1.0;
+    if (X > 1.0) return -1.0;
+    const double s = std::sqrt(std::max(0.0, 1.0 - X * X));  // sin(arccos X)
+    return X < 0.0 ? 1.0 - s : s - 1.0;
+}
+
+size_t tally(lbm3* h, size_t b)
+{
+    h->bytes += b;
+    return b;
+}
+
+void release(lbm3* h)
+{
+    void* ptrs[] = {h->f[0], h->f[1], h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
+                    h->widx, h->wnrm, h->wang};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->f[0] = h->f[1] = nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const double* angles,
+                const double sigma[3], const double nu[3], double beta0, void* stream)
+{
+    if (!out) return fail(nullptr, LBM3_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!g || !solid || !angles || !sigma || !nu)
+        return fail(nullptr, LBM3_ERR_INVALID, "NULL argument");
+    if (g->nx < 8 || g->ny < 8 || (long long)g->nx * g->ny >= (1LL << 31))
+        return fail(nullptr, LBM3_ERR_INVALID, "grid must be at least 8x8 and below 2^31 nodes");
+    if (g->bc_x < 0 || g->bc_x > 3) return fail(nullptr, LBM3_ERR_INVALID, "bad bc_x");
+    if (g->precision != LBM3_FP32)
+        return fail(nullptr, LBM3_ERR_INVALID, "precision not built in this library");
+    for (int j = 0; j < 3; j++) {
+        if (!(sigma[j] > 0.0) || !std::isfinite(sigma[j]))
+            return fail(nullptr, LBM3_ERR_INVALID, "sigma must be positive");
+        if (!(nu[j] > 0.0) || !std::isfinite(nu[j]))
+            return fail(nullptr, LBM3_ERR_INVALID, "nu must be positive");
+    }
+    if (!(beta0 >= 0.0)) return fail(nullptr, LBM3_ERR_INVALID, "beta0 must be >= 0");
+    if (g->bc_x == kZouHe && (!(std::fabs(g->u_in) < 0.3) || !(g->rho_out > 0.0)))
+        return fail(nullptr, LBM3_ERR_INVALID, "Zou-He needs |u_in| < 0.3 and rho_out > 0");
+    if (g->bc_x == kModPer && sigma[0] != sigma[2])
+        return fail(nullptr, LBM3_ERR_INVALID, "modified periodic boundary needs sigma_01 == sigma_12");
+
+    const int nx = g->nx, ny = g->ny;
+    const size_t N = (size_t)nx * ny;
+    const Indicator S{nx, ny, g->periodic_y ? 1 : 0, g->bc_x, solid};
+
+    // ---- node classes: a node is a boundary node when any D2Q9 neighbour is of the other kind
+    std::vector<uint8_t> cls(N);
+    long long n_fluid = 0;
+    for (int y = 0; y < ny; y++)
+        for (int x = 0; x < nx; x++) {
+            const int me = S(x, y);
+            bool touch = false;
+            for (int a = 1; a < kQ; a++) {
+                if (!me && S.outside_solid(x + ex(a), y + ey(a)))
+                    return fail(nullptr, LBM3_ERR_INVALID,
+                                "a fluid node touches a wall side: make the boundary rows/columns solid");
+                if (S(x + ex(a), y + ey(a)) != me) touch = true;
+            }
+            cls[(size_t)y * nx + x] = me ? (touch ? kSB : kSI) : (touch ? kFB : kFI);
+            n_fluid += !me;
+        }
+    if (g->bc_x == kZouHe) {
+        if (!g->periodic_y) return fail(nullptr, LBM3_ERR_INVALID, "Zou-He boundary needs periodic y");
+        for (int y = 0; y < ny; y++)
+            for (int j = 0; j < 4; j++)
+                if (solid[(size_t)y * nx + j] || solid[(size_t)y * nx + nx - 1 - j])
+                    return fail(nullptr, LBM3_ERR_INVALID, "no solid node allowed within 4 columns of an open side");
+    }
+
+    // ---- wall list: C_SB nodes, outward normals by the eighth-order stencil, angle triples
+    std::vector<int> widx;
+    std::vector<double> wnrm;
+    std::vector<float> wang;
+    double young = 0.0;
+    for (size_t i = 0; i < N; i++) {
+        if (cls[i] != kSB) continue;
+        const int x = (int)(i % nx), y = (int)(i / nx);
+        double sx = 0.0, sy = 0.0;
+        // eighth-order weights of Eq.(20) by |c|^2 (index = |c|^2)
+        static const double w8[9] = {0.0, 4.0 / 21.0, 4.0 / 45.0, 0.0, 1.0 / 60.0, 2.0 / 315.0, 0.0, 0.0, 1.0 / 5040.0};
+        for (int cy = -2; cy <= 2; cy++)
+            for (int cx = -2; cx <= 2; cx++) {
+                const int c2 = cx * cx + cy * cy;
+                if (c2 == 0 || w8[c2] == 0.0) continue;
+                if (S(x + cx, y + cy)) {
+                    sx += w8[c2] * cx;
+                    sy += w8[c2] * cy;
+                }
+            }
+        double len = std::sqrt(sx * sx + sy * sy);
+        if (len < 1e-12) {
+            sx = sy = 0.0;
+            for (int a = 1; a < kQ; a++)
+                if (S(x + ex(a), y + ey(a))) {
+                    const double w = a < 5 ? 1.0 / 9.0 : 1.0 / 36.0;
+                    sx += w * ex(a);
+                    sy += w * ey(a);
+                }
+            len = std::sqrt(sx * sx + sy * sy);
+            if (len < 1e-12) {
+                sx = 0.0;
+                sy = -1.0;
+                len = 1.0;
+            }
+        }
+        widx.push_back((int)i);
+        // Eq.(19) points into the solid; the characteristic lines leave along -n_s
+        wnrm.push_back(-sx / len);
+        wnrm.push_back(-sy / len);
+        double th[3];
+        for (int j = 0; j < 3; j++) {
+            th[j] = angles[3 * i + j];
+            if (!(th[j] > 0.0 && th[j] < 180.0))
+                return fail(nullptr, LBM3_ERR_INVALID, "wall angles must lie in (0, 180) degrees");
+            wang.push_back((float)th[j]);
+        }
+        const double d2r = M_PI / 180.0;
+        const double r = sigma[0] * std::cos(th[0] * d2r) + sigma[1] * std::cos(th[1] * d2r) +
+                         sigma[2] * std::cos(th[2] * d2r);
+        young = std::max(young, std::fabs(r));
+    }
+
+    // ---- parameters
+    lbm3* h = new lbm3();
+    h->stream = (cudaStream_t)stream;
+    h->precision = g->precision;
+    Params& P = h->P;
+    P.nx = nx;
+    P.ny = ny;
+    P.N = (long long)N;
+    P.per_y = g->periodic_y ? 1 : 0;
+    P.bc_x = g->bc_x;
+    P.u_in = (float)g->u_in;
+    P.rho_out = (float)g->rho_out;
+    P.sig01 = (float)sigma[0];
+    P.sig02 = (float)sigma[1];
+    P.sig12 = (float)sigma[2];
+    P.inv_nu0 = (float)(1.0 / nu[0]);
+    P.inv_nu1 = (float)(1.0 / nu[1]);
+    P.inv_nu2 = (float)(1.0 / nu[2]);
+    P.beta0 = (float)beta0;
+    // X_kl = (sigma_mk^2 + sigma_ml^2 - sigma_kl^2) / (2 sigma_mk sigma_ml), m = the third fluid
+    const double s01 = sigma[0], s02 = sigma[1], s12 = sigma[2];
+    P.g01 = (float)seg_g((s02 * s02 + s12 * s12 - s01 * s01) / (2.0 * s02 * s12));
+    P.g02 = (float)seg_g((s01 * s01 + s12 * s12 - s02 * s02) / (2.0 * s01 * s12));
+    P.g12 = (float)seg_g((s01 * s01 + s02 * s02 - s12 * s12) / (2.0 * s01 * s02));
+    h->nw = (int)widx.size();
+    h->n_fluid = n_fluid;
+    h->wall_host = widx;
+
+    // ---- device buffers
+    auto dmalloc = [&](void** p, size_t b) -> cudaError_t {
+        cudaError_t e = cudaMalloc(p, b ? b : 16);
+        if (e == cudaSuccess) tally(h, b);
+        return e;
+    };
+    const size_t fbytes = (size_t)27 * N * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = dmalloc((void**)&h->f[0], fbytes);
+    if (e == cudaSuccess) e = dmalloc((void**)&h->f[1], fbytes);
+    if (e == cudaSuccess) e = dmalloc((void**)&h->type, N);
+    if (e == cudaSuccess) e = dmalloc((void**)&h->Cw, 3 * N * sizeof(double));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->u, 2 * N * sizeof(float));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->scratch, 3 * N * sizeof(float));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->partials, (size_t)diag_blocks(P) * 8 * sizeof(double));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->dout, 8 * sizeof(double));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->widx, widx.size() * sizeof(int));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->wnrm, wnrm.size() * sizeof(double));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->wang, wang.size() * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(h->type, cls.data(), N, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !widx.empty()) e = cudaMemcpy(h->widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !wnrm.empty()) e = cudaMemcpy(h->wnrm, wnrm.data(), wnrm.size() * sizeof(double), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !wang.empty()) e = cudaMemcpy(h->wang, wang.data(), wang.size() * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->Cw, 0, 3 * N * sizeof(double));
+    if (e == cudaSuccess) e = cudaMemset(h->u, 0, 2 * N * sizeof(float));
+    if (e != cudaSuccess) {
+        const int code = e == cudaErrorMemoryAllocation ? LBM3_ERR_OOM : LBM3_ERR_CUDA;
+        release(h);
+        delete h;
+        return fail(nullptr, code, std::string("device set-up failed: ") + cudaGetErrorString(e));
+    }
+    *out = h;
+    if (young > 1e-6) {
+        char buf[160];
+        std::snprintf(buf, sizeof buf, "wall angles violate Eq.(18): max |sum sigma cos theta| = %.3g", young);
+        h->err = buf;
+        return LBM3_WARN_YOUNG;
+    }
+    h->err.clear();
+    return LBM3_OK;
+}
+
+int lbm3_set_fields(lbm3* h, const double* rho)
+{
+    if (!h || !rho) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)h->P.N;
+    double* drho = nullptr;
+    CUDA_TRY(h, cudaMallocAsync((void**)&drho, 3 * N * sizeof(double), h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(drho, rho, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->cur = 0;
+    launch_init_f32(h->P, drho, h->type, h->f[0], h->stream);
+    launch_wet_init(h->P, h->nw, h->widx, h->f[0], h->type, h->Cw, h->stream);
+    CUDA_TRY(h, cudaMemsetAsync(h->u, 0, 2 * N * sizeof(float), h->stream));
+    CUDA_TRY(h, cudaFreeAsync(drho, h->stream));
+    CUDA_TRY(h, cudaGetLastError());
+    h->ready = true;
+    return LBM3_OK;
+}
+
+int lbm3_step(lbm3* h, int32_t nsteps)
+{
+    if (!h) return fail(h, LBM3_ERR_INVALID, "NULL handle");
+    if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
+    if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
+    for (int s = 0; s < nsteps; s++) {
+        float* fin = h->f[h->cur];
+        float* fo = h->f[1 - h->cur];
+        launch_wet(h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->stream);
+        launch_step_f32(h->P, fin, fo, h->type, h->Cw, s == nsteps - 1 ? h->u : nullptr, h->stream);
+        h->cur = 1 - h->cur;
+    }
+    CUDA_TRY(h, cudaGetLastError());
+    return LBM3_OK;
+}
+
+int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[2])
+{
+    if (!h || !ms_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
+    if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
+    ms_out[0] = ms_out[1] = 0.0;
+    std::vector<cudaEvent_t> ev(3 * (size_t)nsteps);
+    for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
+    for (int s = 0; s < nsteps; s++) {
+        float* fin = h->f[h->cur];
+        float* fo = h->f[1 - h->cur];
+        CUDA_TRY(h, cudaEventRecord(ev[3 * s], h->stream));
+        launch_wet(h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->stream);
+        CUDA_TRY(h, cudaEventRecord(ev[3 * s + 1], h->stream));
+        launch_step_f32(h->P, fin, fo, h->type, h->Cw, s == nsteps - 1 ? h->u : nullptr, h->stream);
+        CUDA_TRY(h, cudaEventRecord(ev[3 * s + 2], h->stream));
+        h->cur = 1 - h->cur;
+    }
+    CUDA_TRY(h, cudaGetLastError());
+    if (nsteps > 0) CUDA_TRY(h, cudaEventSynchronize(ev[3 * (nsteps - 1) + 2]));
+    for (int s = 0; s < nsteps; s++) {
+        float a = 0.f, b = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]));
+        CUDA_TRY(h, cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]));
+        ms_out[0] += a;
+        ms_out[1] += b;
+    }
+    for (auto& e : ev) cudaEventDestroy(e);
+    return LBM3_OK;
+}
+
+int lbm3_fields(lbm3* h, double* rho_out, double* u_out)
+{
+    if (!h || !rho_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
+    const size_t N = (size_t)h->P.N;
+    launch_fields_f32(h->P, h->f[h->cur], h->type, h->scratch, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    std::vector<float> tmp(3 * N);
+    CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), h->scratch, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    std::vector<float> tu;
+    if (u_out) {
+        tu.resize(2 * N);
+        CUDA_TRY(h, cudaMemcpyAsync(tu.data(), h->u, 2 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < 3 * N; i++) rho_out[i] = tmp[i];
+    if (u_out)
+        for (size_t i = 0; i < 2 * N; i++) u_out[i] = tu[i];
+    return LBM3_OK;
+}
+
+int lbm3_diag(lbm3* h, double out[8])
+{
+    if (!h || !out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
+    launch_diag_f32(h->P, h->f[h->cur], h->type, h->u, h->partials, h->dout, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaMemcpyAsync(out, h->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (out[7] > 0.0 || !(out[6] > 0.0)) return fail(h, LBM3_ERR_DIVERGED, "non-finite or non-positive density");
+    return LBM3_OK;
+}
+
+int lbm3_n_wall(const lbm3* h) { return h ? h->nw : LBM3_ERR_INVALID; }
+
+int lbm3_wall_nodes(const lbm3* h, int32_t* idx, int32_t cap)
+{
+    if (!h || (!idx && cap > 0)) return LBM3_ERR_INVALID;
+    const int n = std::min<int>(cap, h->nw);
+    for (int j = 0; j < n; j++) idx[j] = h->wall_host[j];
+    return h->nw;
+}
+
+int lbm3_wall_values(lbm3* h, double* c, int32_t cap)
+{
+    if (!h || (!c && cap > 0)) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
+    const size_t N = (size_t)h->P.N;
+    std::vector<double> cw(3 * N);
+    CUDA_TRY(h, cudaMemcpyAsync(cw.data(), h->Cw, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    const int n = std::min<int>(cap, h->nw);
+    for (int j = 0; j < n; j++) {
+        const size_t i = (size_t)h->wall_host[j];
+        for (int k = 0; k < 3; k++) c[3 * j + k] = cw[k * N + i];
+    }
+    return h->nw;
+}
+
+int lbm3_get_state(lbm3* h, double* f_post, double* wall_c)
+{
+    if (!h || !f_post) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
+    const size_t N = (size_t)h->P.N;
+    float* post = h->f[1 - h->cur];  // the idle population buffer serves as scratch
+    launch_get_state_f32(h->P, h->f[h->cur], h->type, post, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
+    std::vector<float> tmp(27 * N);
+    CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), post, 27 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    std::vector<double> cw;
+    if (wall_c) {
+        cw.resize(3 * N);
+        CUDA_TRY(h, cudaMemcpyAsync(cw.data(), h->Cw, 3 * N * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    }
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    for (size_t i = 0; i < 27 * N; i++) f_post[i] = tmp[i];
+    if (wall_c) std::memcpy(wall_c, cw.data(), 3 * N * sizeof(double));
+    return LBM3_OK;
+}
+
+int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c)
+{
+    if (!h || !f_post || !wall_c) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    const size_t N = (size_t)h->P.N;
+    double* dpost = nullptr;
+    CUDA_TRY(h, cudaMallocAsync((void**)&dpost, 27 * N * sizeof(double), h->stream));
+    CUDA_TRY(h, cudaMemcpyAsync(dpost, f_post, 27 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->cur = 0;
+    launch_set_state_f32(h->P, dpost, h->type, h->f[0], h->stream);
+    CUDA_TRY(h, cudaMemcpyAsync(h->Cw, wall_c, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaMemsetAsync(h->u, 0, 2 * N * sizeof(float), h->stream));
+    CUDA_TRY(h, cudaFreeAsync(dpost, h->stream));
+    CUDA_TRY(h, cudaGetLastError());
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    h->ready = true;
+    return LBM3_OK;
+}
+
+int lbm3_info(const lbm3* h, int64_t out[8])
+{
+    if (!h || !out) return LBM3_ERR_INVALID;
+    for (int j = 0; j < 8; j++) out[j] = 0;
+    out[0] = h->n_fluid;
+    out[1] = h->nw;
+    // 27 FP32 populations read and written per fluid node, plus one class byte per node
+    out[2] = h->n_fluid * 216 + h->P.N;
+    out[3] = 1;
+    out[4] = h->nw > 0 ? 1 : 0;
+    out[5] = (int64_t)h->bytes;
+    return LBM3_OK;
+}
+
+int lbm3_set_stream(lbm3* h, void* stream)
+{
+    if (!h) return LBM3_ERR_INVALID;
+    h->stream = (cudaStream_t)stream;
+    return LBM3_OK;
+}
+
+int lbm3_sync(lbm3* h)
+{
+    if (!h) return LBM3_ERR_INVALID;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM3_OK;
+}
+
+void lbm3_destroy(lbm3* h)
+{
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+const char* lbm3_last_error(const lbm3* h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,217 @@
+// lbm3_common.cuh -- lattice constants, parameters and device helpers shared by the
+// kernels of the three-phase colour-gradient step (arXiv:2102.04709, Section II).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace lbm3k {
+
+constexpr int kQ = 9;   // D2Q9
+constexpr int kNF = 3;  // fluids r, g, b -> 0, 1, 2
+
+// node classes of Section II.B (Fig.1); bit 1 set = solid
+enum : uint8_t { kFI = 0, kFB = 1, kSB = 2, kSI = 3 };
+// x boundary kinds
+enum : int { kPeriodic = 0, kModPer = 1, kZouHe = 2, kWalls = 3 };
+// population storage
+enum : int { kStoreF32 = 0, kStoreF16 = 1, kStoreBF16 = 2 };
+
+// D2Q9 velocities e_0..e_8 = (0,0), (1,0), (0,1), (-1,0), (0,-1), (1,1), (-1,1), (-1,-1), (1,-1)
+__host__ __device__ constexpr int ex(int a)
+{
+    return (a == 1 || a == 5 || a == 8) ? 1 : ((a == 3 || a == 6 || a == 7) ? -1 : 0);
+}
+__host__ __device__ constexpr int ey(int a)
+{
+    return (a == 2 || a == 5 || a == 6) ? 1 : ((a == 4 || a == 7 || a == 8) ? -1 : 0);
+}
+// weights 4/9, 1/9 (axes), 1/36 (diagonals)
+__host__ __device__ constexpr float wq(int a)
+{
+    return a == 0 ? 4.0f / 9.0f : (a < 5 ? 1.0f / 9.0f : 1.0f / 36.0f);
+}
+// opposite direction
+__host__ __device__ constexpr int opp(int a)
+{
+    return a == 0 ? 0 : (a < 5 ? ((a + 1) % 4) + 1 : ((a - 3) % 4) + 5);
+}
+// label of fluid k after crossing the modified periodic seam an odd number of times
+__host__ __device__ constexpr int relabel(int k, bool swapped) { return (swapped && k != 1) ? 2 - k : k; }
+
+struct Params {
+    int nx, ny;
+    long long N;          // nx * ny
+    int per_y, bc_x;
+    float u_in, rho_out;
+    float sig01, sig02, sig12;
+    float inv_nu0, inv_nu1, inv_nu2;
+    float beta0;
+    float g01, g02, g12;  // g(X_kl) of Eq.(15), constant per pair
+};
+
+// Reduced-storage view (per fluid: FP32 rho_k plane + 8 16-bit offset planes).
+struct R16 {
+    float* rho;           // [3][N]
+    uint16_t* off;        // [3][8][N]; offset of direction a (1..8) is plane a-1
+};
+
+__host__ __device__ inline int floordiv_i(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// Where an unwrapped lattice position lives.  kind: 0 inside, 1 solid outside a wall side,
+// 2 ghost beyond an open x side (idx = nearest boundary-column node).  par: the position lies
+// an odd number of modified-periodic seams away from the home domain.
+struct Loc {
+    int idx;
+    int kind;
+    bool par;
+};
+
+__device__ __forceinline__ Loc locate(const Params& P, int X, int Y)
+{
+    Loc L;
+    L.par = false;
+    L.kind = 0;
+    L.idx = 0;
+    if (Y < 0 || Y >= P.ny) {
+        if (!P.per_y) {
+            L.kind = 1;
+            return L;
+        }
+        Y -= floordiv_i(Y, P.ny) * P.ny;
+    }
+    if (X < 0 || X >= P.nx) {
+        if (P.bc_x == kPeriodic || P.bc_x == kModPer) {
+            int q = floordiv_i(X, P.nx);
+            X -= q * P.nx;
+            L.par = (P.bc_x == kModPer) && (q & 1);
+        } else if (P.bc_x == kWalls) {
+            L.kind = 1;
+            return L;
+        } else {
+            X = X < 0 ? 0 : P.nx - 1;
+            L.kind = 2;
+        }
+    }
+    L.idx = Y * P.nx + X;
+    return L;
+}
+
+__device__ __forceinline__ bool parity_x(const Params& P, int X)
+{
+    return P.bc_x == kModPer && (floordiv_i(X, P.nx) & 1);
+}
+
+// Zou-He completion of the populations p[k*9+a] of a node in an open column
+// (inlet: x = 0, unknown a = 1, 5, 8; outlet: x = nx-1, unknown a = 3, 6, 7).
+__device__ __forceinline__ void zou_he(const Params& P, float p[27], bool inlet)
+{
+    float f[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; a++) f[a] = p[a] + p[9 + a] + p[18 + a];
+    if (inlet) {
+        const float U = P.u_in;
+        const float rho = (f[0] + f[2] + f[4] + 2.0f * (f[3] + f[6] + f[7])) / (1.0f - U);
+        const float half = 0.5f * (f[2] - f[4]);
+        const float g1 = f[3] + (2.0f / 3.0f) * rho * U;
+        const float g5 = f[7] - half + (1.0f / 6.0f) * rho * U;
+        const float g8 = f[6] + half + (1.0f / 6.0f) * rho * U;
+        // the inlet reservoir holds the carrier fluid 2
+        p[1] = p[5] = p[8] = 0.0f;
+        p[10] = p[14] = p[17] = 0.0f;
+        p[19] = g1;
+        p[23] = g5;
+        p[26] = g8;
+    } else {
+        const float ro = P.rho_out;
+        const float ux = -1.0f + (f[0] + f[2] + f[4] + 2.0f * (f[1] + f[5] + f[8])) / ro;
+        const float half = 0.5f * (f[2] - f[4]);
+        const float h3 = f[1] - (2.0f / 3.0f) * ro * ux;
+        const float h7 = f[5] + half - (1.0f / 6.0f) * ro * ux;
+        const float h6 = f[8] - half - (1.0f / 6.0f) * ro * ux;
+        float part[kNF], tot = 0.0f;
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            const float* q = p + 9 * k;
+            part[k] = q[0] + q[1] + q[2] + q[4] + q[5] + q[8];
+            tot += part[k];
+        }
+        const float it = 1.0f / tot;
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            p[9 * k + 3] = h3 * part[k] * it;
+            p[9 * k + 6] = h6 * part[k] * it;
+            p[9 * k + 7] = h7 * part[k] * it;
+        }
+    }
+}
+
+// Post-streaming populations of fluid k for the pull from a stored buffer.
+template <int STORE>
+struct Store;
+
+template <>
+struct Store<kStoreF32> {
+    const float* f;  // [27][N] post-collision, pre-streaming populations
+    long long N;
+    // population a of (storage) fluid k stored at node idx
+    __device__ __forceinline__ float get(int k, int a, int idx) const
+    {
+        return __ldg(f + (long long)(k * kQ + a) * N + idx);
+    }
+};
+
+// Pull the post-streaming populations of the fluid node at unwrapped (X, Y) from global
+// memory (labels in the frame of that unwrapped position), Eq.(16) with halfway bounce-back,
+// periodic / modified periodic wrap and Zou-He on open columns.  A ghost position beyond an
+// open side returns the populations of the nearest boundary-column node.
+template <class S>
+__device__ void pull_global(const Params& P, const S& st, const uint8_t* __restrict__ type,
+                            int X, int Y, float p[27])
+{
+    Loc n = locate(P, X, Y);
+    int nX = X;
+    if (n.kind == 2) nX = X < 0 ? 0 : P.nx - 1;
+    bool inlet = false, outlet = false;
+#pragma unroll
+    for (int a = 0; a < kQ; a++) {
+        Loc s = locate(P, nX - ex(a), Y - ey(a));
+        if (s.kind == 2) {
+            if (nX == 0) inlet = true; else outlet = true;
+#pragma unroll
+            for (int k = 0; k < kNF; k++) p[9 * k + a] = 0.0f;
+        } else if (s.kind == 1 || (__ldg(type + s.idx) & 2)) {
+#pragma unroll
+            for (int k = 0; k < kNF; k++) p[9 * k + a] = st.get(relabel(k, n.par), opp(a), n.idx);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kNF; k++) p[9 * k + a] = st.get(relabel(k, s.par), a, s.idx);
+        }
+    }
+    if (inlet) zou_he(P, p, true);
+    if (outlet) zou_he(P, p, false);
+}
+
+// ---- kernel launchers (lbm3_step.cu) ----
+void launch_wet(const Params& P, int nw, const int* widx, const double* wnrm, const float* wang,
+                const float* f, const uint8_t* type, double* Cw, cudaStream_t s);
+void launch_wet_init(const Params& P, int nw, const int* widx, const float* f,
+                     const uint8_t* type, double* Cw, cudaStream_t s);
+void launch_step_f32(const Params& P, const float* fin, float* fout, const uint8_t* type,
+                     const double* Cw, float* u, cudaStream_t s);
+void launch_init_f32(const Params& P, const double* rho, const uint8_t* type, float* f,
+                     cudaStream_t s);
+void launch_fields_f32(const Params& P, const float* f, const uint8_t* type, float* rho_out,
+                       cudaStream_t s);
+void launch_get_state_f32(const Params& P, const float* f, const uint8_t* type, float* post,
+                          cudaStream_t s);
+void launch_set_state_f32(const Params& P, const double* post, const uint8_t* type, float* f,
+                          cudaStream_t s);
+int diag_blocks(const Params& P);
+void launch_diag_f32(const Params& P, const float* f, const uint8_t* type, const float* u,
+                     double* partials, double* out, cudaStream_t s);
+const char* step_kernel_name();
+
+}  // namespace lbm3k

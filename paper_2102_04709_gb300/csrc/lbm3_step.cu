@@ -1,0 +1,843 @@
+// lbm3_step.cu -- sm_103a kernels of one timestep of the three-phase MRT colour-gradient
+// lattice Boltzmann model with the characteristic-line wetting condition
+// (arXiv:2102.04709, Section II).
+//
+//   k_wet      Eq.(21)-(22) and the characteristic lines of Section II.B, one thread per
+//              solid boundary node (C_SB), FP64 ray geometry
+//   k_step     fused Eq.(1)-(16): pull-streaming with halfway bounce-back (and the x boundary),
+//              densities and phase fields, isotropic gradients (Eq.12), the surface-stress
+//              tensor and its divergence (Eq.10), MRT collision with forcing (Eq.1-9, 11),
+//              recolouring (Eq.13-15); one CTA per TX x TY tile, halo staged in shared memory
+//   k_init     rest-equilibrium initial state written as the pre-image of a pull
+//   k_fields   post-streaming densities
+//   k_diag     FP64 block partials of mass, centroid, max|u|, min rho, non-finite count
+#include <cfloat>
+#include <cmath>
+
+#include "lbm3_common.cuh"
+
+namespace lbm3k {
+
+namespace {
+
+constexpr float kG2Eps = 1e-24f;   // |G|^2 at or below which n_kl = 0 and the stress vanishes
+constexpr double kRayEps = 1e-6;   // crossings this close to a node are node hits
+constexpr double kPhiSnap = 1e-6;  // |90 - theta_k| below this (deg): both lines along n_s
+constexpr double kRayTmax = 16.0;  // the characteristic-line search stops beyond this length
+
+// ------------------------------------------------------------------------------------------
+// wetting: characteristic lines (Section II.B)
+// ------------------------------------------------------------------------------------------
+template <class S>
+__device__ __forceinline__ bool node_is_fluid(const Params& P, const uint8_t* __restrict__ type,
+                                              int X, int Y)
+{
+    Loc L = locate(P, X, Y);
+    if (L.kind != 0) return false;  // solid beyond a wall side, or beyond an open side
+    return !(__ldg(type + L.idx) & 2);
+}
+
+// C_k at the fluid node at unwrapped (X, Y), in the frame of the home domain (FP64 sums of the
+// stored populations, so that a node holding one fluid gives exactly 0 or 1)
+template <class S>
+__device__ double node_C(const Params& P, const S& st, const uint8_t* __restrict__ type, int X,
+                         int Y, int k)
+{
+    float p[27];
+    pull_global(P, st, type, X, Y, p);
+    double r[kNF];
+#pragma unroll
+    for (int j = 0; j < kNF; j++) {
+        double s = 0.0;
+#pragma unroll
+        for (int a = 0; a < kQ; a++) s += (double)p[9 * j + a];
+        r[j] = s;
+    }
+    return r[k] / (r[0] + r[1] + r[2]);
+}
+
+template <class S>
+__device__ double neighbour_mean(const Params& P, const S& st, const uint8_t* __restrict__ type,
+                                 int px, int py, int k)
+{
+    double s = 0.0, ws = 0.0;
+#pragma unroll 1
+    for (int a = 1; a < kQ; a++) {
+        if (node_is_fluid<S>(P, type, px + ex(a), py + ey(a))) {
+            const double w = a < 5 ? 1.0 / 9.0 : 1.0 / 36.0;
+            s += w * node_C(P, st, type, px + ex(a), py + ey(a), k);
+            ws += w;
+        }
+    }
+    return ws > 0.0 ? s / ws : 0.0;
+}
+
+// March from the C_SB node (px, py) along direction (dx, dy); C_D at the first grid-line
+// crossing whose bracketing nodes are both fluid (node hits use the node itself).
+template <class S>
+__device__ bool characteristic_line(const Params& P, const S& st, const uint8_t* __restrict__ type,
+                                    int px, int py, double dx, double dy, int k, double* CD)
+{
+    const int sx = dx > 0.0 ? 1 : -1;
+    const int sy = dy > 0.0 ? 1 : -1;
+    int X = px + sx;  // next vertical grid line
+    int Y = py + sy;  // next horizontal grid line
+    double tX = fabs(dx) > 1e-14 ? (double)(X - px) / dx : HUGE_VAL;
+    double tY = fabs(dy) > 1e-14 ? (double)(Y - py) / dy : HUGE_VAL;
+#pragma unroll 1
+    for (int it = 0; it < 64; it++) {
+        const double t = fmin(tX, tY);
+        if (!(t <= kRayTmax)) return false;
+        const bool onX = (tX - t) <= kRayEps;
+        const bool onY = (tY - t) <= kRayEps;
+        if (onX && onY) {
+            if (node_is_fluid<S>(P, type, X, Y)) {
+                *CD = node_C(P, st, type, X, Y, k);
+                return true;
+            }
+        } else {
+            // position along the crossed line, without fused multiply-add so that the node-hit
+            // test sees the same value as a plain double evaluation
+            const double s = onX ? __dadd_rn((double)py, __dmul_rn(t, dy))
+                                 : __dadd_rn((double)px, __dmul_rn(t, dx));
+            const double sr = floor(s + 0.5);
+            if (fabs(s - sr) < kRayEps) {
+                const int nx_ = onX ? X : (int)sr, ny_ = onX ? (int)sr : Y;
+                if (node_is_fluid<S>(P, type, nx_, ny_)) {
+                    *CD = node_C(P, st, type, nx_, ny_, k);
+                    return true;
+                }
+            } else {
+                const int s0 = (int)floor(s);
+                const double fr = s - (double)s0;
+                const int ax = onX ? X : s0, ay = onX ? s0 : Y;
+                const int bx = onX ? X : s0 + 1, by = onX ? s0 + 1 : Y;
+                if (node_is_fluid<S>(P, type, ax, ay) && node_is_fluid<S>(P, type, bx, by)) {
+                    const double ca = node_C(P, st, type, ax, ay, k);
+                    const double cb = node_C(P, st, type, bx, by, k);
+                    *CD = ca + fr * (cb - ca);
+                    return true;
+                }
+            }
+        }
+        if (onX) {
+            X += sx;
+            tX = (double)(X - px) / dx;
+        }
+        if (onY) {
+            Y += sy;
+            tY = (double)(Y - py) / dy;
+        }
+    }
+    return false;
+}
+
+template <class S>
+__device__ double wet_fluid(const Params& P, const S& st, const uint8_t* __restrict__ type, int px,
+                            int py, double nx_, double ny_, double theta, int k)
+{
+    const double dev = fabs(90.0 - theta);
+    const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
+    double sn, cs;
+    sincos(phi, &sn, &cs);
+    // the two lines make the angle phi with n_s, one on each side (tangent (-n_y, n_x))
+    const double d1x = cs * nx_ - sn * ny_, d1y = cs * ny_ + sn * nx_;
+    const double d2x = cs * nx_ + sn * ny_, d2y = cs * ny_ - sn * nx_;
+    double c1, c2;
+    if (!characteristic_line(P, st, type, px, py, d1x, d1y, k, &c1)) c1 = neighbour_mean(P, st, type, px, py, k);
+    if (!characteristic_line(P, st, type, px, py, d2x, d2y, k, &c2)) c2 = neighbour_mean(P, st, type, px, py, k);
+    return theta <= 90.0 ? fmax(c1, c2) : fmin(c1, c2);  // Eq.(22)
+}
+
+// Eq.(21) for one fluid k with the other two fractions w_m, w_l and angles t_m, t_l: the paper's
+// (w_m t_m + w_l t_l) / (1 - C_k) with 1 - C_k = w_m + w_l, written as the convex combination
+// t_l + w_m / (w_m + w_l) (t_m - t_l); the mean of the two angles when both weights vanish
+__device__ __forceinline__ double local_angle(double wm, double tm, double wl, double tl)
+{
+    return wm + wl < 1e-12 ? 0.5 * (tm + tl) : tl + wm / (wm + wl) * (tm - tl);
+}
+
+template <class S>
+__global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const int* __restrict__ widx,
+                                             const double* __restrict__ wnrm,
+                                             const float* __restrict__ wang, const S st,
+                                             const uint8_t* __restrict__ type, double* __restrict__ Cw)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    const int i = widx[w];
+    const int px = i % P.nx, py = i / P.nx;
+    // Eq.(21) with the wall values of the previous step
+    const double Cr = Cw[i], Cg = Cw[P.N + i], Cb = Cw[2 * P.N + i];
+    const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
+    const double t_rb = 180.0 - t_br, t_gr = 180.0 - t_rg;
+    const double th_r = local_angle(Cb, t_rb, Cg, t_rg);
+    const double th_g = local_angle(Cb, t_gb, Cr, t_gr);
+    const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
+    double cr = wet_fluid(P, st, type, px, py, nx_, ny_, th_r, 0);
+    double cg = wet_fluid(P, st, type, px, py, nx_, ny_, th_g, 1);
+    const double s = cr + cg;
+    if (s > 1.0) {
+        cr /= s;
+        cg /= s;
+    }
+    Cw[i] = cr;
+    Cw[P.N + i] = cg;
+    Cw[2 * P.N + i] = fmax(0.0, 1.0 - cr - cg);
+}
+
+// initial wall values: w-weighted mean of the fluid neighbours, for each fluid
+template <class S>
+__global__ void k_wet_init(const Params P, const int nw, const int* __restrict__ widx, const S st,
+                           const uint8_t* __restrict__ type, double* __restrict__ Cw)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    const int i = widx[w];
+    const int px = i % P.nx, py = i / P.nx;
+    for (int k = 0; k < kNF; k++) Cw[k * P.N + i] = neighbour_mean(P, st, type, px, py, k);
+}
+
+// ------------------------------------------------------------------------------------------
+// fused step
+// ------------------------------------------------------------------------------------------
+// Rest populations of unit density as R constants, and the FP64 residuals of the rounded
+// constants in the density and energy moments: sum_a fl(w_a) = 1 + kDRho, energy row
+// M_1 . fl(w) = -2 + kDE, M_2 . fl(w) = 1 + kDEps (row weights -4 + 3|e|^2 and
+// 4 - 21/2 |e|^2 + 9/2 |e|^4).  Moments are taken of f - fl(w), which is exact for
+// populations within a factor 2 of fl(w_a) and small otherwise, so that the equilibrium
+// deviations e - e_eq and eps - eps_eq carry no O(1) cancellation.
+constexpr float kW0 = 4.0f / 9.0f, kW1 = 1.0f / 9.0f, kW5 = 1.0f / 36.0f;
+constexpr double kDRho = (double)kW0 + 4.0 * (double)kW1 + 4.0 * (double)kW5 - 1.0;
+constexpr double kDE = -4.0 * (double)kW0 - 4.0 * (double)kW1 + 8.0 * (double)kW5 + 2.0;
+constexpr double kDEps = 4.0 * (double)kW0 - 8.0 * (double)kW1 + 4.0 * (double)kW5 - 1.0;
+
+// MRT collision with forcing in moment space (the rows of M in Eq.4; M^-1 = M^T diag(1/|row|^2)).
+// f: totals f_a; F: interfacial force; returns f_dag in f and the velocity of Eq.(11).  The
+// update is applied as f_dag = f + M^-1 dm with dm = -S (m - m_eq) + (I - S/2) M Ftilde, so that
+// the rounded constants 1/9, 1/36 ... only scale the small non-equilibrium change (dm_0 = 0).
+template <typename R>
+__device__ __forceinline__ void collide_mrt(R f[kQ], R rho, R Fx, R Fy, R tau, R& ux, R& uy)
+{
+    const R d0 = f[0] - kW0;
+    const R d1 = f[1] - kW1, d2 = f[2] - kW1, d3 = f[3] - kW1, d4 = f[4] - kW1;
+    const R d5 = f[5] - kW5, d6 = f[6] - kW5, d7 = f[7] - kW5, d8 = f[8] - kW5;
+    const R b14 = (d1 + d3) + (d2 + d4);
+    const R b58 = (d5 + d7) + (d6 + d8);
+    const R drho = (d0 + b14) + b58 + (R)kDRho;          // rho - 1
+    const R de = (-R(4.0) * d0 - b14 + R(2.0) * b58) + (R)kDE;   // e + 2
+    const R deps = (R(4.0) * d0 - R(2.0) * b14 + b58) + (R)kDEps; // eps - 1
+    const R jx = (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+    const R qx = -R(2.0) * (f[1] - f[3]) + (f[5] - f[7]) + (f[8] - f[6]);
+    const R jy = (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    const R qy = -R(2.0) * (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
+    const R pxx = (f[1] - f[2]) + (f[3] - f[4]);
+    const R pxy = (f[5] - f[6]) + (f[7] - f[8]);
+    const R irho = R(1.0) / rho;
+    ux = (jx + R(0.5) * Fx) * irho;  // Eq.(11)
+    uy = (jy + R(0.5) * Fy) * irho;
+    const R u2 = ux * ux + uy * uy;
+    const R uF = ux * Fx + uy * Fy;
+    // relaxation rates, Eq.(5)-(6)
+    const R s1 = R(1.0) / tau;
+    const R s4 = R(8.0) * (R(2.0) - s1) / (R(8.0) - s1);
+    const R h1 = R(1.0) - R(0.5) * s1, h4 = R(1.0) - R(0.5) * s4;
+    // moment changes: relaxation towards the Eq.(3) equilibrium moments
+    // e_eq = rho(-2 + 3u^2), eps_eq = rho(1 - 3u^2), q_eq = -rho u, p_eq = rho(ux^2 - uy^2), rho ux uy,
+    // plus the moments of the Eq.(9) forcing vector
+    // (0, 6uF, -6uF, Fx, -Fx, Fy, -Fy, 2(uxFx - uyFy), uxFy + uyFx)
+    const R dE = -s1 * (de + R(2.0) * drho - R(3.0) * rho * u2) + h1 * R(6.0) * uF;
+    const R dEps = -s1 * (deps - drho + R(3.0) * rho * u2) - h1 * R(6.0) * uF;
+    const R djx = Fx, djy = Fy;
+    const R dqx = -s4 * (qx + rho * ux) - h4 * Fx;
+    const R dqy = -s4 * (qy + rho * uy) - h4 * Fy;
+    const R dpxx = -s1 * (pxx - rho * (ux * ux - uy * uy)) + h1 * R(2.0) * (ux * Fx - uy * Fy);
+    const R dpxy = -s1 * (pxy - rho * ux * uy) + h1 * (ux * Fy + uy * Fx);
+    // back to populations
+    const R c0 = (R(1.0) / R(9.0)) * (dEps - dE);
+    const R ca = -(R(1.0) / R(36.0)) * dE - (R(1.0) / R(18.0)) * dEps;
+    const R cd = (R(1.0) / R(18.0)) * dE + (R(1.0) / R(36.0)) * dEps;
+    const R X1 = (R(1.0) / R(6.0)) * (djx - dqx), Y1 = (R(1.0) / R(6.0)) * (djy - dqy);
+    const R X2 = (R(1.0) / R(6.0)) * djx + (R(1.0) / R(12.0)) * dqx;
+    const R Y2 = (R(1.0) / R(6.0)) * djy + (R(1.0) / R(12.0)) * dqy;
+    const R P4 = R(0.25) * dpxx, Q4 = R(0.25) * dpxy;
+    f[0] += c0;
+    f[1] += ca + X1 + P4;
+    f[2] += ca + Y1 - P4;
+    f[3] += ca - X1 + P4;
+    f[4] += ca - Y1 - P4;
+    f[5] += cd + X2 + Y2 + Q4;
+    f[6] += cd - X2 + Y2 - Q4;
+    f[7] += cd - X2 - Y2 + Q4;
+    f[8] += cd + X2 - Y2 - Q4;
+}
+
+// accumulate sigma A (|G|^2 I - G G)/|G| of one fluid pair into (Txx, Txy, Tyy)
+template <typename R>
+__device__ __forceinline__ void pair_stress(R sig, R ck, R cl, R gkx, R gky, R glx, R gly, R rho2,
+                                            R& Txx, R& Txy, R& Tyy)
+{
+    const R Gx = cl * gkx - ck * glx;
+    const R Gy = cl * gky - ck * gly;
+    const R G2 = Gx * Gx + Gy * Gy;
+    if (G2 > kG2Eps) {
+        const R A = fmin(1e6f * ck * cl * rho2, R(1.0));
+        const R s = sig * A * rsqrt(G2);
+        Txx += s * Gy * Gy;
+        Txy -= s * Gx * Gy;
+        Tyy += s * Gx * Gx;
+    }
+}
+
+// unit normal of one pair (0 if |G| vanishes)
+template <typename R>
+__device__ __forceinline__ void pair_normal(R ck, R cl, R gkx, R gky, R glx, R gly, R& nx_, R& ny_)
+{
+    const R Gx = cl * gkx - ck * glx;
+    const R Gy = cl * gky - ck * gly;
+    const R G2 = Gx * Gx + Gy * Gy;
+    if (G2 > kG2Eps) {
+        const R r = rsqrt(G2);
+        nx_ = Gx * r;
+        ny_ = Gy * r;
+    } else {
+        nx_ = ny_ = R(0.0);
+    }
+}
+
+// ---- compensated (float-float) phase fields ----
+// Near a contact line the colour gradient of a well-mixed node can be 1e-3 while C ~ 0.5, so
+// the normal n_kl = G_kl/|G_kl| of Eq.(13) and the stress of Eq.(10) need C to more bits than a
+// float holds.  C_k is kept as an unevaluated pair hi + lo: the populations are summed with
+// error-free transformations (Knuth's TwoSum), the division carries its exact FMA residual,
+// and the Eq.(12) stencil is applied to hi and lo separately (hi differences of close values
+// are exact).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// sum of the 9 populations q[0..8] as hi + lo
+__device__ __forceinline__ void sum9_df(const float* q, float& hi, float& lo)
+{
+    float s = q[0], e = 0.0f;
+#pragma unroll
+    for (int a = 1; a < kQ; a++) {
+        float t;
+        two_sum(s, q[a], s, t);
+        e += t;
+    }
+    two_sum(s, e, hi, lo);
+}
+
+// (nh + nl) / (dh + dl) as hi + lo
+__device__ __forceinline__ void div_df(float nh, float nl, float dh, float dl, float& qh, float& ql)
+{
+    qh = nh / dh;
+    const float r = fmaf(-qh, dh, nh) + nl - qh * dl;
+    ql = r / dh;
+}
+
+// Eq.(12) derivative weights: d_x psi = (psi_1 - psi_3)/3 + (psi_5 - psi_6 - psi_7 + psi_8)/12
+template <int W, typename R>
+__device__ __forceinline__ void grad9_df(const float (*h)[W], const float (*l)[W], int cx, int cy,
+                                         R& gx, R& gy)
+{
+    R hx, hy, lx_, ly_;
+    {
+        const R c1 = h[cy][cx + 1], c3 = h[cy][cx - 1], c2 = h[cy + 1][cx], c4 = h[cy - 1][cx];
+        const R c5 = h[cy + 1][cx + 1], c6 = h[cy + 1][cx - 1], c7 = h[cy - 1][cx - 1], c8 = h[cy - 1][cx + 1];
+        hx = (R(1.0) / R(3.0)) * (c1 - c3) + (R(1.0) / R(12.0)) * ((c5 - c7) + (c8 - c6));
+        hy = (R(1.0) / R(3.0)) * (c2 - c4) + (R(1.0) / R(12.0)) * ((c5 - c7) + (c6 - c8));
+    }
+    {
+        const R c1 = l[cy][cx + 1], c3 = l[cy][cx - 1], c2 = l[cy + 1][cx], c4 = l[cy - 1][cx];
+        const R c5 = l[cy + 1][cx + 1], c6 = l[cy + 1][cx - 1], c7 = l[cy - 1][cx - 1], c8 = l[cy - 1][cx + 1];
+        lx_ = (R(1.0) / R(3.0)) * (c1 - c3) + (R(1.0) / R(12.0)) * ((c5 - c7) + (c8 - c6));
+        ly_ = (R(1.0) / R(3.0)) * (c2 - c4) + (R(1.0) / R(12.0)) * ((c5 - c7) + (c6 - c8));
+    }
+    gx = hx + lx_;
+    gy = hy + ly_;
+}
+
+template <int TX, int TY, typename R>
+__global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float* __restrict__ fin,
+                                                      float* __restrict__ fout,
+                                                      const uint8_t* __restrict__ type,
+                                                      const double* __restrict__ Cw,
+                                                      float* __restrict__ uout)
+{
+    constexpr int NT = TX * TY;
+    constexpr int HX = TX + 6, HY = TY + 6;  // geometry region (halo 3)
+    constexpr int CX = TX + 4, CY = TY + 4;  // phase-field region (halo 2)
+    constexpr int RX = TX + 2, RY = TY + 2;  // stress region (halo 1)
+    __shared__ int s_idx[HY][HX];
+    __shared__ uint8_t s_t[HY][HX];          // class bits 0-1; bit 3: ghost beyond an open side
+    __shared__ uint8_t s_par[HX];
+    __shared__ float s_ch[kNF][CY][CX], s_cl[kNF][CY][CX];  // C_k = hi + lo
+    __shared__ R s_rho[CY][CX];
+    __shared__ R s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
+
+    const Store<kStoreF32> st{fin, P.N};
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+
+    // ---- geometry of the halo-3 region ----
+    for (int j = tid; j < HX * HY; j += NT) {
+        const int hx = j % HX, hy = j / HX;
+        const int X = x0 + hx - 3, Y = y0 + hy - 3;
+        const Loc L = locate(P, X, Y);
+        uint8_t t = kSI;
+        if (L.kind != 1) {
+            t = __ldg(type + L.idx);
+            if (L.kind == 2) t |= 8;
+        }
+        s_t[hy][hx] = t;
+        s_idx[hy][hx] = L.idx;
+        if (hy == 0) s_par[hx] = parity_x(P, X);
+    }
+    __syncthreads();
+
+    // ---- densities and phase fields on the halo-2 region (Eq.16 pull, then rho_k, C_k) ----
+    // position (cx, cy) of the phase-field region; q receives the post-streaming populations
+    auto fill = [&](int cx, int cy, float q[27]) -> bool {
+        const int hx = cx + 1, hy = cy + 1;
+        const uint8_t t = s_t[hy][hx];
+        bool fluid = false;
+        if (t & 8) {
+            // ghost beyond an open side: copy of the boundary-column node (zero gradient)
+            pull_global(P, st, type, x0 + cx - 2, y0 + cy - 2, q);
+            fluid = true;
+        } else if (!(t & 2)) {
+            const bool pn = s_par[hx];
+            const int in = s_idx[hy][hx];
+            bool inl = false, outl = false;
+#pragma unroll
+            for (int a = 0; a < kQ; a++) {
+                const int sx = hx - ex(a), sy = hy - ey(a);
+                const uint8_t ts = s_t[sy][sx];
+                if (ts & 8) {
+                    if (x0 + cx - 2 == 0) inl = true; else outl = true;
+#pragma unroll
+                    for (int k = 0; k < kNF; k++) q[9 * k + a] = R(0.0);
+                } else if (ts & 2) {
+#pragma unroll
+                    for (int k = 0; k < kNF; k++) q[9 * k + a] = st.get(relabel(k, pn), opp(a), in);
+                } else {
+                    const bool ps = s_par[sx];
+                    const int is = s_idx[sy][sx];
+#pragma unroll
+                    for (int k = 0; k < kNF; k++) q[9 * k + a] = st.get(relabel(k, ps), a, is);
+                }
+            }
+            if (inl) zou_he(P, q, true);
+            if (outl) zou_he(P, q, false);
+            fluid = true;
+        }
+        if (fluid) {
+            float rh[kNF], rl[kNF];
+#pragma unroll
+            for (int k = 0; k < kNF; k++) sum9_df(q + 9 * k, rh[k], rl[k]);
+            float th, tl, sh, sl;
+            two_sum(rh[0], rh[1], th, tl);
+            two_sum(th, rh[2], sh, sl);
+            const float dl = (tl + sl) + ((rl[0] + rl[1]) + rl[2]);
+            float dh;
+            two_sum(sh, dl, dh, sl);  // rho = dh + sl
+#pragma unroll
+            for (int k = 0; k < kNF; k++) div_df(rh[k], rl[k], dh, sl, s_ch[k][cy][cx], s_cl[k][cy][cx]);
+            s_rho[cy][cx] = dh;
+        } else if ((t & 3) == kSB) {
+            // wall value from the wetting pass (FP64, split into hi + lo); rho := 1 at solid nodes
+            const int in = s_idx[hy][hx];
+            const bool pr = s_par[hx];
+#pragma unroll
+            for (int k = 0; k < kNF; k++) {
+                const double c = Cw[relabel(k, pr) * P.N + in];
+                const float h = (float)c;
+                s_ch[k][cy][cx] = h;
+                s_cl[k][cy][cx] = (float)(c - (double)h);
+            }
+            s_rho[cy][cx] = R(1.0);
+        } else {
+#pragma unroll
+            for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = s_cl[k][cy][cx] = 0.0f;
+            s_rho[cy][cx] = R(0.0);
+        }
+        return fluid;
+    };
+
+    {
+        // ring of the halo-2 region: rows 0, 1, CY-2, CY-1 and columns 0, 1, CX-2, CX-1
+        constexpr int NRING = CX * CY - TX * TY;
+        for (int j = tid; j < NRING; j += NT) {
+            int cx, cy;
+            if (j < 2 * CX) {
+                cx = j % CX;
+                cy = j / CX;
+            } else if (j < 4 * CX) {
+                cx = (j - 2 * CX) % CX;
+                cy = CY - 2 + (j - 2 * CX) / CX;
+            } else {
+                const int r = j - 4 * CX;  // 4 * TY side nodes
+                const int side = r / (2 * TY), rr = r % (2 * TY);
+                cy = 2 + rr / 2;
+                cx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
+            }
+            float q[27];
+            fill(cx, cy, q);
+        }
+    }
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int gx = x0 + lx, gy = y0 + ly;
+    float p[27];
+    const bool own_fluid = fill(lx + 2, ly + 2, p);
+    __syncthreads();
+
+    // ---- stress tensor of Eq.(10) on the halo-1 region ----
+    for (int j = tid; j < RX * RY; j += NT) {
+        const int rx = j % RX, ry = j / RX;
+        const int cx = rx + 1, cy = ry + 1, hx = rx + 2, hy = ry + 2;
+        R Txx = 0.f, Txy = 0.f, Tyy = 0.f;
+        const uint8_t t = s_t[hy][hx];
+        if ((t & 3) != kSI) {
+            const R rho = s_rho[cy][cx];
+            R c[kNF], gxk[kNF], gyk[kNF];
+#pragma unroll
+            for (int k = 0; k < kNF; k++) c[k] = s_ch[k][cy][cx];
+            if ((t & 3) == kSB) {
+                // solid node: a solid-interior neighbour takes the node's own value
+#pragma unroll
+                for (int k = 0; k < kNF; k++) {
+                    R v[kQ];
+                    const R ch = s_ch[k][cy][cx], cl = s_cl[k][cy][cx];
+                    R vl[kQ];
+#pragma unroll
+                    for (int a = 1; a < kQ; a++) {
+                        const bool si = (s_t[hy + ey(a)][hx + ex(a)] & 3) == kSI;
+                        v[a] = si ? ch : s_ch[k][cy + ey(a)][cx + ex(a)];
+                        vl[a] = si ? cl : s_cl[k][cy + ey(a)][cx + ex(a)];
+                    }
+                    gxk[k] = (R(1.0) / R(3.0)) * (v[1] - v[3]) + (R(1.0) / R(12.0)) * ((v[5] - v[7]) + (v[8] - v[6])) +
+                             ((R(1.0) / R(3.0)) * (vl[1] - vl[3]) + (R(1.0) / R(12.0)) * ((vl[5] - vl[7]) + (vl[8] - vl[6])));
+                    gyk[k] = (R(1.0) / R(3.0)) * (v[2] - v[4]) + (R(1.0) / R(12.0)) * ((v[5] - v[7]) + (v[6] - v[8])) +
+                             ((R(1.0) / R(3.0)) * (vl[2] - vl[4]) + (R(1.0) / R(12.0)) * ((vl[5] - vl[7]) + (vl[6] - vl[8])));
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < kNF; k++) grad9_df<CX>(s_ch[k], s_cl[k], cx, cy, gxk[k], gyk[k]);
+            }
+            const R rho2 = rho * rho;
+            pair_stress(R(P.sig01), c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
+            pair_stress(R(P.sig02), c[0], c[2], gxk[0], gyk[0], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+            pair_stress(R(P.sig12), c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+        }
+        s_txx[ry][rx] = Txx;
+        s_txy[ry][rx] = Txy;
+        s_tyy[ry][rx] = Tyy;
+    }
+    __syncthreads();
+
+    if (!own_fluid || gx >= P.nx || gy >= P.ny) return;
+
+    // ---- interfacial force F_s = div T (Eq.10 with Eq.12) ----
+    const int rx = lx + 1, ry = ly + 1;
+    const R Fx = (R(1.0) / R(3.0)) * (s_txx[ry][rx + 1] - s_txx[ry][rx - 1]) +
+                     (R(1.0) / R(12.0)) * (s_txx[ry + 1][rx + 1] - s_txx[ry + 1][rx - 1] -
+                                       s_txx[ry - 1][rx - 1] + s_txx[ry - 1][rx + 1]) +
+                     (R(1.0) / R(3.0)) * (s_txy[ry + 1][rx] - s_txy[ry - 1][rx]) +
+                     (R(1.0) / R(12.0)) * (s_txy[ry + 1][rx + 1] + s_txy[ry + 1][rx - 1] -
+                                       s_txy[ry - 1][rx - 1] - s_txy[ry - 1][rx + 1]);
+    const R Fy = (R(1.0) / R(3.0)) * (s_txy[ry][rx + 1] - s_txy[ry][rx - 1]) +
+                     (R(1.0) / R(12.0)) * (s_txy[ry + 1][rx + 1] - s_txy[ry + 1][rx - 1] -
+                                       s_txy[ry - 1][rx - 1] + s_txy[ry - 1][rx + 1]) +
+                     (R(1.0) / R(3.0)) * (s_tyy[ry + 1][rx] - s_tyy[ry - 1][rx]) +
+                     (R(1.0) / R(12.0)) * (s_tyy[ry + 1][rx + 1] + s_tyy[ry + 1][rx - 1] -
+                                       s_tyy[ry - 1][rx - 1] - s_tyy[ry - 1][rx + 1]);
+
+    // ---- own densities, colour gradients, normals ----
+    const int cx = lx + 2, cy = ly + 2;
+    R r0 = 0.f, r1 = 0.f, r2 = 0.f, f[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; a++) {
+        r0 += p[a];
+        r1 += p[9 + a];
+        r2 += p[18 + a];
+        f[a] = p[a] + p[9 + a] + p[18 + a];
+    }
+    const R rho = r0 + r1 + r2;
+    const R ir = R(1.0) / rho;
+    // correctly rounded fractions: a node that holds one fluid gets exactly C = 1, so the
+    // recolouring below leaves its mass unscaled (r * fl(1/r) can round below 1 every step)
+    const R c0 = r0 / rho, c1 = r1 / rho, c2 = r2 / rho;
+    R g0x, g0y, g1x, g1y, g2x, g2y;
+    grad9_df<CX>(s_ch[0], s_cl[0], cx, cy, g0x, g0y);
+    grad9_df<CX>(s_ch[1], s_cl[1], cx, cy, g1x, g1y);
+    grad9_df<CX>(s_ch[2], s_cl[2], cx, cy, g2x, g2y);
+    R n01x, n01y, n02x, n02y, n12x, n12y;
+    pair_normal(c0, c1, g0x, g0y, g1x, g1y, n01x, n01y);
+    pair_normal(c0, c2, g0x, g0y, g2x, g2y, n02x, n02y);
+    pair_normal(c1, c2, g1x, g1y, g2x, g2y, n12x, n12y);
+
+    // ---- MRT collision with forcing (Eq.1-9, 11), mixture tau of Eq.(7) ----
+    const R tau = R(0.5) + R(3.0) / (r0 * P.inv_nu0 + r1 * P.inv_nu1 + r2 * P.inv_nu2);
+    R ux, uy;
+    collide_mrt(f, rho, Fx, Fy, tau, ux, uy);
+    const int i = gy * P.nx + gx;
+    if (uout) {
+        uout[i] = ux;
+        uout[P.N + i] = uy;
+    }
+
+    // ---- recolouring, Eq.(13)-(15) ----
+    const R trip = fmin(R(35.0) * r0 * r1 * r2 * ir * ir * ir, R(1.0));
+    const R b01 = P.beta0 * (R(1.0) + trip * P.g01) * r0 * r1 * ir;
+    const R b02 = P.beta0 * (R(1.0) + trip * P.g02) * r0 * r2 * ir;
+    const R b12 = P.beta0 * (R(1.0) + trip * P.g12) * r1 * r2 * ir;
+    const R V0x = b01 * n01x + b02 * n02x, V0y = b01 * n01y + b02 * n02y;
+    const R V1x = -b01 * n01x + b12 * n12x, V1y = -b01 * n01y + b12 * n12y;
+    const R V2x = -b02 * n02x - b12 * n12x, V2y = -b02 * n02y - b12 * n12y;
+    const R Cs[3] = {c0, c1, c2};
+    const R Vx[3] = {V0x, V1x, V2x}, Vy[3] = {V0y, V1y, V2y};
+#pragma unroll
+    for (int k = 0; k < kNF; k++) {
+#pragma unroll
+        for (int a = 0; a < kQ; a++) {
+            const R v = Cs[k] * f[a] + wq(a) * (Vx[k] * (R)ex(a) + Vy[k] * (R)ey(a));
+            fout[(long long)(k * kQ + a) * P.N + i] = v;
+        }
+    }
+}
+
+constexpr int kTX = 32, kTY = 8;
+
+// ------------------------------------------------------------------------------------------
+// initial state, fields, diagnostics
+// ------------------------------------------------------------------------------------------
+// Stored populations whose pull gives f_ak(x) = w_a rho_k(x): population a of node y is
+// w_a rho_k at its destination y + e_a (or at y itself when the destination is solid).
+__global__ void k_init_f32(const Params P, const double* __restrict__ rho,
+                           const uint8_t* __restrict__ type, float* __restrict__ f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int x = i % P.nx, y = i / P.nx;
+    const bool solid = type[i] & 2;
+#pragma unroll
+    for (int a = 0; a < kQ; a++) {
+        const Loc d = locate(P, x + ex(a), y + ey(a));
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            float v = 0.0f;
+            if (!solid) {
+                if (d.kind == 1 || (d.kind == 0 && (type[d.idx] & 2)))
+                    v = wq(a) * (float)rho[(long long)k * P.N + i];
+                else if (d.kind == 0)
+                    v = wq(a) * (float)rho[(long long)relabel(k, d.par) * P.N + d.idx];
+            }
+            f[(long long)(k * kQ + a) * P.N + i] = v;
+        }
+    }
+}
+
+template <class S>
+__global__ void k_fields(const Params P, const S st, const uint8_t* __restrict__ type,
+                         float* __restrict__ rho_out)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    float r[kNF] = {0.f, 0.f, 0.f};
+    if (!(type[i] & 2)) {
+        float p[27];
+        pull_global(P, st, type, i % P.nx, i / P.nx, p);
+#pragma unroll
+        for (int k = 0; k < kNF; k++)
+#pragma unroll
+            for (int a = 0; a < kQ; a++) r[k] += p[9 * k + a];
+    }
+#pragma unroll
+    for (int k = 0; k < kNF; k++) rho_out[(long long)k * P.N + i] = r[k];
+}
+
+// post-streaming populations of every fluid node (0 at solid nodes)
+template <class S>
+__global__ void k_get_state(const Params P, const S st, const uint8_t* __restrict__ type,
+                            float* __restrict__ post)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    float p[27];
+    if (!(type[i] & 2)) {
+        pull_global(P, st, type, i % P.nx, i / P.nx, p);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 27; j++) p[j] = 0.0f;
+    }
+#pragma unroll
+    for (int j = 0; j < 27; j++) post[(long long)j * P.N + i] = p[j];
+}
+
+// stored populations whose pull reproduces the post-streaming state `post`: population a of
+// node y is post_a at its destination y + e_a, or post_opp(a) at y when that destination is solid
+__global__ void k_set_state_f32(const Params P, const double* __restrict__ post,
+                                const uint8_t* __restrict__ type, float* __restrict__ f)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.N) return;
+    const int x = i % P.nx, y = i / P.nx;
+    const bool solid = type[i] & 2;
+#pragma unroll
+    for (int a = 0; a < kQ; a++) {
+        const Loc d = locate(P, x + ex(a), y + ey(a));
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            float v = 0.0f;
+            if (!solid) {
+                if (d.kind == 1 || (d.kind == 0 && (type[d.idx] & 2)))
+                    v = (float)post[(long long)(k * kQ + opp(a)) * P.N + i];
+                else if (d.kind == 0)
+                    v = (float)post[(long long)(relabel(k, d.par) * kQ + a) * P.N + d.idx];
+            }
+            f[(long long)(k * kQ + a) * P.N + i] = v;
+        }
+    }
+}
+
+constexpr int kDiagThreads = 256;
+
+// out per block: [0..2] sum rho_k, [3] sum x rho_0, [4] sum y rho_0, [5] max|u|, [6] min rho,
+// [7] non-finite count
+template <class S>
+__global__ void __launch_bounds__(kDiagThreads) k_diag(const Params P, const S st,
+                                                       const uint8_t* __restrict__ type,
+                                                       const float* __restrict__ u,
+                                                       double* __restrict__ partials)
+{
+    double acc[8] = {0, 0, 0, 0, 0, 0, DBL_MAX, 0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P.N;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (type[i] & 2) continue;
+        const int x = (int)(i % P.nx), y = (int)(i / P.nx);
+        float p[27];
+        pull_global(P, st, type, x, y, p);
+        double r[kNF];
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            float s = 0.f;
+#pragma unroll
+            for (int a = 0; a < kQ; a++) s += p[9 * k + a];
+            r[k] = s;
+            acc[k] += s;
+            if (!isfinite(s)) acc[7] += 1.0;
+        }
+        acc[3] += x * r[0];
+        acc[4] += y * r[0];
+        const double um = sqrt((double)u[i] * u[i] + (double)u[P.N + i] * u[P.N + i]);
+        acc[5] = fmax(acc[5], um);
+        acc[6] = fmin(acc[6], r[0] + r[1] + r[2]);
+    }
+    __shared__ double sh[8][kDiagThreads];
+#pragma unroll
+    for (int j = 0; j < 8; j++) sh[j][threadIdx.x] = acc[j];
+    __syncthreads();
+    for (int s = kDiagThreads / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+#pragma unroll
+            for (int j = 0; j < 5; j++) sh[j][threadIdx.x] += sh[j][threadIdx.x + s];
+            sh[5][threadIdx.x] = fmax(sh[5][threadIdx.x], sh[5][threadIdx.x + s]);
+            sh[6][threadIdx.x] = fmin(sh[6][threadIdx.x], sh[6][threadIdx.x + s]);
+            sh[7][threadIdx.x] += sh[7][threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) partials[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void k_diag_final(const int nb, const double* __restrict__ partials, double* __restrict__ out)
+{
+    if (threadIdx.x != 0) return;
+    double acc[8] = {0, 0, 0, 0, 0, 0, DBL_MAX, 0};
+    for (int b = 0; b < nb; b++) {
+        const double* q = partials + 8 * b;
+        for (int j = 0; j < 5; j++) acc[j] += q[j];
+        acc[5] = fmax(acc[5], q[5]);
+        acc[6] = fmin(acc[6], q[6]);
+        acc[7] += q[7];
+    }
+    for (int j = 0; j < 8; j++) out[j] = acc[j];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------
+void launch_wet(const Params& P, int nw, const int* widx, const double* wnrm, const float* wang,
+                const float* f, const uint8_t* type, double* Cw, cudaStream_t s)
+{
+    if (nw <= 0) return;
+    const Store<kStoreF32> st{f, P.N};
+    k_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw);
+}
+
+void launch_wet_init(const Params& P, int nw, const int* widx, const float* f,
+                     const uint8_t* type, double* Cw, cudaStream_t s)
+{
+    if (nw <= 0) return;
+    const Store<kStoreF32> st{f, P.N};
+    k_wet_init<<<(nw + 127) / 128, 128, 0, s>>>(P, nw, widx, st, type, Cw);
+}
+
+void launch_step_f32(const Params& P, const float* fin, float* fout, const uint8_t* type,
+                     const double* Cw, float* u, cudaStream_t s)
+{
+    dim3 grid((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
+    k_step_f32<kTX, kTY, float><<<grid, dim3(kTX, kTY), 0, s>>>(P, fin, fout, type, Cw, u);
+}
+
+void launch_init_f32(const Params& P, const double* rho, const uint8_t* type, float* f,
+                     cudaStream_t s)
+{
+    k_init_f32<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, rho, type, f);
+}
+
+void launch_fields_f32(const Params& P, const float* f, const uint8_t* type, float* rho_out,
+                       cudaStream_t s)
+{
+    const Store<kStoreF32> st{f, P.N};
+    k_fields<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, st, type, rho_out);
+}
+
+void launch_get_state_f32(const Params& P, const float* f, const uint8_t* type, float* post,
+                          cudaStream_t s)
+{
+    const Store<kStoreF32> st{f, P.N};
+    k_get_state<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, st, type, post);
+}
+
+void launch_set_state_f32(const Params& P, const double* post, const uint8_t* type, float* f,
+                          cudaStream_t s)
+{
+    k_set_state_f32<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, post, type, f);
+}
+
+int diag_blocks(const Params& P)
+{
+    long long b = (P.N + kDiagThreads - 1) / kDiagThreads;
+    return (int)(b < 1216 ? b : 1216);
+}
+
+void launch_diag_f32(const Params& P, const float* f, const uint8_t* type, const float* u,
+                     double* partials, double* out, cudaStream_t s)
+{
+    const Store<kStoreF32> st{f, P.N};
+    const int nb = diag_blocks(P);
+    k_diag<<<nb, kDiagThreads, 0, s>>>(P, st, type, u, partials);
+    k_diag_final<<<1, 32, 0, s>>>(nb, partials, out);
+}
+
+const char* step_kernel_name() { return "k_step_f32"; }
+
+}  // namespace lbm3k

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of the C ABI in include/lbm3.h (argument marshalling only: every step of
+the method runs in the sm_103a kernels of liblbm3.so).
+
+The functions keep the C names (``lbm3_create``, ``lbm3_step`` ...); ``Lbm3`` wraps a handle.
+There is no CPU fallback: loading fails loudly when the library or a GPU is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liblbm3.so")
+
+LBM3_OK = 0
+LBM3_WARN_YOUNG = 1
+LBM3_ERR_INVALID = -1
+LBM3_ERR_CUDA = -2
+LBM3_ERR_OOM = -3
+LBM3_ERR_DIVERGED = -4
+LBM3_ERR_STATE = -5
+LBM3_FP32, LBM3_FP16, LBM3_BF16 = 0, 1, 2
+
+# every entry point declared in include/lbm3.h
+EXPORTS = ("lbm3_create", "lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields",
+           "lbm3_diag", "lbm3_n_wall", "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state",
+           "lbm3_set_state", "lbm3_info", "lbm3_set_stream", "lbm3_sync", "lbm3_destroy",
+           "lbm3_last_error")
+
+
+class lbm3_grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+                ("bc_x", ctypes.c_int32), ("u_in", ctypes.c_double), ("rho_out", ctypes.c_double),
+                ("precision", ctypes.c_int32)]
+
+
+class Lbm3Error(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lbm3 error {code}: {msg}")
+        self.code = code
+
+
+_D = ctypes.POINTER(ctypes.c_double)
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblbm3.so (built by ``paper_2102_04709_gb300.build``); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2102_04709_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    vp = ctypes.c_void_p
+    L.lbm3_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(lbm3_grid),
+                              ctypes.POINTER(ctypes.c_uint8), _D, _D, _D, ctypes.c_double, vp]
+    L.lbm3_create.restype = ctypes.c_int
+    L.lbm3_set_fields.argtypes = [vp, _D]
+    L.lbm3_step.argtypes = [vp, ctypes.c_int32]
+    L.lbm3_step_timed.argtypes = [vp, ctypes.c_int32, _D]
+    L.lbm3_fields.argtypes = [vp, _D, _D]
+    L.lbm3_diag.argtypes = [vp, _D]
+    L.lbm3_n_wall.argtypes = [vp]
+    L.lbm3_wall_nodes.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.c_int32]
+    L.lbm3_wall_values.argtypes = [vp, _D, ctypes.c_int32]
+    L.lbm3_get_state.argtypes = [vp, _D, _D]
+    L.lbm3_set_state.argtypes = [vp, _D, _D]
+    L.lbm3_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    L.lbm3_set_stream.argtypes = [vp, vp]
+    L.lbm3_sync.argtypes = [vp]
+    L.lbm3_destroy.argtypes = [vp]
+    L.lbm3_destroy.restype = None
+    L.lbm3_last_error.argtypes = [vp]
+    L.lbm3_last_error.restype = ctypes.c_char_p
+    for name in ("lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields", "lbm3_diag", "lbm3_n_wall",
+                 "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state", "lbm3_set_state", "lbm3_info", "lbm3_set_stream", "lbm3_sync"):
+        getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _dp(a):
+    return a.ctypes.data_as(_D)
+
+
+def _check(h, code):
+    if code < 0:
+        msg = load().lbm3_last_error(h)
+        raise Lbm3Error(code, msg.decode() if msg else "")
+    return code
+
+
+def _torch_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return ctypes.c_void_p(None)
+
+
+class Lbm3:
+    """One GPU simulation owned by a C-ABI handle."""
+
+    def __init__(self, nx, ny, periodic_y, bc_x, solid, angles, sigma, nu, beta0=0.7, u_in=0.0,
+                 rho_out=1.0, precision=LBM3_FP32, stream=None):
+        L = load()
+        self.nx, self.ny = int(nx), int(ny)
+        self.n = self.nx * self.ny
+        solid = np.ascontiguousarray(solid, dtype=np.uint8).reshape(-1)
+        angles = np.ascontiguousarray(angles, dtype=np.float64).reshape(-1)
+        if solid.size != self.n or angles.size != 3 * self.n:
+            raise ValueError("solid must be [ny, nx] and angles [ny, nx, 3]")
+        sig = np.ascontiguousarray(sigma, dtype=np.float64)
+        nus = np.ascontiguousarray(nu, dtype=np.float64)
+        g = lbm3_grid(self.nx, self.ny, int(periodic_y), int(bc_x), float(u_in), float(rho_out),
+                      int(precision))
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _torch_stream()
+        code = L.lbm3_create(ctypes.byref(h), ctypes.byref(g),
+                             solid.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), _dp(angles),
+                             _dp(sig), _dp(nus), float(beta0), st)
+        if code < 0:
+            raise Lbm3Error(code, L.lbm3_last_error(None).decode())
+        self._h = h
+        self.warning = L.lbm3_last_error(h).decode() if code > 0 else ""
+
+    @classmethod
+    def from_workload(cls, w, precision=LBM3_FP32, stream=None, init=True):
+        s = cls(w.nx, w.ny, w.periodic_y, w.bc_x, w.solid, w.angles, w.sigma, w.nu, w.beta0,
+                w.u_in, w.rho_out, precision=precision, stream=stream)
+        if init:
+            s.set_fields(w.rho)
+        return s
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().lbm3_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def set_fields(self, rho):
+        r = np.ascontiguousarray(rho, dtype=np.float64).reshape(-1)
+        if r.size != 3 * self.n:
+            raise ValueError("rho must be [3, ny, nx]")
+        _check(self._h, load().lbm3_set_fields(self._h, _dp(r)))
+
+    def step(self, n=1):
+        _check(self._h, load().lbm3_step(self._h, int(n)))
+
+    def step_timed(self, n):
+        """Advance n steps; return (ms in wetting kernels, ms in step kernels), CUDA-event timed."""
+        out = np.zeros(2)
+        _check(self._h, load().lbm3_step_timed(self._h, int(n), _dp(out)))
+        return float(out[0]), float(out[1])
+
+    def fields(self):
+        rho = np.empty(3 * self.n)
+        u = np.empty(2 * self.n)
+        _check(self._h, load().lbm3_fields(self._h, _dp(rho), _dp(u)))
+        return rho.reshape(3, self.ny, self.nx), u.reshape(2, self.ny, self.nx)
+
+    def diag(self, check=True):
+        out = np.empty(8)
+        code = load().lbm3_diag(self._h, _dp(out))
+        if check:
+            _check(self._h, code)
+        return out
+
+    def wall_nodes(self):
+        n = load().lbm3_n_wall(self._h)
+        idx = np.empty(max(n, 1), np.int32)
+        _check(self._h, load().lbm3_wall_nodes(self._h, idx.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), n))
+        return idx[:n]
+
+    def wall_values(self):
+        n = load().lbm3_n_wall(self._h)
+        c = np.empty((max(n, 1), 3))
+        _check(self._h, load().lbm3_wall_values(self._h, _dp(c), n))
+        return c[:n]
+
+    def get_state(self):
+        f = np.empty(27 * self.n)
+        c = np.empty(3 * self.n)
+        _check(self._h, load().lbm3_get_state(self._h, _dp(f), _dp(c)))
+        return f.reshape(3, 9, self.ny, self.nx), c.reshape(3, self.ny, self.nx)
+
+    def set_state(self, f_post, wall_c):
+        f = np.ascontiguousarray(f_post, dtype=np.float64).reshape(-1)
+        c = np.ascontiguousarray(wall_c, dtype=np.float64).reshape(-1)
+        if f.size != 27 * self.n or c.size != 3 * self.n:
+            raise ValueError("f_post must be [3, 9, ny, nx] and wall_c [3, ny, nx]")
+        _check(self._h, load().lbm3_set_state(self._h, _dp(f), _dp(c)))
+
+    def info(self):
+        out = np.zeros(8, np.int64)
+        _check(self._h, load().lbm3_info(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return {"n_fluid": int(out[0]), "n_wall": int(out[1]), "step_bytes": int(out[2]),
+                "step_kernels": int(out[3]), "wet_kernels": int(out[4]), "device_bytes": int(out[5])}
+
+    def set_stream(self, stream):
+        _check(self._h, load().lbm3_set_stream(self._h, stream))
+
+    def sync(self):
+        _check(self._h, load().lbm3_sync(self._h))

@@ -1,0 +1,145 @@
+"""GPU (sm_103a, through the C ABI) against the FP64 oracle, element by element on the same
+seeded inputs.  Sizes span several 32x8 tiles with ragged tails in x and y, every node class,
+every x boundary and a curved solid.  Tolerance (FP32 path vs FP64 oracle):
+|rho_k^GPU - rho_k^oracle| <= 1e-5 (relative to the pure-fluid density 1) on every node."""
+import numpy as np
+import pytest
+
+from paper_2102_04709_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL_RHO = 1e-5
+TOL_U = 1e-6
+
+
+@pytest.fixture(scope="module")
+def gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2102_04709_gb300 import build, lbm3
+    build.build()
+    lbm3.load()
+    return lbm3
+
+
+def run_both(gpu, oracle_mod, w, steps):
+    g = gpu.Lbm3.from_workload(w)
+    g.step(steps)
+    rg, ug = g.fields()
+    dg = g.diag()
+    o = oracle_mod.Oracle.from_workload(w)
+    o.step(steps)
+    ro, uo = o.fields()
+    do = o.diag()
+    return (rg, ug, dg), (ro, uo, do), g
+
+
+def assert_parity(w, G, O):
+    rg, ug, dg = G
+    ro, uo, do = O
+    err = np.abs(rg - ro).max()
+    assert err <= TOL_RHO, f"{w.name}: max |d rho_k| = {err:.3e}"
+    erru = np.abs(ug - uo).max()
+    assert erru <= TOL_U, f"{w.name}: max |d u| = {erru:.3e}"
+    # FP64 diagnostics: masses agree to the FP32 storage level
+    assert np.allclose(dg[:3], do[:3], rtol=1e-6, atol=1e-6)
+    assert dg[7] == 0
+
+
+def test_config1_janus_flat_1000_steps(gpu, oracle_mod):
+    """Janus droplet on a flat wall, 128x64, angles 90/60/120, 1000 steps (the full case)."""
+    w = W.config1()
+    G, O, _ = run_both(gpu, oracle_mod, w, 1000)
+    assert_parity(w, G, O)
+
+
+def test_ragged_janus(gpu, oracle_mod):
+    """100x44: ragged last tile in x (100 = 3*32 + 4) and y (44 = 5*8 + 4); unequal tensions."""
+    w = W.janus_flat(nx=100, ny=44, R=14.0, triple=(80.0, 60.0, 110.0), sigma=(0.012, 0.009, 0.011),
+                     nu=(0.1, 0.15, 0.2))
+    G, O, _ = run_both(gpu, oracle_mod, w, 300)
+    assert_parity(w, G, O)
+
+
+def test_cylinder_periodic_box(gpu, oracle_mod):
+    """Janus droplet on a staircased cylinder in a periodic box (curved-wall characteristic
+    lines, sigma_02 = 0.005)."""
+    w = W.janus_cylinder(nx=96, ny=90, Rs=16.0, Rj=14.0)
+    G, O, _ = run_both(gpu, oracle_mod, w, 400)
+    assert_parity(w, G, O)
+
+
+def test_capillary_modified_periodic(gpu, oracle_mod):
+    """Capillary channel with the modified periodic seam and a viscosity contrast."""
+    w = W.capillary(nx=160, ny=40, y_lo=6, y_hi=34, s0=40, Lg=40, nu=(0.1, 0.01, 0.02))
+    G, O, _ = run_both(gpu, oracle_mod, w, 400)
+    assert_parity(w, G, O)
+
+
+def test_pillars_zou_he_random_angles(gpu, oracle_mod):
+    """Compound droplet, 4 seeded pillars, Zou-He inlet/outlet, per-node random wall angles."""
+    w = W.pillars(nx=200, ny=96, count=4, r_lo=8.0, r_hi=14.0, x_lo=90.0, x_hi=180.0, gap=6.0,
+                  seed=11, drop=(50.0, 48.0), r_core=12.0, r_shell=22.0, theta_range=(60.0, 120.0),
+                  u_in=0.02)
+    G, O, _ = run_both(gpu, oracle_mod, w, 400)
+    assert_parity(w, G, O)
+
+
+def test_minimum_grid_and_zero_steps(gpu, oracle_mod):
+    """8x8 (one ragged tile), fully periodic, no walls; nsteps = 0 returns the initial state."""
+    nx = ny = 8
+    solid = np.zeros((ny, nx), np.uint8)
+    rho = np.zeros((3, ny, nx))
+    rho[0, :, :4] = 1.0
+    rho[2, :, 4:] = 1.0
+    w = W.Workload("tiny", nx, ny, 1, W.BC_PERIODIC, solid, rho, np.full((ny, nx, 3), 90.0),
+                   (0.01, 0.01, 0.01), (0.1, 0.1, 0.1))
+    g = gpu.Lbm3.from_workload(w)
+    assert g.info()["n_wall"] == 0
+    g.step(0)
+    r0, _ = g.fields()
+    assert np.abs(r0 - rho).max() < 1e-7
+    G, O, _ = run_both(gpu, oracle_mod, w, 50)
+    assert_parity(w, G, O)
+
+
+def test_single_fluid_rest_is_exact(gpu):
+    """One fluid at rest with walls and a disc stays exactly at rest on the GPU too."""
+    nx, ny = 70, 40
+    x, y = np.meshgrid(np.arange(nx), np.arange(ny))
+    solid = (((x - 30) ** 2 + (y - 20) ** 2) <= 49).astype(np.uint8)
+    solid[0] = solid[-1] = 1
+    rho = np.zeros((3, ny, nx))
+    rho[1] = 1.0 - solid
+    w = W.Workload("rest", nx, ny, 0, W.BC_PERIODIC, solid, rho,
+                   np.tile(np.array([60.0, 120.0, 60.0]), (ny, nx, 1)), (0.01,) * 3, (0.1,) * 3)
+    g = gpu.Lbm3.from_workload(w)
+    g.step(30)
+    r, u = g.fields()
+    assert np.abs(u).max() < 1e-7
+    assert np.abs(r[1] - (1.0 - solid)).max() < 1e-6
+
+
+def test_step_is_deterministic_and_resumable(gpu):
+    """Two runs of the same input give bit-identical states; 2 x 50 steps == 100 steps."""
+    w = W.janus_flat(nx=96, ny=48, R=14.0)
+    a = gpu.Lbm3.from_workload(w)
+    a.step(100)
+    b = gpu.Lbm3.from_workload(w)
+    b.step(50)
+    b.step(50)
+    ra, ua = a.fields()
+    rb, ub = b.fields()
+    assert np.array_equal(ra, rb) and np.array_equal(ua, ub)
+
+
+def test_mass_conserved_fp64_diag(gpu):
+    """Per-fluid mass of a closed problem is conserved by the FP32 step to FP32 round-off."""
+    w = W.janus_cylinder(nx=128, ny=128, Rs=20.0, Rj=18.0)
+    g = gpu.Lbm3.from_workload(w)
+    d0 = g.diag()
+    g.step(500)
+    d1 = g.diag()
+    assert np.all(np.abs(d1[:3] - d0[:3]) <= 2e-5 * np.maximum(d0[:3], 1.0))
