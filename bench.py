@@ -1,0 +1,312 @@
+#!/usr/bin/env python
+"""Throughput of the three-phase colour-gradient LBM step (arXiv:2102.04709) on one GB300.
+
+One "step" is one timestep of the whole hot path: the wetting pass over the solid boundary
+nodes (Eq.21-22) and the fused step kernel (Eq.1-16).  The workload is the compound droplet
+through 60 seeded pillars on a 4096 x 2048 D2Q9 grid (Section III.D), FP32 populations;
+inputs (2 x 0.9 GB of populations) are larger than L2, so no flush is needed.
+
+Prints ONE JSON line (rank 0):  value = whole-job MLUPS (grid nodes x steps / s / 1e6).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle (the only reference this paper has) on the box's
+host cores, one 128 x 128 window of the same workload per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+FALLBACK_HBM_GBS = 6800.0
+WORKLOAD = "pillars_4096x2048_theta90"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--theta", type=float, default=90.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("timestamp", "clocks.sm", "clocks.max.sm", "power.draw",
+              "clocks_event_reasons.active", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.samples = []
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(device_index), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == len(self.FIELDS):
+                self.samples.append((time.time(), parts))
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sel = [s for (t, s) in self.samples if t0 <= t <= t1]
+        window = "timed region"
+        if not sel:
+            sel = [s for (_, s) in self.samples[-5:]]
+            window = "nearest samples (timed region shorter than the sampling period)"
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(s[1]) for s in sel if num(s[1]) is not None]
+        smax = [num(s[2]) for s in sel if num(s[2]) is not None]
+        pw = [num(s[3]) for s in sel if num(s[3]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for s in sel for j in range(4) if s[5 + j].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w": statistics.median(pw) if pw else None,
+                "reasons": reasons, "samples": len(sel), "window": window}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if key in d and isinstance(d[key], (int, float)):
+                return float(d[key]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except (OSError, ValueError):
+        pass
+    return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
+
+
+def profiled_traffic(n_fluid):
+    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken on the
+    current kernel source (hash match), scaled to this workload's fluid nodes."""
+    src = os.path.join(ROOT, "paper_2102_04709_gb300", "csrc", "lbm3_step.cu")
+    path = os.path.join(ROOT, "profiles", "k_step_f32_traffic.txt")
+    try:
+        d = {}
+        with open(path) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    d[k.strip()] = v.strip()
+        with open(src, "rb") as fh:
+            h = hashlib.sha256(fh.read()).hexdigest()[:16]
+        if d.get("source_sha256_16") != h:
+            return None
+        return float(d["dram_bytes_per_fluid_node"]) * n_fluid
+    except (OSError, ValueError, KeyError):
+        return None
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle timing
+# ------------------------------------------------------------------------------------------
+def oracle_window(w, x0, y0, size):
+    """A size x size window of workload w, periodic on both sides (same per-node work)."""
+    from paper_2102_04709_gb300 import workloads as W
+    sl = (slice(y0, y0 + size), slice(x0, x0 + size))
+    return W.Workload(f"{w.name}_window{size}", size, size, 1, W.BC_PERIODIC,
+                      w.solid[sl].copy(), w.rho[:, sl[0], sl[1]].copy(), w.angles[sl].copy(),
+                      w.sigma, w.nu, w.beta0)
+
+
+def cpu_baseline(w, steps=2):
+    """The FP64 oracle on `steps` full timesteps of the whole workload, one host core."""
+    from oracle import oracle as ora
+    o = ora.Oracle.from_workload(w)
+    t = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t
+    return {"value": w.n * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{steps} full timesteps of {w.name} ({w.nx}x{w.ny}) by the FP64 oracle, "
+                      f"{dt:.1f} s, single-threaded C"}
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import oracle as ora
+    from paper_2102_04709_gb300 import workloads as W
+    ora.build()
+    w = W.config4(args.theta)
+    win = oracle_window(w, 336, 960, 128)
+    o = ora.Oracle.from_workload(win)
+    o.step(args.warmup)
+    t = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t
+    v = win.n * args.steps / dt / 1e6
+    line = {"impl": "reference", "metric": "MLUPS", "value": v, "unit": "MLUPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": "128x128 window of the workload per step",
+                       "storage": "fp64 (oracle)"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
+                             "sample": "one timestep of a 128x128 window of the pillar workload "
+                                       "per step, FP64 oracle, single-threaded C"},
+            "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# GPU arm
+# ------------------------------------------------------------------------------------------
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a GPU")
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2102_04709_gb300 import build, lbm3
+    from paper_2102_04709_gb300 import workloads as W
+    build.build()
+    lbm3.load()
+
+    w = W.config4(args.theta)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sim = lbm3.Lbm3.from_workload(w, stream=stream.cuda_stream)
+    info = sim.info()
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    sim.step(args.warmup)
+    barrier()
+    sampler = ClockSampler(local)
+    time.sleep(0.5)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0 = time.time()
+    e0.record(stream)
+    ms_wet, ms_step = sim.step_timed(args.steps)
+    e1.record(stream)
+    barrier()
+    t1 = time.time()
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    d = sim.diag(check=False)
+
+    # end to end through the C ABI with host buffers: H2D of the initial densities, the steps,
+    # D2H of the densities and velocity
+    e2e = None
+    if not args.no_e2e:
+        rho_host = torch.from_numpy(np.ascontiguousarray(w.rho)).pin_memory().numpy()
+        barrier()
+        ta = time.perf_counter()
+        sim.set_fields(rho_host)
+        sim.step(args.steps)
+        rho_out, u_out = sim.fields()
+        barrier()
+        tb = time.perf_counter()
+        e2e = {"value": w.n * args.steps * ws / (tb - ta) / 1e6, "unit": "MLUPS",
+               "h2d_bytes_per_step": int(math.ceil(rho_host.nbytes / args.steps)),
+               "d2h_bytes_per_step": int(math.ceil((rho_out.nbytes + u_out.nbytes) / args.steps))}
+
+    if rank != 0:
+        return
+    value = w.n * args.steps * ws / (ms * 1e-3) / 1e6
+    bytes_launch = info["step_bytes"]
+    achieved = bytes_launch / (ms_step / args.steps * 1e-3) / 1e9
+    peak, peak_src = measured_peak()
+    traffic = profiled_traffic(info["n_fluid"])
+    clocks = sampler.summary(t0, t1)
+    line = {
+        "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "fluid_nodes": info["n_fluid"],
+                   "wall_nodes": info["n_wall"], "storage": "fp32",
+                   "mflups": info["n_fluid"] * args.steps * ws / (ms * 1e-3) / 1e6,
+                   "l2": "populations 2 x 0.91 GB > 129 MB L2: no flush between steps",
+                   "replicas": ws, "ms_wet_per_step": ms_wet / args.steps,
+                   "ms_step_kernel_per_step": ms_step / args.steps,
+                   "max_u": float(d[5])},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "k_step_f32",
+                     "algorithmic_bytes_per_launch": bytes_launch},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clocks,
+        "e2e": e2e,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -196,9 +196,16 @@ def pillars(nx=4096, ny=2048, count=60, r_lo=40.0, r_hi=80.0, x_lo=900.0, x_hi=3
     x, y = _grid(nx, ny)
     solid = np.zeros((ny, nx), np.uint8)
     for (cx, cy, r) in pl:
-        dy = np.abs(y - cy)
+        # bounding box of the disc (rows wrap periodically)
+        x0, x1 = max(0, int(math.floor(cx - r)) - 1), min(nx, int(math.ceil(cx + r)) + 2)
+        rows = np.arange(int(math.floor(cy - r)) - 1, int(math.ceil(cy + r)) + 2) % ny
+        xs = np.arange(x0, x1, dtype=np.float64)
+        dy = np.abs(rows.astype(np.float64)[:, None] - cy)
         dy = np.minimum(dy, ny - dy)
-        solid[((x - cx) ** 2 + dy ** 2) <= r * r] = 1
+        hit = ((xs[None, :] - cx) ** 2 + dy ** 2) <= r * r
+        sub = solid[rows, x0:x1]
+        sub[hit] = 1
+        solid[rows, x0:x1] = sub
     dx, dy = x - drop[0], y - drop[1]
     d2 = dx * dx + dy * dy
     labels = np.full((ny, nx), 2, np.int64)
