@@ -55,7 +55,7 @@ typedef struct lbm3 lbm3;
 #define LBM3_BF16 2              /* per fluid: FP32 rho_k + 8 BF16 offsets f_ak - w_a rho_k */
 
 typedef struct lbm3_grid {
-    int32_t nx, ny;        /* grid size, nx >= 8, ny >= 8, nx * ny < 2^31 */
+    int32_t nx, ny;        /* grid size, nx >= 8, ny >= 8, 27 * nx * ny < 2^31 */
     int32_t periodic_y;    /* 1: periodic in y; 0: rows 0 and ny-1 must be solid */
     int32_t bc_x;          /* LBM3_BC_* */
     double u_in;           /* inlet velocity for LBM3_BC_ZOUHE (|u_in| < 0.3) */

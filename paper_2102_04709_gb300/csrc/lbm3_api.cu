@@ -116,8 +116,9 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     *out = nullptr;
     if (!g || !solid || !angles || !sigma || !nu)
         return fail(nullptr, LBM3_ERR_INVALID, "NULL argument");
-    if (g->nx < 8 || g->ny < 8 || (long long)g->nx * g->ny >= (1LL << 31))
-        return fail(nullptr, LBM3_ERR_INVALID, "grid must be at least 8x8 and below 2^31 nodes");
+    // the step kernel addresses the 27 population planes with 32-bit offsets
+    if (g->nx < 8 || g->ny < 8 || 27LL * g->nx * g->ny >= (1LL << 31))
+        return fail(nullptr, LBM3_ERR_INVALID, "grid must be at least 8x8 with 27 * nx * ny < 2^31");
     if (g->bc_x < 0 || g->bc_x > 3) return fail(nullptr, LBM3_ERR_INVALID, "bad bc_x");
     if (g->precision != LBM3_FP32)
         return fail(nullptr, LBM3_ERR_INVALID, "precision not built in this library");

@@ -25,6 +25,41 @@ constexpr double kRayEps = 1e-6;   // crossings this close to a node are node hi
 constexpr double kPhiSnap = 1e-6;  // |90 - theta_k| below this (deg): both lines along n_s
 constexpr double kRayTmax = 16.0;  // the characteristic-line search stops beyond this length
 
+// ---- compensated (float-float) phase fields ----
+// Near a contact line the colour gradient of a well-mixed node can be 1e-3 while C ~ 0.5, so
+// the normal n_kl = G_kl/|G_kl| of Eq.(13) and the stress of Eq.(10) need C to more bits than a
+// float holds.  C_k is kept as an unevaluated pair hi + lo: the populations are summed with
+// error-free transformations (Knuth's TwoSum), the division carries its exact FMA residual,
+// and the Eq.(12) stencil is applied to hi and lo separately (hi differences of close values
+// are exact).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// sum of the 9 populations q[0..8] as hi + lo
+__device__ __forceinline__ void sum9_df(const float* q, float& hi, float& lo)
+{
+    float s = q[0], e = 0.0f;
+#pragma unroll
+    for (int a = 1; a < kQ; a++) {
+        float t;
+        two_sum(s, q[a], s, t);
+        e += t;
+    }
+    two_sum(s, e, hi, lo);
+}
+
+// (nh + nl) / (dh + dl) as hi + lo
+__device__ __forceinline__ void div_df(float nh, float nl, float dh, float dl, float& qh, float& ql)
+{
+    qh = nh / dh;
+    const float r = fmaf(-qh, dh, nh) + nl - qh * dl;
+    ql = r / dh;
+}
+
 // ------------------------------------------------------------------------------------------
 // wetting: characteristic lines (Section II.B)
 // ------------------------------------------------------------------------------------------
@@ -37,23 +72,27 @@ __device__ __forceinline__ bool node_is_fluid(const Params& P, const uint8_t* __
     return !(__ldg(type + L.idx) & 2);
 }
 
-// C_k at the fluid node at unwrapped (X, Y), in the frame of the home domain (FP64 sums of the
-// stored populations, so that a node holding one fluid gives exactly 0 or 1)
+// C_k at the fluid node at unwrapped (X, Y), in the frame of the home domain.  The populations
+// are summed with error-free transformations and divided with the FMA residual, so the value is
+// the FP64 fraction of the stored FP32 populations (a node holding one fluid gives exactly 0 or 1).
 template <class S>
 __device__ double node_C(const Params& P, const S& st, const uint8_t* __restrict__ type, int X,
                          int Y, int k)
 {
-    float p[27];
-    pull_global(P, st, type, X, Y, p);
-    double r[kNF];
+    float q[27];
+    pull_global(P, st, type, X, Y, q);
+    float rh[kNF], rl[kNF];
 #pragma unroll
-    for (int j = 0; j < kNF; j++) {
-        double s = 0.0;
-#pragma unroll
-        for (int a = 0; a < kQ; a++) s += (double)p[9 * j + a];
-        r[j] = s;
-    }
-    return r[k] / (r[0] + r[1] + r[2]);
+    for (int j = 0; j < kNF; j++) sum9_df(q + 9 * j, rh[j], rl[j]);
+    float th, tl, sh, sl, dh;
+    two_sum(rh[0], rh[1], th, tl);
+    two_sum(th, rh[2], sh, sl);
+    const float dl = (tl + sl) + ((rl[0] + rl[1]) + rl[2]);
+    two_sum(sh, dl, dh, sl);
+    const float nh = k == 0 ? rh[0] : (k == 1 ? rh[1] : rh[2]);
+    const float nl = k == 0 ? rl[0] : (k == 1 ? rl[1] : rl[2]);
+    const double num = (double)nh + (double)nl, den = (double)dh + (double)sl;
+    return num / den;
 }
 
 template <class S>
@@ -72,12 +111,19 @@ __device__ double neighbour_mean(const Params& P, const S& st, const uint8_t* __
     return ws > 0.0 ? s / ws : 0.0;
 }
 
-// March from the C_SB node (px, py) along direction (dx, dy); C_D at the first grid-line
-// crossing whose bracketing nodes are both fluid (node hits use the node itself).
+// Where a characteristic line from the C_SB node (px, py) along (dx, dy) picks up its value:
+// kind 0 = no valid crossing within the search length, 1 = a node hit (node a),
+// 2 = a crossing between the fluid nodes a and b at fraction fr from a.
+struct Crossing {
+    int kind, ax, ay, bx, by;
+    double fr;
+};
+
 template <class S>
-__device__ bool characteristic_line(const Params& P, const S& st, const uint8_t* __restrict__ type,
-                                    int px, int py, double dx, double dy, int k, double* CD)
+__device__ Crossing characteristic_line(const Params& P, const uint8_t* __restrict__ type, int px,
+                                        int py, double dx, double dy)
 {
+    Crossing c{0, 0, 0, 0, 0, 0.0};
     const int sx = dx > 0.0 ? 1 : -1;
     const int sy = dy > 0.0 ? 1 : -1;
     int X = px + sx;  // next vertical grid line
@@ -87,13 +133,15 @@ __device__ bool characteristic_line(const Params& P, const S& st, const uint8_t*
 #pragma unroll 1
     for (int it = 0; it < 64; it++) {
         const double t = fmin(tX, tY);
-        if (!(t <= kRayTmax)) return false;
+        if (!(t <= kRayTmax)) return c;
         const bool onX = (tX - t) <= kRayEps;
         const bool onY = (tY - t) <= kRayEps;
         if (onX && onY) {
             if (node_is_fluid<S>(P, type, X, Y)) {
-                *CD = node_C(P, st, type, X, Y, k);
-                return true;
+                c.kind = 1;
+                c.ax = X;
+                c.ay = Y;
+                return c;
             }
         } else {
             // position along the crossed line, without fused multiply-add so that the node-hit
@@ -102,21 +150,25 @@ __device__ bool characteristic_line(const Params& P, const S& st, const uint8_t*
                                  : __dadd_rn((double)px, __dmul_rn(t, dx));
             const double sr = floor(s + 0.5);
             if (fabs(s - sr) < kRayEps) {
-                const int nx_ = onX ? X : (int)sr, ny_ = onX ? (int)sr : Y;
-                if (node_is_fluid<S>(P, type, nx_, ny_)) {
-                    *CD = node_C(P, st, type, nx_, ny_, k);
-                    return true;
+                const int hx = onX ? X : (int)sr, hy = onX ? (int)sr : Y;
+                if (node_is_fluid<S>(P, type, hx, hy)) {
+                    c.kind = 1;
+                    c.ax = hx;
+                    c.ay = hy;
+                    return c;
                 }
             } else {
                 const int s0 = (int)floor(s);
-                const double fr = s - (double)s0;
                 const int ax = onX ? X : s0, ay = onX ? s0 : Y;
                 const int bx = onX ? X : s0 + 1, by = onX ? s0 + 1 : Y;
                 if (node_is_fluid<S>(P, type, ax, ay) && node_is_fluid<S>(P, type, bx, by)) {
-                    const double ca = node_C(P, st, type, ax, ay, k);
-                    const double cb = node_C(P, st, type, bx, by, k);
-                    *CD = ca + fr * (cb - ca);
-                    return true;
+                    c.kind = 2;
+                    c.ax = ax;
+                    c.ay = ay;
+                    c.bx = bx;
+                    c.by = by;
+                    c.fr = s - (double)s0;
+                    return c;
                 }
             }
         }
@@ -129,24 +181,7 @@ __device__ bool characteristic_line(const Params& P, const S& st, const uint8_t*
             tY = (double)(Y - py) / dy;
         }
     }
-    return false;
-}
-
-template <class S>
-__device__ double wet_fluid(const Params& P, const S& st, const uint8_t* __restrict__ type, int px,
-                            int py, double nx_, double ny_, double theta, int k)
-{
-    const double dev = fabs(90.0 - theta);
-    const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
-    double sn, cs;
-    sincos(phi, &sn, &cs);
-    // the two lines make the angle phi with n_s, one on each side (tangent (-n_y, n_x))
-    const double d1x = cs * nx_ - sn * ny_, d1y = cs * ny_ + sn * nx_;
-    const double d2x = cs * nx_ + sn * ny_, d2y = cs * ny_ - sn * nx_;
-    double c1, c2;
-    if (!characteristic_line(P, st, type, px, py, d1x, d1y, k, &c1)) c1 = neighbour_mean(P, st, type, px, py, k);
-    if (!characteristic_line(P, st, type, px, py, d2x, d2y, k, &c2)) c2 = neighbour_mean(P, st, type, px, py, k);
-    return theta <= 90.0 ? fmax(c1, c2) : fmin(c1, c2);  // Eq.(22)
+    return c;
 }
 
 // Eq.(21) for one fluid k with the other two fractions w_m, w_l and angles t_m, t_l: the paper's
@@ -157,33 +192,60 @@ __device__ __forceinline__ double local_angle(double wm, double tm, double wl, d
     return wm + wl < 1e-12 ? 0.5 * (tm + tl) : tl + wm / (wm + wl) * (tm - tl);
 }
 
+// Four lanes per C_SB node: lane = 2 * k + side, for the wetted fluids k = 0, 1 and the two
+// characteristic lines (rotated by +phi and -phi from n_s).  Each lane marches its line over the
+// class bytes, then gathers C at the one or two nodes it found; Eq.(22) combines the two lines
+// of a fluid with a shuffle, and lane 0 writes the wall values.
 template <class S>
 __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const int* __restrict__ widx,
                                              const double* __restrict__ wnrm,
                                              const float* __restrict__ wang, const S st,
                                              const uint8_t* __restrict__ type, double* __restrict__ Cw)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= nw) return;
-    const int i = widx[w];
-    const int px = i % P.nx, py = i / P.nx;
-    // Eq.(21) with the wall values of the previous step
-    const double Cr = Cw[i], Cg = Cw[P.N + i], Cb = Cw[2 * P.N + i];
-    const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
-    const double t_rb = 180.0 - t_br, t_gr = 180.0 - t_rg;
-    const double th_r = local_angle(Cb, t_rb, Cg, t_rg);
-    const double th_g = local_angle(Cb, t_gb, Cr, t_gr);
-    const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
-    double cr = wet_fluid(P, st, type, px, py, nx_, ny_, th_r, 0);
-    double cg = wet_fluid(P, st, type, px, py, nx_, ny_, th_g, 1);
-    const double s = cr + cg;
-    if (s > 1.0) {
-        cr /= s;
-        cg /= s;
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = g >> 2;
+    const int k = (g >> 1) & 1, side = g & 1;
+    const bool valid = w < nw;
+    int i = 0, px = 0, py = 0;
+    double th = 90.0;
+    Crossing cr{0, 0, 0, 0, 0, 0.0};
+    if (valid) {
+        i = widx[w];
+        px = i % P.nx;
+        py = i / P.nx;
+        // Eq.(21) with the wall values of the previous step
+        const double Cr = Cw[i], Cg = Cw[P.N + i], Cb = Cw[2 * P.N + i];
+        const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
+        th = k == 0 ? local_angle(Cb, 180.0 - t_br, Cg, t_rg) : local_angle(Cb, t_gb, Cr, 180.0 - t_rg);
+        const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
+        const double dev = fabs(90.0 - th);
+        const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
+        double sn, cs;
+        sincos(phi, &sn, &cs);
+        if (side) sn = -sn;
+        // the line makes the angle phi with n_s (tangent (-n_y, n_x))
+        cr = characteristic_line<S>(P, type, px, py, cs * nx_ - sn * ny_, cs * ny_ + sn * nx_);
     }
-    Cw[i] = cr;
-    Cw[P.N + i] = cg;
-    Cw[2 * P.N + i] = fmax(0.0, 1.0 - cr - cg);
+    double ca = 0.0, cb = 0.0;
+    if (valid && cr.kind >= 1) ca = node_C(P, st, type, cr.ax, cr.ay, k);
+    if (valid && cr.kind == 2) cb = node_C(P, st, type, cr.bx, cr.by, k);
+    if (valid && cr.kind == 0) ca = neighbour_mean(P, st, type, px, py, k);
+    const double cd = cr.kind == 2 ? ca + cr.fr * (cb - ca) : ca;
+    // Eq.(22): max of the two lines for theta_k <= 90 deg, min otherwise
+    const double other = __shfl_xor_sync(0xffffffffu, cd, 1);
+    const double cp = th <= 90.0 ? fmax(cd, other) : fmin(cd, other);
+    const double cg = __shfl_xor_sync(0xffffffffu, cp, 2);
+    if (valid && (g & 3) == 0) {
+        double c0 = cp, c1 = cg;
+        const double s = c0 + c1;
+        if (s > 1.0) {
+            c0 /= s;
+            c1 /= s;
+        }
+        Cw[i] = c0;
+        Cw[P.N + i] = c1;
+        Cw[2 * P.N + i] = fmax(0.0, 1.0 - c0 - c1);
+    }
 }
 
 // initial wall values: w-weighted mean of the fluid neighbours, for each fluid
@@ -305,41 +367,6 @@ __device__ __forceinline__ void pair_normal(R ck, R cl, R gkx, R gky, R glx, R g
     }
 }
 
-// ---- compensated (float-float) phase fields ----
-// Near a contact line the colour gradient of a well-mixed node can be 1e-3 while C ~ 0.5, so
-// the normal n_kl = G_kl/|G_kl| of Eq.(13) and the stress of Eq.(10) need C to more bits than a
-// float holds.  C_k is kept as an unevaluated pair hi + lo: the populations are summed with
-// error-free transformations (Knuth's TwoSum), the division carries its exact FMA residual,
-// and the Eq.(12) stencil is applied to hi and lo separately (hi differences of close values
-// are exact).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = a + b;
-    const float bb = s - a;
-    e = (a - (s - bb)) + (b - bb);
-}
-
-// sum of the 9 populations q[0..8] as hi + lo
-__device__ __forceinline__ void sum9_df(const float* q, float& hi, float& lo)
-{
-    float s = q[0], e = 0.0f;
-#pragma unroll
-    for (int a = 1; a < kQ; a++) {
-        float t;
-        two_sum(s, q[a], s, t);
-        e += t;
-    }
-    two_sum(s, e, hi, lo);
-}
-
-// (nh + nl) / (dh + dl) as hi + lo
-__device__ __forceinline__ void div_df(float nh, float nl, float dh, float dl, float& qh, float& ql)
-{
-    qh = nh / dh;
-    const float r = fmaf(-qh, dh, nh) + nl - qh * dl;
-    ql = r / dh;
-}
-
 // Eq.(12) derivative weights: d_x psi = (psi_1 - psi_3)/3 + (psi_5 - psi_6 - psi_7 + psi_8)/12
 template <int W, typename R>
 __device__ __forceinline__ void grad9_df(const float (*h)[W], const float (*l)[W], int cx, int cy,
@@ -362,7 +389,28 @@ __device__ __forceinline__ void grad9_df(const float (*h)[W], const float (*l)[W
     gy = hy + ly_;
 }
 
-template <int TX, int TY, typename R>
+// Eq.(12) derivative of a float field held in shared memory
+template <int W>
+__device__ __forceinline__ void grad9_f(const float (*c)[W], int cx, int cy, float& gx, float& gy)
+{
+    const float c1 = c[cy][cx + 1], c3 = c[cy][cx - 1], c2 = c[cy + 1][cx], c4 = c[cy - 1][cx];
+    const float c5 = c[cy + 1][cx + 1], c6 = c[cy + 1][cx - 1], c7 = c[cy - 1][cx - 1], c8 = c[cy - 1][cx + 1];
+    gx = (1.0f / 3.0f) * (c1 - c3) + (1.0f / 12.0f) * ((c5 - c7) + (c8 - c6));
+    gy = (1.0f / 3.0f) * (c2 - c4) + (1.0f / 12.0f) * ((c5 - c7) + (c6 - c8));
+}
+
+// One CTA per TX x TY tile of interior nodes.
+//   phase 0: class bytes (and, for tiles touching the domain edge, storage indices and seam
+//            parities) of the halo-3 region into shared memory
+//   phase 1: pull-streaming of every fluid node of the halo-2 region, densities rho_k and the
+//            phase fields C_k; the tile's own nodes keep their 9 post-streaming totals and 3
+//            densities in registers
+//   phase 2: the Eq.(10) stress tensor on the halo-1 region
+//   phase 3: force, velocity, MRT collision with forcing, recolouring, 27 stores per node
+// Tiles whose halo-3 region stays inside the domain take arithmetic source indices and skip the
+// bounce-back tests at C_FI nodes; only tiles whose halo-2 region holds a C_SB node carry the
+// float-float phase fields (the wetting feedback at contact lines needs them, see above).
+template <int TX, int TY>
 __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float* __restrict__ fin,
                                                       float* __restrict__ fout,
                                                       const uint8_t* __restrict__ type,
@@ -373,70 +421,104 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
     constexpr int HX = TX + 6, HY = TY + 6;  // geometry region (halo 3)
     constexpr int CX = TX + 4, CY = TY + 4;  // phase-field region (halo 2)
     constexpr int RX = TX + 2, RY = TY + 2;  // stress region (halo 1)
-    __shared__ int s_idx[HY][HX];
+    __shared__ int s_idx[HY][HX];            // storage index (tiles at the domain edge only)
     __shared__ uint8_t s_t[HY][HX];          // class bits 0-1; bit 3: ghost beyond an open side
     __shared__ uint8_t s_par[HX];
-    __shared__ float s_ch[kNF][CY][CX], s_cl[kNF][CY][CX];  // C_k = hi + lo
-    __shared__ R s_rho[CY][CX];
-    __shared__ R s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
+    __shared__ float s_ch[kNF][CY][CX], s_cl[kNF][CY][CX];  // C_k = hi (+ lo in wall tiles)
+    __shared__ float s_rho[CY][CX];
+    __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
 
-    const Store<kStoreF32> st{fin, P.N};
     const int tid = threadIdx.x + TX * threadIdx.y;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nx = P.nx;
+    const int N = (int)P.N;
+    // halo-3 region inside the domain: no wrap, no ghost, no seam
+    const bool inner = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= P.nx && y0 + TY + 3 <= P.ny;
 
-    // ---- geometry of the halo-3 region ----
-    for (int j = tid; j < HX * HY; j += NT) {
-        const int hx = j % HX, hy = j / HX;
-        const int X = x0 + hx - 3, Y = y0 + hy - 3;
-        const Loc L = locate(P, X, Y);
-        uint8_t t = kSI;
-        if (L.kind != 1) {
-            t = __ldg(type + L.idx);
-            if (L.kind == 2) t |= 8;
+    // ---- phase 0: geometry of the halo-3 region ----
+    int wall = 0;
+    if (inner) {
+        for (int j = tid; j < HX * HY; j += NT) {
+            const int hx = j % HX, hy = j / HX;
+            const uint8_t t = __ldg(type + (y0 + hy - 3) * nx + (x0 + hx - 3));
+            s_t[hy][hx] = t;
+            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY) wall = 1;
         }
-        s_t[hy][hx] = t;
-        s_idx[hy][hx] = L.idx;
-        if (hy == 0) s_par[hx] = parity_x(P, X);
+    } else {
+        for (int j = tid; j < HX * HY; j += NT) {
+            const int hx = j % HX, hy = j / HX;
+            const int X = x0 + hx - 3, Y = y0 + hy - 3;
+            const Loc L = locate(P, X, Y);
+            uint8_t t = kSI;
+            if (L.kind != 1) {
+                t = __ldg(type + L.idx);
+                if (L.kind == 2) t |= 8;
+            }
+            s_t[hy][hx] = t;
+            s_idx[hy][hx] = L.idx;
+            if (hy == 0) s_par[hx] = parity_x(P, X);
+            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY) wall = 1;
+        }
     }
-    __syncthreads();
+    const bool df = __syncthreads_or(wall);
 
-    // ---- densities and phase fields on the halo-2 region (Eq.16 pull, then rho_k, C_k) ----
-    // position (cx, cy) of the phase-field region; q receives the post-streaming populations
-    auto fill = [&](int cx, int cy, float q[27]) -> bool {
-        const int hx = cx + 1, hy = cy + 1;
+    // ---- phase 1: post-streaming populations, densities and phase fields ----
+    // pull of the fluid node at (hx, hy) of the geometry region into q[27]
+    auto pull = [&](int hx, int hy, float q[27]) {
         const uint8_t t = s_t[hy][hx];
-        bool fluid = false;
-        if (t & 8) {
-            // ghost beyond an open side: copy of the boundary-column node (zero gradient)
-            pull_global(P, st, type, x0 + cx - 2, y0 + cy - 2, q);
-            fluid = true;
-        } else if (!(t & 2)) {
-            const bool pn = s_par[hx];
-            const int in = s_idx[hy][hx];
-            bool inl = false, outl = false;
+        if (inner) {
+            const int i = (y0 + hy - 3) * nx + (x0 + hx - 3);
+            if ((t & 3) == kFI) {
 #pragma unroll
-            for (int a = 0; a < kQ; a++) {
-                const int sx = hx - ex(a), sy = hy - ey(a);
-                const uint8_t ts = s_t[sy][sx];
-                if (ts & 8) {
-                    if (x0 + cx - 2 == 0) inl = true; else outl = true;
+                for (int a = 0; a < kQ; a++)
 #pragma unroll
-                    for (int k = 0; k < kNF; k++) q[9 * k + a] = R(0.0);
-                } else if (ts & 2) {
+                    for (int k = 0; k < kNF; k++)
+                        q[9 * k + a] = __ldg(fin + (k * kQ + a) * N + (i - ex(a) - ey(a) * nx));
+            } else {
 #pragma unroll
-                    for (int k = 0; k < kNF; k++) q[9 * k + a] = st.get(relabel(k, pn), opp(a), in);
-                } else {
-                    const bool ps = s_par[sx];
-                    const int is = s_idx[sy][sx];
+                for (int a = 0; a < kQ; a++) {
+                    const bool bb = s_t[hy - ey(a)][hx - ex(a)] & 2;
+                    const int off = bb ? opp(a) * N + i : a * N + (i - ex(a) - ey(a) * nx);
 #pragma unroll
-                    for (int k = 0; k < kNF; k++) q[9 * k + a] = st.get(relabel(k, ps), a, is);
+                    for (int k = 0; k < kNF; k++) q[9 * k + a] = __ldg(fin + k * kQ * N + off);
                 }
             }
-            if (inl) zou_he(P, q, true);
-            if (outl) zou_he(P, q, false);
-            fluid = true;
+            return;
         }
-        if (fluid) {
+        if (t & 8) {
+            // ghost beyond an open side: copy of the boundary-column node (zero gradient)
+            const Store<kStoreF32> st{fin, P.N};
+            pull_global(P, st, type, x0 + hx - 3, y0 + hy - 3, q);
+            return;
+        }
+        const Store<kStoreF32> st{fin, P.N};
+        const bool pn = s_par[hx];
+        const int in = s_idx[hy][hx];
+        bool inl = false, outl = false;
+#pragma unroll
+        for (int a = 0; a < kQ; a++) {
+            const int sx = hx - ex(a), sy = hy - ey(a);
+            const uint8_t ts = s_t[sy][sx];
+            if (ts & 8) {
+                if (x0 + hx - 3 == 0) inl = true; else outl = true;
+#pragma unroll
+                for (int k = 0; k < kNF; k++) q[9 * k + a] = 0.0f;
+            } else if (ts & 2) {
+#pragma unroll
+                for (int k = 0; k < kNF; k++) q[9 * k + a] = st.get(relabel(k, pn), opp(a), in);
+            } else {
+                const bool ps = s_par[sx];
+                const int is = s_idx[sy][sx];
+#pragma unroll
+                for (int k = 0; k < kNF; k++) q[9 * k + a] = st.get(relabel(k, ps), a, is);
+            }
+        }
+        if (inl) zou_he(P, q, true);
+        if (outl) zou_he(P, q, false);
+    };
+    // densities / phase fields of the position (cx, cy) of the phase-field region from q
+    auto store_phase = [&](int cx, int cy, const float q[27]) {
+        if (df) {
             float rh[kNF], rl[kNF];
 #pragma unroll
             for (int k = 0; k < kNF; k++) sum9_df(q + 9 * k, rh[k], rl[k]);
@@ -449,24 +531,46 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
 #pragma unroll
             for (int k = 0; k < kNF; k++) div_df(rh[k], rl[k], dh, sl, s_ch[k][cy][cx], s_cl[k][cy][cx]);
             s_rho[cy][cx] = dh;
-        } else if ((t & 3) == kSB) {
-            // wall value from the wetting pass (FP64, split into hi + lo); rho := 1 at solid nodes
-            const int in = s_idx[hy][hx];
-            const bool pr = s_par[hx];
+        } else {
+            float r[kNF];
 #pragma unroll
             for (int k = 0; k < kNF; k++) {
-                const double c = Cw[relabel(k, pr) * P.N + in];
+                const float* qk = q + 9 * k;
+                r[k] = ((qk[0] + (qk[1] + qk[3])) + (qk[2] + qk[4])) + ((qk[5] + qk[7]) + (qk[6] + qk[8]));
+            }
+            const float rho = (r[0] + r[1]) + r[2];
+            const float ir = 1.0f / rho;
+#pragma unroll
+            for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = r[k] * ir;
+            s_rho[cy][cx] = rho;
+        }
+    };
+    auto fill = [&](int cx, int cy, float q[27]) -> bool {
+        const int hx = cx + 1, hy = cy + 1;
+        const uint8_t t = s_t[hy][hx];
+        if (!(t & 2)) {
+            pull(hx, hy, q);
+            store_phase(cx, cy, q);
+            return true;
+        }
+        if ((t & 3) == kSB) {
+            // wall value from the wetting pass (FP64, split into hi + lo); rho := 1 at solid nodes
+            const int in = inner ? (y0 + hy - 3) * nx + (x0 + hx - 3) : s_idx[hy][hx];
+            const bool pr = inner ? false : s_par[hx];
+#pragma unroll
+            for (int k = 0; k < kNF; k++) {
+                const double c = Cw[(long long)relabel(k, pr) * P.N + in];
                 const float h = (float)c;
                 s_ch[k][cy][cx] = h;
                 s_cl[k][cy][cx] = (float)(c - (double)h);
             }
-            s_rho[cy][cx] = R(1.0);
+            s_rho[cy][cx] = 1.0f;
         } else {
 #pragma unroll
             for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = s_cl[k][cy][cx] = 0.0f;
-            s_rho[cy][cx] = R(0.0);
+            s_rho[cy][cx] = 0.0f;
         }
-        return fluid;
+        return false;
     };
 
     {
@@ -492,47 +596,59 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
     }
     const int lx = threadIdx.x, ly = threadIdx.y;
     const int gx = x0 + lx, gy = y0 + ly;
-    float p[27];
-    const bool own_fluid = fill(lx + 2, ly + 2, p);
+    // own node: keep the 9 post-streaming totals and the 3 densities
+    float f[kQ], r0, r1, r2;
+    bool own_fluid;
+    {
+        float q[27];
+        own_fluid = fill(lx + 2, ly + 2, q);
+#pragma unroll
+        for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
+        r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+        r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
+        r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+    }
     __syncthreads();
 
-    // ---- stress tensor of Eq.(10) on the halo-1 region ----
+    // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
     for (int j = tid; j < RX * RY; j += NT) {
         const int rx = j % RX, ry = j / RX;
         const int cx = rx + 1, cy = ry + 1, hx = rx + 2, hy = ry + 2;
-        R Txx = 0.f, Txy = 0.f, Tyy = 0.f;
+        float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
         const uint8_t t = s_t[hy][hx];
         if ((t & 3) != kSI) {
-            const R rho = s_rho[cy][cx];
-            R c[kNF], gxk[kNF], gyk[kNF];
+            const float rho = s_rho[cy][cx];
+            float c[kNF], gxk[kNF], gyk[kNF];
 #pragma unroll
             for (int k = 0; k < kNF; k++) c[k] = s_ch[k][cy][cx];
             if ((t & 3) == kSB) {
                 // solid node: a solid-interior neighbour takes the node's own value
 #pragma unroll
                 for (int k = 0; k < kNF; k++) {
-                    R v[kQ];
-                    const R ch = s_ch[k][cy][cx], cl = s_cl[k][cy][cx];
-                    R vl[kQ];
+                    float v[kQ], vl[kQ];
+                    const float ch = s_ch[k][cy][cx], cl = s_cl[k][cy][cx];
 #pragma unroll
                     for (int a = 1; a < kQ; a++) {
                         const bool si = (s_t[hy + ey(a)][hx + ex(a)] & 3) == kSI;
                         v[a] = si ? ch : s_ch[k][cy + ey(a)][cx + ex(a)];
                         vl[a] = si ? cl : s_cl[k][cy + ey(a)][cx + ex(a)];
                     }
-                    gxk[k] = (R(1.0) / R(3.0)) * (v[1] - v[3]) + (R(1.0) / R(12.0)) * ((v[5] - v[7]) + (v[8] - v[6])) +
-                             ((R(1.0) / R(3.0)) * (vl[1] - vl[3]) + (R(1.0) / R(12.0)) * ((vl[5] - vl[7]) + (vl[8] - vl[6])));
-                    gyk[k] = (R(1.0) / R(3.0)) * (v[2] - v[4]) + (R(1.0) / R(12.0)) * ((v[5] - v[7]) + (v[6] - v[8])) +
-                             ((R(1.0) / R(3.0)) * (vl[2] - vl[4]) + (R(1.0) / R(12.0)) * ((vl[5] - vl[7]) + (vl[6] - vl[8])));
+                    gxk[k] = (1.0f / 3.0f) * (v[1] - v[3]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[8] - v[6])) +
+                             ((1.0f / 3.0f) * (vl[1] - vl[3]) + (1.0f / 12.0f) * ((vl[5] - vl[7]) + (vl[8] - vl[6])));
+                    gyk[k] = (1.0f / 3.0f) * (v[2] - v[4]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[6] - v[8])) +
+                             ((1.0f / 3.0f) * (vl[2] - vl[4]) + (1.0f / 12.0f) * ((vl[5] - vl[7]) + (vl[6] - vl[8])));
                 }
-            } else {
+            } else if (df) {
 #pragma unroll
                 for (int k = 0; k < kNF; k++) grad9_df<CX>(s_ch[k], s_cl[k], cx, cy, gxk[k], gyk[k]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < kNF; k++) grad9_f<CX>(s_ch[k], cx, cy, gxk[k], gyk[k]);
             }
-            const R rho2 = rho * rho;
-            pair_stress(R(P.sig01), c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
-            pair_stress(R(P.sig02), c[0], c[2], gxk[0], gyk[0], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
-            pair_stress(R(P.sig12), c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+            const float rho2 = rho * rho;
+            pair_stress(P.sig01, c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
+            pair_stress(P.sig02, c[0], c[2], gxk[0], gyk[0], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+            pair_stress(P.sig12, c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
         }
         s_txx[ry][rx] = Txx;
         s_txy[ry][rx] = Txy;
@@ -544,69 +660,68 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
 
     // ---- interfacial force F_s = div T (Eq.10 with Eq.12) ----
     const int rx = lx + 1, ry = ly + 1;
-    const R Fx = (R(1.0) / R(3.0)) * (s_txx[ry][rx + 1] - s_txx[ry][rx - 1]) +
-                     (R(1.0) / R(12.0)) * (s_txx[ry + 1][rx + 1] - s_txx[ry + 1][rx - 1] -
-                                       s_txx[ry - 1][rx - 1] + s_txx[ry - 1][rx + 1]) +
-                     (R(1.0) / R(3.0)) * (s_txy[ry + 1][rx] - s_txy[ry - 1][rx]) +
-                     (R(1.0) / R(12.0)) * (s_txy[ry + 1][rx + 1] + s_txy[ry + 1][rx - 1] -
-                                       s_txy[ry - 1][rx - 1] - s_txy[ry - 1][rx + 1]);
-    const R Fy = (R(1.0) / R(3.0)) * (s_txy[ry][rx + 1] - s_txy[ry][rx - 1]) +
-                     (R(1.0) / R(12.0)) * (s_txy[ry + 1][rx + 1] - s_txy[ry + 1][rx - 1] -
-                                       s_txy[ry - 1][rx - 1] + s_txy[ry - 1][rx + 1]) +
-                     (R(1.0) / R(3.0)) * (s_tyy[ry + 1][rx] - s_tyy[ry - 1][rx]) +
-                     (R(1.0) / R(12.0)) * (s_tyy[ry + 1][rx + 1] + s_tyy[ry + 1][rx - 1] -
-                                       s_tyy[ry - 1][rx - 1] - s_tyy[ry - 1][rx + 1]);
+    const float Fx = (1.0f / 3.0f) * (s_txx[ry][rx + 1] - s_txx[ry][rx - 1]) +
+                     (1.0f / 12.0f) * ((s_txx[ry + 1][rx + 1] - s_txx[ry - 1][rx - 1]) +
+                                       (s_txx[ry - 1][rx + 1] - s_txx[ry + 1][rx - 1])) +
+                     (1.0f / 3.0f) * (s_txy[ry + 1][rx] - s_txy[ry - 1][rx]) +
+                     (1.0f / 12.0f) * ((s_txy[ry + 1][rx + 1] - s_txy[ry - 1][rx - 1]) +
+                                       (s_txy[ry + 1][rx - 1] - s_txy[ry - 1][rx + 1]));
+    const float Fy = (1.0f / 3.0f) * (s_txy[ry][rx + 1] - s_txy[ry][rx - 1]) +
+                     (1.0f / 12.0f) * ((s_txy[ry + 1][rx + 1] - s_txy[ry - 1][rx - 1]) +
+                                       (s_txy[ry - 1][rx + 1] - s_txy[ry + 1][rx - 1])) +
+                     (1.0f / 3.0f) * (s_tyy[ry + 1][rx] - s_tyy[ry - 1][rx]) +
+                     (1.0f / 12.0f) * ((s_tyy[ry + 1][rx + 1] - s_tyy[ry - 1][rx - 1]) +
+                                       (s_tyy[ry + 1][rx - 1] - s_tyy[ry - 1][rx + 1]));
 
-    // ---- own densities, colour gradients, normals ----
+    // ---- own colour gradients and pair normals ----
     const int cx = lx + 2, cy = ly + 2;
-    R r0 = 0.f, r1 = 0.f, r2 = 0.f, f[kQ];
-#pragma unroll
-    for (int a = 0; a < kQ; a++) {
-        r0 += p[a];
-        r1 += p[9 + a];
-        r2 += p[18 + a];
-        f[a] = p[a] + p[9 + a] + p[18 + a];
-    }
-    const R rho = r0 + r1 + r2;
-    const R ir = R(1.0) / rho;
+    const float rho = (r0 + r1) + r2;
+    const float ir = 1.0f / rho;
     // correctly rounded fractions: a node that holds one fluid gets exactly C = 1, so the
     // recolouring below leaves its mass unscaled (r * fl(1/r) can round below 1 every step)
-    const R c0 = r0 / rho, c1 = r1 / rho, c2 = r2 / rho;
-    R g0x, g0y, g1x, g1y, g2x, g2y;
-    grad9_df<CX>(s_ch[0], s_cl[0], cx, cy, g0x, g0y);
-    grad9_df<CX>(s_ch[1], s_cl[1], cx, cy, g1x, g1y);
-    grad9_df<CX>(s_ch[2], s_cl[2], cx, cy, g2x, g2y);
-    R n01x, n01y, n02x, n02y, n12x, n12y;
+    const float c0 = r0 / rho, c1 = r1 / rho, c2 = r2 / rho;
+    float g0x, g0y, g1x, g1y, g2x, g2y;
+    if (df) {
+        grad9_df<CX>(s_ch[0], s_cl[0], cx, cy, g0x, g0y);
+        grad9_df<CX>(s_ch[1], s_cl[1], cx, cy, g1x, g1y);
+        grad9_df<CX>(s_ch[2], s_cl[2], cx, cy, g2x, g2y);
+    } else {
+        grad9_f<CX>(s_ch[0], cx, cy, g0x, g0y);
+        grad9_f<CX>(s_ch[1], cx, cy, g1x, g1y);
+        grad9_f<CX>(s_ch[2], cx, cy, g2x, g2y);
+    }
+    float n01x, n01y, n02x, n02y, n12x, n12y;
     pair_normal(c0, c1, g0x, g0y, g1x, g1y, n01x, n01y);
     pair_normal(c0, c2, g0x, g0y, g2x, g2y, n02x, n02y);
     pair_normal(c1, c2, g1x, g1y, g2x, g2y, n12x, n12y);
 
     // ---- MRT collision with forcing (Eq.1-9, 11), mixture tau of Eq.(7) ----
-    const R tau = R(0.5) + R(3.0) / (r0 * P.inv_nu0 + r1 * P.inv_nu1 + r2 * P.inv_nu2);
-    R ux, uy;
+    const float tau = 0.5f + 3.0f / (r0 * P.inv_nu0 + r1 * P.inv_nu1 + r2 * P.inv_nu2);
+    float ux, uy;
     collide_mrt(f, rho, Fx, Fy, tau, ux, uy);
-    const int i = gy * P.nx + gx;
+    const int i = gy * nx + gx;
     if (uout) {
         uout[i] = ux;
-        uout[P.N + i] = uy;
+        uout[N + i] = uy;
     }
 
     // ---- recolouring, Eq.(13)-(15) ----
-    const R trip = fmin(R(35.0) * r0 * r1 * r2 * ir * ir * ir, R(1.0));
-    const R b01 = P.beta0 * (R(1.0) + trip * P.g01) * r0 * r1 * ir;
-    const R b02 = P.beta0 * (R(1.0) + trip * P.g02) * r0 * r2 * ir;
-    const R b12 = P.beta0 * (R(1.0) + trip * P.g12) * r1 * r2 * ir;
-    const R V0x = b01 * n01x + b02 * n02x, V0y = b01 * n01y + b02 * n02y;
-    const R V1x = -b01 * n01x + b12 * n12x, V1y = -b01 * n01y + b12 * n12y;
-    const R V2x = -b02 * n02x - b12 * n12x, V2y = -b02 * n02y - b12 * n12y;
-    const R Cs[3] = {c0, c1, c2};
-    const R Vx[3] = {V0x, V1x, V2x}, Vy[3] = {V0y, V1y, V2y};
+    const float trip = fminf(35.0f * r0 * r1 * r2 * ir * ir * ir, 1.0f);
+    const float b01 = P.beta0 * (1.0f + trip * P.g01) * r0 * r1 * ir;
+    const float b02 = P.beta0 * (1.0f + trip * P.g02) * r0 * r2 * ir;
+    const float b12 = P.beta0 * (1.0f + trip * P.g12) * r1 * r2 * ir;
+    const float V0x = b01 * n01x + b02 * n02x, V0y = b01 * n01y + b02 * n02y;
+    const float V1x = -b01 * n01x + b12 * n12x, V1y = -b01 * n01y + b12 * n12y;
+    const float V2x = -b02 * n02x - b12 * n12x, V2y = -b02 * n02y - b12 * n12y;
+    const float Cs[3] = {c0, c1, c2};
+    const float Vx[3] = {V0x, V1x, V2x}, Vy[3] = {V0y, V1y, V2y};
+    float* o = fout + i;
 #pragma unroll
     for (int k = 0; k < kNF; k++) {
 #pragma unroll
         for (int a = 0; a < kQ; a++) {
-            const R v = Cs[k] * f[a] + wq(a) * (Vx[k] * (R)ex(a) + Vy[k] * (R)ey(a));
-            fout[(long long)(k * kQ + a) * P.N + i] = v;
+            const float v = Cs[k] * f[a] + wq(a) * (Vx[k] * (float)ex(a) + Vy[k] * (float)ey(a));
+            o[(k * kQ + a) * N] = v;
         }
     }
 }
@@ -779,7 +894,8 @@ void launch_wet(const Params& P, int nw, const int* widx, const double* wnrm, co
 {
     if (nw <= 0) return;
     const Store<kStoreF32> st{f, P.N};
-    k_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw);
+    const long long threads = 4LL * nw;
+    k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw);
 }
 
 void launch_wet_init(const Params& P, int nw, const int* widx, const float* f,
@@ -794,7 +910,7 @@ void launch_step_f32(const Params& P, const float* fin, float* fout, const uint8
                      const double* Cw, float* u, cudaStream_t s)
 {
     dim3 grid((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
-    k_step_f32<kTX, kTY, float><<<grid, dim3(kTX, kTY), 0, s>>>(P, fin, fout, type, Cw, u);
+    k_step_f32<kTX, kTY><<<grid, dim3(kTX, kTY), 0, s>>>(P, fin, fout, type, Cw, u);
 }
 
 void launch_init_f32(const Params& P, const double* rho, const uint8_t* type, float* f,

@@ -74,6 +74,7 @@ def _create(lib, **over):
 
 @pytest.mark.parametrize("over,needle", [
     (dict(nx=4), "8x8"),
+    (dict(nx=16, ny=5_000_000), "2^31"),
     (dict(bc_x=7), "bc_x"),
     (dict(nu=(0.1, -1.0, 0.1)), "nu"),
     (dict(sigma=(0.01, 0.0, 0.01)), "sigma"),
