@@ -83,16 +83,20 @@ int lbm3_create(lbm3** out, const lbm3_grid* grid, const uint8_t* solid_mask,
 int lbm3_set_fields(lbm3* h, const double* rho);
 
 /* Advance nsteps >= 0 timesteps (Eq.1-22), asynchronously on the handle's stream.  Each step is
- * the wetting pass over the C_SB list (Eq.21-22) followed by the fused step kernel
- * (Eq.1-16: densities, gradients, interfacial force, MRT collision, recolouring, streaming with
- * halfway bounce-back and the x boundary).  The velocity of the last collision of the call is
- * recorded for lbm3_fields / lbm3_diag. */
+ * the wetting pass over the C_SB list (Eq.21-22) and the fused step kernel (Eq.1-16: densities,
+ * gradients, interfacial force, MRT collision, recolouring, streaming with halfway bounce-back
+ * and the x boundary).  Tiles with no solid node within 3 nodes run concurrently with the wetting
+ * pass on the handle's stream; the other tiles follow the wetting pass on an internal
+ * higher-priority stream that is joined back before the call's work completes.  The velocity of
+ * the last collision of the call is recorded for lbm3_fields / lbm3_diag. */
 int lbm3_step(lbm3* h, int32_t nsteps);
 
-/* lbm3_step with per-launch timing: CUDA events are recorded on the handle's stream around every
- * wetting launch and every fused step launch; after the last step the call synchronises and
- * writes ms_out[0] = summed wetting-kernel time, ms_out[1] = summed step-kernel time (ms). */
-int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[2]);
+/* lbm3_step with per-launch timing: CUDA events are recorded around every launch on the stream
+ * it runs on; after the last step the call synchronises and writes the summed times in ms:
+ * ms_out[0] = wetting pass, ms_out[1] = fused step kernel on the pure tiles (no solid within
+ * 3 nodes; main stream), ms_out[2] = fused step kernel on the other tiles (side stream, after the
+ * wetting pass).  The pure-tile launch overlaps the other two. */
+int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3]);
 
 /* Copy the current post-streaming densities rho_k (host [3][ny][nx], 0 at solid nodes) and the
  * velocity of the most recent collision, Eq.(11) (host [2][ny][nx], may be NULL).  Synchronises. */
@@ -122,9 +126,11 @@ int lbm3_wall_values(lbm3* h, double* c, int32_t cap);
 int lbm3_get_state(lbm3* h, double* f_post, double* wall_c);
 int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c);
 
-/* Size facts: out[0] = fluid nodes, out[1] = C_SB nodes, out[2] = algorithmic HBM bytes of one
- * step-kernel launch, out[3] = step kernels launched per timestep, out[4] = wetting kernels per
- * timestep, out[5] = device bytes held by the handle. */
+/* Size facts: out[0] = fluid nodes, out[1] = C_SB nodes, out[2] = algorithmic HBM bytes of the
+ * fused step per timestep (216 B per fluid node + 1 class byte per node), out[3] = fused-step
+ * launches per timestep, out[4] = wetting launches per timestep, out[5] = device bytes held by
+ * the handle, out[6] = algorithmic bytes of the pure-tile launch (216 B per node), out[7] = nodes
+ * in pure tiles. */
 int lbm3_info(const lbm3* h, int64_t out[8]);
 
 /* Change the stream used by later calls (cudaStream_t). */

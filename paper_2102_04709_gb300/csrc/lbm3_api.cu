@@ -30,6 +30,15 @@ struct lbm3 {
     float* wang = nullptr;
     int nw = 0;
     long long n_fluid = 0;
+    // tiles of the fused step kernel: pure tiles (no solid within 3 nodes, away from the domain
+    // edge) run on the main stream and do not wait for the wetting pass; the other tiles run
+    // after the wetting pass on a higher-priority side stream
+    int* tiles_pure = nullptr;
+    int* tiles_gen = nullptr;
+    int n_pure = 0, n_gen = 0;
+    long long pure_fluid = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t bytes = 0;
     int cur = 0;
     bool ready = false;
@@ -99,10 +108,38 @@ size_t tally(lbm3* h, size_t b)
 void release(lbm3* h)
 {
     void* ptrs[] = {h->f[0], h->f[1], h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
-                    h->widx, h->wnrm, h->wang};
+                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->f[0] = h->f[1] = nullptr;
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->side) cudaStreamDestroy(h->side);
+}
+
+// One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
+// while the side stream runs the wetting pass and then the remaining tiles, join.  With ev != NULL
+// the launches are bracketed by the events ev[0..5] (main: 0-1 pure; side: 2-3 wet, 4-5 rest).
+cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
+{
+    cudaError_t e;
+    float* fin = h->f[h->cur];
+    float* fo = h->f[1 - h->cur];
+    float* u = last ? h->u : nullptr;
+    if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[0], h->stream);
+    launch_step_f32(h->P, h->tiles_pure, h->n_pure, true, fin, fo, h->type, h->Cw, u, h->stream);
+    if (ev) cudaEventRecord(ev[1], h->stream);
+    if (ev) cudaEventRecord(ev[2], h->side);
+    launch_wet(h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->side);
+    if (ev) cudaEventRecord(ev[3], h->side);
+    launch_step_f32(h->P, h->tiles_gen, h->n_gen, false, fin, fo, h->type, h->Cw, u, h->side);
+    if (ev) cudaEventRecord(ev[4], h->side);
+    if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
+    h->cur = 1 - h->cur;
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -215,6 +252,35 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         young = std::max(young, std::fabs(r));
     }
 
+    // ---- tiles of the fused step kernel (2-D prefix sums of the solid mask)
+    std::vector<int> tp, tg;
+    long long pure_fluid = 0;
+    {
+        std::vector<long long> ps((size_t)(nx + 1) * (ny + 1), 0);
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++)
+                ps[(size_t)(y + 1) * (nx + 1) + x + 1] = ps[(size_t)y * (nx + 1) + x + 1] +
+                                                         ps[(size_t)(y + 1) * (nx + 1) + x] -
+                                                         ps[(size_t)y * (nx + 1) + x] +
+                                                         (solid[(size_t)y * nx + x] ? 1 : 0);
+        auto box = [&](int xa, int ya, int xb, int yb) {  // solids in [xa, xb) x [ya, yb)
+            return ps[(size_t)yb * (nx + 1) + xb] - ps[(size_t)ya * (nx + 1) + xb] -
+                   ps[(size_t)yb * (nx + 1) + xa] + ps[(size_t)ya * (nx + 1) + xa];
+        };
+        const int ntx = (nx + kTX - 1) / kTX, nty = (ny + kTY - 1) / kTY;
+        for (int ty = 0; ty < nty; ty++)
+            for (int tx = 0; tx < ntx; tx++) {
+                const int x0 = tx * kTX, y0 = ty * kTY;
+                const bool inner = x0 >= 3 && y0 >= 3 && x0 + kTX + 3 <= nx && y0 + kTY + 3 <= ny;
+                if (inner && box(x0 - 3, y0 - 3, x0 + kTX + 3, y0 + kTY + 3) == 0) {
+                    tp.push_back(ty * ntx + tx);
+                    pure_fluid += (long long)kTX * kTY;
+                } else {
+                    tg.push_back(ty * ntx + tx);
+                }
+            }
+    }
+
     // ---- parameters
     lbm3* h = new lbm3();
     h->stream = (cudaStream_t)stream;
@@ -239,8 +305,16 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     P.g01 = (float)seg_g((s02 * s02 + s12 * s12 - s01 * s01) / (2.0 * s02 * s12));
     P.g02 = (float)seg_g((s01 * s01 + s12 * s12 - s02 * s02) / (2.0 * s01 * s12));
     P.g12 = (float)seg_g((s01 * s01 + s02 * s02 - s12 * s12) / (2.0 * s01 * s02));
+    for (int k = 0; k < kNF; k++)
+        for (int a = 0; a < kQ; a++) {
+            P.off_plane[k * kQ + a] = (k * kQ + a) * (int)N;
+            P.off_pull[k * kQ + a] = (k * kQ + a) * (int)N - ex(a) - ey(a) * nx;
+        }
     h->nw = (int)widx.size();
     h->n_fluid = n_fluid;
+    h->n_pure = (int)tp.size();
+    h->n_gen = (int)tg.size();
+    h->pure_fluid = pure_fluid;
     h->wall_host = widx;
 
     // ---- device buffers
@@ -262,6 +336,17 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (e == cudaSuccess) e = dmalloc((void**)&h->widx, widx.size() * sizeof(int));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wnrm, wnrm.size() * sizeof(double));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wang, wang.size() * sizeof(float));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->tiles_pure, tp.size() * sizeof(int));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->tiles_gen, tg.size() * sizeof(int));
+    if (e == cudaSuccess && !tp.empty()) e = cudaMemcpy(h->tiles_pure, tp.data(), tp.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !tg.empty()) e = cudaMemcpy(h->tiles_gen, tg.data(), tg.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        int lo = 0, hi = 0;
+        e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpy(h->type, cls.data(), N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !widx.empty()) e = cudaMemcpy(h->widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !wnrm.empty()) e = cudaMemcpy(h->wnrm, wnrm.data(), wnrm.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -307,43 +392,29 @@ int lbm3_step(lbm3* h, int32_t nsteps)
     if (!h) return fail(h, LBM3_ERR_INVALID, "NULL handle");
     if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
-    for (int s = 0; s < nsteps; s++) {
-        float* fin = h->f[h->cur];
-        float* fo = h->f[1 - h->cur];
-        launch_wet(h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->stream);
-        launch_step_f32(h->P, fin, fo, h->type, h->Cw, s == nsteps - 1 ? h->u : nullptr, h->stream);
-        h->cur = 1 - h->cur;
-    }
-    CUDA_TRY(h, cudaGetLastError());
+    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, nullptr));
     return LBM3_OK;
 }
 
-int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[2])
+int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3])
 {
     if (!h || !ms_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
     if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
-    ms_out[0] = ms_out[1] = 0.0;
-    std::vector<cudaEvent_t> ev(3 * (size_t)nsteps);
+    ms_out[0] = ms_out[1] = ms_out[2] = 0.0;
+    std::vector<cudaEvent_t> ev(5 * (size_t)nsteps);
     for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
+    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[5 * (size_t)s]));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     for (int s = 0; s < nsteps; s++) {
-        float* fin = h->f[h->cur];
-        float* fo = h->f[1 - h->cur];
-        CUDA_TRY(h, cudaEventRecord(ev[3 * s], h->stream));
-        launch_wet(h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->stream);
-        CUDA_TRY(h, cudaEventRecord(ev[3 * s + 1], h->stream));
-        launch_step_f32(h->P, fin, fo, h->type, h->Cw, s == nsteps - 1 ? h->u : nullptr, h->stream);
-        CUDA_TRY(h, cudaEventRecord(ev[3 * s + 2], h->stream));
-        h->cur = 1 - h->cur;
-    }
-    CUDA_TRY(h, cudaGetLastError());
-    if (nsteps > 0) CUDA_TRY(h, cudaEventSynchronize(ev[3 * (nsteps - 1) + 2]));
-    for (int s = 0; s < nsteps; s++) {
-        float a = 0.f, b = 0.f;
-        CUDA_TRY(h, cudaEventElapsedTime(&a, ev[3 * s], ev[3 * s + 1]));
-        CUDA_TRY(h, cudaEventElapsedTime(&b, ev[3 * s + 1], ev[3 * s + 2]));
+        float a = 0.f, b = 0.f, c = 0.f;
+        const cudaEvent_t* E = &ev[5 * (size_t)s];
+        CUDA_TRY(h, cudaEventElapsedTime(&a, E[2], E[3]));
+        CUDA_TRY(h, cudaEventElapsedTime(&b, E[0], E[1]));
+        CUDA_TRY(h, cudaEventElapsedTime(&c, E[3], E[4]));
         ms_out[0] += a;
         ms_out[1] += b;
+        ms_out[2] += c;
     }
     for (auto& e : ev) cudaEventDestroy(e);
     return LBM3_OK;
@@ -455,9 +526,12 @@ int lbm3_info(const lbm3* h, int64_t out[8])
     out[1] = h->nw;
     // 27 FP32 populations read and written per fluid node, plus one class byte per node
     out[2] = h->n_fluid * 216 + h->P.N;
-    out[3] = 1;
+    out[3] = (h->n_pure > 0) + (h->n_gen > 0);
     out[4] = h->nw > 0 ? 1 : 0;
     out[5] = (int64_t)h->bytes;
+    // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes
+    out[6] = h->pure_fluid * 216;
+    out[7] = h->pure_fluid;
     return LBM3_OK;
 }
 

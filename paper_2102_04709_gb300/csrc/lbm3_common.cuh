@@ -50,6 +50,10 @@ struct Params {
     float inv_nu0, inv_nu1, inv_nu2;
     float beta0;
     float g01, g02, g12;  // g(X_kl) of Eq.(15), constant per pair
+    // element offsets of the 27 population planes (k * 9 + a) * N, and of the pull sources
+    // (k * 9 + a) * N - e_ax - e_ay * nx, for the step kernel's interior tiles
+    int off_plane[27];
+    int off_pull[27];
 };
 
 // Reduced-storage view (per fluid: FP32 rho_k plane + 8 16-bit offset planes).
@@ -199,8 +203,12 @@ void launch_wet(const Params& P, int nw, const int* widx, const double* wnrm, co
                 const float* f, const uint8_t* type, double* Cw, cudaStream_t s);
 void launch_wet_init(const Params& P, int nw, const int* widx, const float* f,
                      const uint8_t* type, double* Cw, cudaStream_t s);
-void launch_step_f32(const Params& P, const float* fin, float* fout, const uint8_t* type,
-                     const double* Cw, float* u, cudaStream_t s);
+// tile of the fused step kernel (interior nodes per CTA)
+constexpr int kTX = 32, kTY = 8;
+// tiles: list of tile indices ty * ceil(nx / kTX) + tx; pure = every listed tile is free of solid
+// nodes within 3 nodes of it and away from the domain edges
+void launch_step_f32(const Params& P, const int* tiles, int ntiles, bool pure, const float* fin,
+                     float* fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s);
 void launch_init_f32(const Params& P, const double* rho, const uint8_t* type, float* f,
                      cudaStream_t s);
 void launch_fields_f32(const Params& P, const float* f, const uint8_t* type, float* rho_out,

@@ -279,7 +279,7 @@ constexpr double kDEps = 4.0 * (double)kW0 - 8.0 * (double)kW1 + 4.0 * (double)k
 // update is applied as f_dag = f + M^-1 dm with dm = -S (m - m_eq) + (I - S/2) M Ftilde, so that
 // the rounded constants 1/9, 1/36 ... only scale the small non-equilibrium change (dm_0 = 0).
 template <typename R>
-__device__ __forceinline__ void collide_mrt(R f[kQ], R rho, R Fx, R Fy, R tau, R& ux, R& uy)
+__device__ __forceinline__ void collide_mrt(R f[kQ], R rho, R Fx, R Fy, R s1, R& ux, R& uy)
 {
     const R d0 = f[0] - kW0;
     const R d1 = f[1] - kW1, d2 = f[2] - kW1, d3 = f[3] - kW1, d4 = f[4] - kW1;
@@ -295,14 +295,13 @@ __device__ __forceinline__ void collide_mrt(R f[kQ], R rho, R Fx, R Fy, R tau, R
     const R qy = -R(2.0) * (f[2] - f[4]) + (f[5] - f[7]) + (f[6] - f[8]);
     const R pxx = (f[1] - f[2]) + (f[3] - f[4]);
     const R pxy = (f[5] - f[6]) + (f[7] - f[8]);
-    const R irho = R(1.0) / rho;
+    const R irho = __fdividef(R(1.0), rho);  // rounding here only perturbs u by ~1 ulp
     ux = (jx + R(0.5) * Fx) * irho;  // Eq.(11)
     uy = (jy + R(0.5) * Fy) * irho;
     const R u2 = ux * ux + uy * uy;
     const R uF = ux * Fx + uy * Fy;
-    // relaxation rates, Eq.(5)-(6)
-    const R s1 = R(1.0) / tau;
-    const R s4 = R(8.0) * (R(2.0) - s1) / (R(8.0) - s1);
+    // relaxation rates, Eq.(5)-(6) (s1 = 1/tau from the caller)
+    const R s4 = __fdividef(R(8.0) * (R(2.0) - s1), R(8.0) - s1);
     const R h1 = R(1.0) - R(0.5) * s1, h4 = R(1.0) - R(0.5) * s4;
     // moment changes: relaxation towards the Eq.(3) equilibrium moments
     // e_eq = rho(-2 + 3u^2), eps_eq = rho(1 - 3u^2), q_eq = -rho u, p_eq = rho(ux^2 - uy^2), rho ux uy,
@@ -410,8 +409,9 @@ __device__ __forceinline__ void grad9_f(const float (*c)[W], int cx, int cy, flo
 // Tiles whose halo-3 region stays inside the domain take arithmetic source indices and skip the
 // bounce-back tests at C_FI nodes; only tiles whose halo-2 region holds a C_SB node carry the
 // float-float phase fields (the wetting feedback at contact lines needs them, see above).
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float* __restrict__ fin,
+template <int TX, int TY, bool PURE>
+__global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const int* __restrict__ tiles,
+                                                      const float* __restrict__ fin,
                                                       float* __restrict__ fout,
                                                       const uint8_t* __restrict__ type,
                                                       const double* __restrict__ Cw,
@@ -427,17 +427,22 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
     __shared__ float s_ch[kNF][CY][CX], s_cl[kNF][CY][CX];  // C_k = hi (+ lo in wall tiles)
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
+    __shared__ float s_g[2 * kNF][TY][TX];   // colour gradients of the tile's own nodes
 
     const int tid = threadIdx.x + TX * threadIdx.y;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int ntx = (P.nx + TX - 1) / TX;
+    const int tile = tiles[blockIdx.x];
+    const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
     const int nx = P.nx;
     const int N = (int)P.N;
-    // halo-3 region inside the domain: no wrap, no ghost, no seam
-    const bool inner = x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= P.nx && y0 + TY + 3 <= P.ny;
+    // halo-3 region inside the domain: no wrap, no ghost, no seam.  A PURE tile is also free
+    // of solid nodes in that region (every node it touches is in C_FI).
+    const bool inner = PURE || (x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= P.nx && y0 + TY + 3 <= P.ny);
 
     // ---- phase 0: geometry of the halo-3 region ----
     int wall = 0;
-    if (inner) {
+    if (PURE) {
+    } else if (inner) {
         for (int j = tid; j < HX * HY; j += NT) {
             const int hx = j % HX, hy = j / HX;
             const uint8_t t = __ldg(type + (y0 + hy - 3) * nx + (x0 + hx - 3));
@@ -460,27 +465,27 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
             if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY) wall = 1;
         }
     }
-    const bool df = __syncthreads_or(wall);
+    const bool df = PURE ? false : __syncthreads_or(wall);
 
     // ---- phase 1: post-streaming populations, densities and phase fields ----
     // pull of the fluid node at (hx, hy) of the geometry region into q[27]
     auto pull = [&](int hx, int hy, float q[27]) {
-        const uint8_t t = s_t[hy][hx];
+        const uint8_t t = PURE ? (uint8_t)kFI : s_t[hy][hx];
         if (inner) {
             const int i = (y0 + hy - 3) * nx + (x0 + hx - 3);
-            if ((t & 3) == kFI) {
+            const float* b = fin + i;
+            if (PURE || (t & 3) == kFI) {
 #pragma unroll
                 for (int a = 0; a < kQ; a++)
 #pragma unroll
-                    for (int k = 0; k < kNF; k++)
-                        q[9 * k + a] = __ldg(fin + (k * kQ + a) * N + (i - ex(a) - ey(a) * nx));
+                    for (int k = 0; k < kNF; k++) q[9 * k + a] = __ldg(b + P.off_pull[k * kQ + a]);
             } else {
 #pragma unroll
                 for (int a = 0; a < kQ; a++) {
                     const bool bb = s_t[hy - ey(a)][hx - ex(a)] & 2;
-                    const int off = bb ? opp(a) * N + i : a * N + (i - ex(a) - ey(a) * nx);
 #pragma unroll
-                    for (int k = 0; k < kNF; k++) q[9 * k + a] = __ldg(fin + k * kQ * N + off);
+                    for (int k = 0; k < kNF; k++)
+                        q[9 * k + a] = __ldg(b + (bb ? P.off_plane[k * kQ + opp(a)] : P.off_pull[k * kQ + a]));
                 }
             }
             return;
@@ -539,7 +544,7 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
                 r[k] = ((qk[0] + (qk[1] + qk[3])) + (qk[2] + qk[4])) + ((qk[5] + qk[7]) + (qk[6] + qk[8]));
             }
             const float rho = (r[0] + r[1]) + r[2];
-            const float ir = 1.0f / rho;
+            const float ir = __fdividef(1.0f, rho);
 #pragma unroll
             for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = r[k] * ir;
             s_rho[cy][cx] = rho;
@@ -547,7 +552,7 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
     };
     auto fill = [&](int cx, int cy, float q[27]) -> bool {
         const int hx = cx + 1, hy = cy + 1;
-        const uint8_t t = s_t[hy][hx];
+        const uint8_t t = PURE ? (uint8_t)kFI : s_t[hy][hx];
         if (!(t & 2)) {
             pull(hx, hy, q);
             store_phase(cx, cy, q);
@@ -615,13 +620,13 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
         const int rx = j % RX, ry = j / RX;
         const int cx = rx + 1, cy = ry + 1, hx = rx + 2, hy = ry + 2;
         float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
-        const uint8_t t = s_t[hy][hx];
+        const uint8_t t = PURE ? (uint8_t)kFI : s_t[hy][hx];
         if ((t & 3) != kSI) {
             const float rho = s_rho[cy][cx];
             float c[kNF], gxk[kNF], gyk[kNF];
 #pragma unroll
             for (int k = 0; k < kNF; k++) c[k] = s_ch[k][cy][cx];
-            if ((t & 3) == kSB) {
+            if (!PURE && (t & 3) == kSB) {
                 // solid node: a solid-interior neighbour takes the node's own value
 #pragma unroll
                 for (int k = 0; k < kNF; k++) {
@@ -644,6 +649,13 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
             } else {
 #pragma unroll
                 for (int k = 0; k < kNF; k++) grad9_f<CX>(s_ch[k], cx, cy, gxk[k], gyk[k]);
+            }
+            if (rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) {
+#pragma unroll
+                for (int k = 0; k < kNF; k++) {
+                    s_g[2 * k][ry - 1][rx - 1] = gxk[k];
+                    s_g[2 * k + 1][ry - 1][rx - 1] = gyk[k];
+                }
             }
             const float rho2 = rho * rho;
             pair_stress(P.sig01, c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
@@ -673,32 +685,31 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
                      (1.0f / 12.0f) * ((s_tyy[ry + 1][rx + 1] - s_tyy[ry - 1][rx - 1]) +
                                        (s_tyy[ry + 1][rx - 1] - s_tyy[ry - 1][rx + 1]));
 
-    // ---- own colour gradients and pair normals ----
-    const int cx = lx + 2, cy = ly + 2;
+    // ---- own colour gradients (from phase 2) and pair normals ----
     const float rho = (r0 + r1) + r2;
-    const float ir = 1.0f / rho;
-    // correctly rounded fractions: a node that holds one fluid gets exactly C = 1, so the
-    // recolouring below leaves its mass unscaled (r * fl(1/r) can round below 1 every step)
-    const float c0 = r0 / rho, c1 = r1 / rho, c2 = r2 / rho;
-    float g0x, g0y, g1x, g1y, g2x, g2y;
-    if (df) {
-        grad9_df<CX>(s_ch[0], s_cl[0], cx, cy, g0x, g0y);
-        grad9_df<CX>(s_ch[1], s_cl[1], cx, cy, g1x, g1y);
-        grad9_df<CX>(s_ch[2], s_cl[2], cx, cy, g2x, g2y);
-    } else {
-        grad9_f<CX>(s_ch[0], cx, cy, g0x, g0y);
-        grad9_f<CX>(s_ch[1], cx, cy, g1x, g1y);
-        grad9_f<CX>(s_ch[2], cx, cy, g2x, g2y);
-    }
+    const float ir = __fdividef(1.0f, rho);
+    // fractions as the quotient corrected by its exact FMA residual: a node that holds one fluid
+    // gets exactly C = 1, so the recolouring below leaves its mass unscaled (r * fl(1/r) can
+    // round below 1 every step)
+    auto frac = [&](float r) {
+        const float q = r * ir;
+        return fmaf(fmaf(-q, rho, r), ir, q);
+    };
+    const float c0 = frac(r0), c1 = frac(r1), c2 = frac(r2);
+    const float g0x = s_g[0][ly][lx], g0y = s_g[1][ly][lx];
+    const float g1x = s_g[2][ly][lx], g1y = s_g[3][ly][lx];
+    const float g2x = s_g[4][ly][lx], g2y = s_g[5][ly][lx];
     float n01x, n01y, n02x, n02y, n12x, n12y;
     pair_normal(c0, c1, g0x, g0y, g1x, g1y, n01x, n01y);
     pair_normal(c0, c2, g0x, g0y, g2x, g2y, n02x, n02y);
     pair_normal(c1, c2, g1x, g1y, g2x, g2y, n12x, n12y);
 
     // ---- MRT collision with forcing (Eq.1-9, 11), mixture tau of Eq.(7) ----
-    const float tau = 0.5f + 3.0f / (r0 * P.inv_nu0 + r1 * P.inv_nu1 + r2 * P.inv_nu2);
+    // tau = 1/2 + 3 / sum(rho_k / nu_k), so 1/tau = D / (D/2 + 3)
+    const float D = (r0 * P.inv_nu0 + r1 * P.inv_nu1) + r2 * P.inv_nu2;
+    const float s1 = __fdividef(D, 0.5f * D + 3.0f);
     float ux, uy;
-    collide_mrt(f, rho, Fx, Fy, tau, ux, uy);
+    collide_mrt(f, rho, Fx, Fy, s1, ux, uy);
     const int i = gy * nx + gx;
     if (uout) {
         uout[i] = ux;
@@ -721,12 +732,12 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const float
 #pragma unroll
         for (int a = 0; a < kQ; a++) {
             const float v = Cs[k] * f[a] + wq(a) * (Vx[k] * (float)ex(a) + Vy[k] * (float)ey(a));
-            o[(k * kQ + a) * N] = v;
+            o[P.off_plane[k * kQ + a]] = v;
         }
     }
 }
 
-constexpr int kTX = 32, kTY = 8;
+
 
 // ------------------------------------------------------------------------------------------
 // initial state, fields, diagnostics
@@ -906,11 +917,14 @@ void launch_wet_init(const Params& P, int nw, const int* widx, const float* f,
     k_wet_init<<<(nw + 127) / 128, 128, 0, s>>>(P, nw, widx, st, type, Cw);
 }
 
-void launch_step_f32(const Params& P, const float* fin, float* fout, const uint8_t* type,
-                     const double* Cw, float* u, cudaStream_t s)
+void launch_step_f32(const Params& P, const int* tiles, int ntiles, bool pure, const float* fin,
+                     float* fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
 {
-    dim3 grid((P.nx + kTX - 1) / kTX, (P.ny + kTY - 1) / kTY);
-    k_step_f32<kTX, kTY><<<grid, dim3(kTX, kTY), 0, s>>>(P, fin, fout, type, Cw, u);
+    if (ntiles <= 0) return;
+    if (pure)
+        k_step_f32<kTX, kTY, true><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+    else
+        k_step_f32<kTX, kTY, false><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
 }
 
 void launch_init_f32(const Params& P, const double* rho, const uint8_t* type, float* f,

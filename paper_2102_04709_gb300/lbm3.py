@@ -46,11 +46,13 @@ _D = ctypes.POINTER(ctypes.c_double)
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load liblbm3.so (built by ``paper_2102_04709_gb300.build``); raise if it is missing."""
+def load(path: str | None = None):
+    """Load liblbm3.so (built by ``paper_2102_04709_gb300.build``, or the file named by the
+    LBM3_LIB environment variable); raise if it is missing."""
     global _lib
     if _lib is not None:
         return _lib
+    path = path or os.environ.get("LBM3_LIB") or LIB_PATH
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with paper_2102_04709_gb300.build.build()")
     L = ctypes.CDLL(path)
@@ -154,10 +156,11 @@ class Lbm3:
         _check(self._h, load().lbm3_step(self._h, int(n)))
 
     def step_timed(self, n):
-        """Advance n steps; return (ms in wetting kernels, ms in step kernels), CUDA-event timed."""
-        out = np.zeros(2)
+        """Advance n steps; return CUDA-event times in ms summed over the steps:
+        (wetting pass, fused kernel on pure tiles, fused kernel on the other tiles)."""
+        out = np.zeros(3)
         _check(self._h, load().lbm3_step_timed(self._h, int(n), _dp(out)))
-        return float(out[0]), float(out[1])
+        return float(out[0]), float(out[1]), float(out[2])
 
     def fields(self):
         rho = np.empty(3 * self.n)
@@ -201,7 +204,8 @@ class Lbm3:
         out = np.zeros(8, np.int64)
         _check(self._h, load().lbm3_info(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return {"n_fluid": int(out[0]), "n_wall": int(out[1]), "step_bytes": int(out[2]),
-                "step_kernels": int(out[3]), "wet_kernels": int(out[4]), "device_bytes": int(out[5])}
+                "step_kernels": int(out[3]), "wet_kernels": int(out[4]), "device_bytes": int(out[5]),
+                "pure_bytes": int(out[6]), "pure_nodes": int(out[7])}
 
     def set_stream(self, stream):
         _check(self._h, load().lbm3_set_stream(self._h, stream))
