@@ -31,6 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 WORKLOAD = "pillars_4096x2048_theta90"
 
 
@@ -43,6 +44,10 @@ def parse():
     ap.add_argument("--theta", type=float, default=90.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
+                    help="population storage of the headline run")
+    ap.add_argument("--no-alt-storage", action="store_true",
+                    help="skip the extra FP16 / BF16 storage timings")
     return ap.parse_args()
 
 
@@ -223,7 +228,8 @@ def run_ours(args):
     w = W.config4(args.theta)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    sim = lbm3.Lbm3.from_workload(w, stream=stream.cuda_stream)
+    prec = PRECISIONS[args.precision]
+    sim = lbm3.Lbm3.from_workload(w, precision=prec, stream=stream.cuda_stream)
     info = sim.info()
 
     def barrier():
@@ -268,6 +274,30 @@ def run_ours(args):
                "h2d_bytes_per_step": int(math.ceil(rho_host.nbytes / args.steps)),
                "d2h_bytes_per_step": int(math.ceil((rho_out.nbytes + u_out.nbytes) / args.steps))}
 
+    # the same workload with the other population storages (shorter timed region each)
+    alt = {}
+    if not args.no_alt_storage:
+        for name, p in PRECISIONS.items():
+            if name == args.precision:
+                continue
+            del sim
+            sim = lbm3.Lbm3.from_workload(w, precision=p, stream=stream.cuda_stream)
+            sim.step(args.warmup)
+            barrier()
+            n_alt = max(args.steps // 2, 1)
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            _, msp, _ = sim.step_timed(n_alt)
+            a1.record(stream)
+            barrier()
+            ams = a0.elapsed_time(a1)
+            ainfo = sim.info()
+            alt[name] = {"value": w.n * n_alt * ws / (ams * 1e-3) / 1e6, "unit": "MLUPS",
+                         "ms_per_step": ams / n_alt, "steps": n_alt,
+                         "bytes_per_fluid_node": 216 if p == 0 else 120,
+                         "pure_kernel_gbs": ainfo["pure_bytes"] / (msp / n_alt * 1e-3) / 1e9}
+
     if rank != 0:
         return
     value = w.n * args.steps * ws / (ms * 1e-3) / 1e6
@@ -282,7 +312,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "fluid_nodes": info["n_fluid"],
-                   "wall_nodes": info["n_wall"], "storage": "fp32",
+                   "wall_nodes": info["n_wall"], "storage": args.precision,
+                   "alt_storage": alt,
                    "mflups": info["n_fluid"] * args.steps * ws / (ms * 1e-3) / 1e6,
                    "l2": "populations 2 x 0.91 GB > 129 MB L2: no flush between steps",
                    "replicas": ws, "ms_wet_per_step": ms_wet / args.steps,

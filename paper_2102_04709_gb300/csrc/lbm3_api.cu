@@ -17,8 +17,9 @@ struct lbm3 {
     Params P{};
     int precision = 0;
     cudaStream_t stream = nullptr;
-    // device buffers
-    float* f[2] = {nullptr, nullptr};
+    // device buffers: two population buffers (FP32 planes, or FP32 densities + 16-bit offset
+    // records), the node classes, wall values, velocity, scratch
+    Pop pop[2] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     uint8_t* type = nullptr;
     double* Cw = nullptr;          // [3][N] wall values (written at C_SB nodes only)
     float* u = nullptr;
@@ -107,11 +108,12 @@ size_t tally(lbm3* h, size_t b)
 
 void release(lbm3* h)
 {
-    void* ptrs[] = {h->f[0], h->f[1], h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
+    void* ptrs[] = {h->pop[0].f, h->pop[1].f, h->pop[0].rho, h->pop[1].rho, h->pop[0].off,
+                    h->pop[1].off, h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
                     h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    h->f[0] = h->f[1] = nullptr;
+    h->pop[0] = h->pop[1] = Pop{nullptr, nullptr, nullptr};
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->side) cudaStreamDestroy(h->side);
@@ -123,18 +125,18 @@ void release(lbm3* h)
 cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 {
     cudaError_t e;
-    float* fin = h->f[h->cur];
-    float* fo = h->f[1 - h->cur];
+    const Pop& fin = h->pop[h->cur];
+    const Pop& fo = h->pop[1 - h->cur];
     float* u = last ? h->u : nullptr;
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
-    launch_step_f32(h->P, h->tiles_pure, h->n_pure, true, fin, fo, h->type, h->Cw, u, h->stream);
+    launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, true, fin, fo, h->type, h->Cw, u, h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (ev) cudaEventRecord(ev[2], h->side);
-    launch_wet(h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->side);
+    launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->side);
     if (ev) cudaEventRecord(ev[3], h->side);
-    launch_step_f32(h->P, h->tiles_gen, h->n_gen, false, fin, fo, h->type, h->Cw, u, h->side);
+    launch_step(h->precision, h->P, h->tiles_gen, h->n_gen, false, fin, fo, h->type, h->Cw, u, h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
@@ -157,8 +159,8 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (g->nx < 8 || g->ny < 8 || 27LL * g->nx * g->ny >= (1LL << 31))
         return fail(nullptr, LBM3_ERR_INVALID, "grid must be at least 8x8 with 27 * nx * ny < 2^31");
     if (g->bc_x < 0 || g->bc_x > 3) return fail(nullptr, LBM3_ERR_INVALID, "bad bc_x");
-    if (g->precision != LBM3_FP32)
-        return fail(nullptr, LBM3_ERR_INVALID, "precision not built in this library");
+    if (g->precision != LBM3_FP32 && g->precision != LBM3_FP16 && g->precision != LBM3_BF16)
+        return fail(nullptr, LBM3_ERR_INVALID, "precision must be LBM3_FP32, LBM3_FP16 or LBM3_BF16");
     for (int j = 0; j < 3; j++) {
         if (!(sigma[j] > 0.0) || !std::isfinite(sigma[j]))
             return fail(nullptr, LBM3_ERR_INVALID, "sigma must be positive");
@@ -309,6 +311,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         for (int a = 0; a < kQ; a++) {
             P.off_plane[k * kQ + a] = (k * kQ + a) * (int)N;
             P.off_pull[k * kQ + a] = (k * kQ + a) * (int)N - ex(a) - ey(a) * nx;
+            P.off_pull16[k * kQ + a] = k * (int)N - ex(a) - ey(a) * nx;
         }
     h->nw = (int)widx.size();
     h->n_fluid = n_fluid;
@@ -323,10 +326,15 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         if (e == cudaSuccess) tally(h, b);
         return e;
     };
-    const size_t fbytes = (size_t)27 * N * sizeof(float);
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = dmalloc((void**)&h->f[0], fbytes);
-    if (e == cudaSuccess) e = dmalloc((void**)&h->f[1], fbytes);
+    for (int b = 0; b < 2; b++) {
+        if (g->precision == LBM3_FP32) {
+            if (e == cudaSuccess) e = dmalloc((void**)&h->pop[b].f, (size_t)27 * N * sizeof(float));
+        } else {
+            if (e == cudaSuccess) e = dmalloc((void**)&h->pop[b].rho, (size_t)3 * N * sizeof(float));
+            if (e == cudaSuccess) e = dmalloc((void**)&h->pop[b].off, (size_t)3 * N * sizeof(uint4));
+        }
+    }
     if (e == cudaSuccess) e = dmalloc((void**)&h->type, N);
     if (e == cudaSuccess) e = dmalloc((void**)&h->Cw, 3 * N * sizeof(double));
     if (e == cudaSuccess) e = dmalloc((void**)&h->u, 2 * N * sizeof(float));
@@ -378,8 +386,8 @@ int lbm3_set_fields(lbm3* h, const double* rho)
     CUDA_TRY(h, cudaMallocAsync((void**)&drho, 3 * N * sizeof(double), h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(drho, rho, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->cur = 0;
-    launch_init_f32(h->P, drho, h->type, h->f[0], h->stream);
-    launch_wet_init(h->P, h->nw, h->widx, h->f[0], h->type, h->Cw, h->stream);
+    launch_init(h->precision, h->P, drho, h->type, h->pop[0], h->stream);
+    launch_wet_init(h->precision, h->P, h->nw, h->widx, h->pop[0], h->type, h->Cw, h->stream);
     CUDA_TRY(h, cudaMemsetAsync(h->u, 0, 2 * N * sizeof(float), h->stream));
     CUDA_TRY(h, cudaFreeAsync(drho, h->stream));
     CUDA_TRY(h, cudaGetLastError());
@@ -425,7 +433,7 @@ int lbm3_fields(lbm3* h, double* rho_out, double* u_out)
     if (!h || !rho_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
     const size_t N = (size_t)h->P.N;
-    launch_fields_f32(h->P, h->f[h->cur], h->type, h->scratch, h->stream);
+    launch_fields(h->precision, h->P, h->pop[h->cur], h->type, h->scratch, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     std::vector<float> tmp(3 * N);
     CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), h->scratch, 3 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
@@ -445,7 +453,7 @@ int lbm3_diag(lbm3* h, double out[8])
 {
     if (!h || !out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
-    launch_diag_f32(h->P, h->f[h->cur], h->type, h->u, h->partials, h->dout, h->stream);
+    launch_diag(h->precision, h->P, h->pop[h->cur], h->type, h->u, h->partials, h->dout, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaMemcpyAsync(out, h->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
@@ -484,11 +492,13 @@ int lbm3_get_state(lbm3* h, double* f_post, double* wall_c)
     if (!h || !f_post) return fail(h, LBM3_ERR_INVALID, "NULL argument");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
     const size_t N = (size_t)h->P.N;
-    float* post = h->f[1 - h->cur];  // the idle population buffer serves as scratch
-    launch_get_state_f32(h->P, h->f[h->cur], h->type, post, h->stream);
+    float* post = nullptr;
+    CUDA_TRY(h, cudaMallocAsync((void**)&post, 27 * N * sizeof(float), h->stream));
+    launch_get_state(h->precision, h->P, h->pop[h->cur], h->type, post, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     std::vector<float> tmp(27 * N);
     CUDA_TRY(h, cudaMemcpyAsync(tmp.data(), post, 27 * N * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CUDA_TRY(h, cudaFreeAsync(post, h->stream));
     std::vector<double> cw;
     if (wall_c) {
         cw.resize(3 * N);
@@ -508,7 +518,7 @@ int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c)
     CUDA_TRY(h, cudaMallocAsync((void**)&dpost, 27 * N * sizeof(double), h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(dpost, f_post, 27 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->cur = 0;
-    launch_set_state_f32(h->P, dpost, h->type, h->f[0], h->stream);
+    launch_set_state(h->precision, h->P, dpost, h->type, h->pop[0], h->stream);
     CUDA_TRY(h, cudaMemcpyAsync(h->Cw, wall_c, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->u, 0, 2 * N * sizeof(float), h->stream));
     CUDA_TRY(h, cudaFreeAsync(dpost, h->stream));
@@ -525,12 +535,15 @@ int lbm3_info(const lbm3* h, int64_t out[8])
     out[0] = h->n_fluid;
     out[1] = h->nw;
     // 27 FP32 populations read and written per fluid node, plus one class byte per node
-    out[2] = h->n_fluid * 216 + h->P.N;
+    // populations read and written per fluid node: 27 FP32 (216 B), or per fluid an FP32 density
+    // and 8 16-bit offsets (120 B); plus one class byte per node
+    const long long per = h->precision == LBM3_FP32 ? 216 : 120;
+    out[2] = h->n_fluid * per + h->P.N;
     out[3] = (h->n_pure > 0) + (h->n_gen > 0);
     out[4] = h->nw > 0 ? 1 : 0;
     out[5] = (int64_t)h->bytes;
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes
-    out[6] = h->pure_fluid * 216;
+    out[6] = h->pure_fluid * per;
     out[7] = h->pure_fluid;
     return LBM3_OK;
 }

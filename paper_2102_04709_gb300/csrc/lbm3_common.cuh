@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lbm3k {
@@ -54,13 +56,39 @@ struct Params {
     // (k * 9 + a) * N - e_ax - e_ay * nx, for the step kernel's interior tiles
     int off_plane[27];
     int off_pull[27];
+    // reduced storage: element offsets k * N - e_ax - e_ay * nx of the pull sources in the rho and
+    // offset-record planes
+    int off_pull16[27];
 };
 
-// Reduced-storage view (per fluid: FP32 rho_k plane + 8 16-bit offset planes).
-struct R16 {
-    float* rho;           // [3][N]
-    uint16_t* off;        // [3][8][N]; offset of direction a (1..8) is plane a-1
+// One population buffer.  FP32 storage: f[27][N], plane k*9+a, the post-collision populations
+// f''_ak.  Reduced storage (FP16 / BF16 offsets): rho[3][N] = sum_a f''_ak in FP32 and
+// off[3][N] = one 16-byte record per node and fluid holding the 8 offsets f''_ak - w_a rho_k
+// (a = 1..8, element a-1); the rest population is w_0 rho_k - sum of the offsets, so the
+// stored mass of every fluid is exact whatever the 16-bit rounding.
+struct Pop {
+    float* f;
+    float* rho;
+    uint4* off;
 };
+
+template <int STORE>
+__device__ __forceinline__ float dec16(unsigned short u)
+{
+    if constexpr (STORE == kStoreF16)
+        return __half2float(__ushort_as_half(u));
+    else
+        return __uint_as_float((unsigned)u << 16);
+}
+
+template <int STORE>
+__device__ __forceinline__ unsigned short enc16(float v)
+{
+    if constexpr (STORE == kStoreF16)
+        return __half_as_ushort(__float2half_rn(v));
+    else
+        return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
 
 __host__ __device__ inline int floordiv_i(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
 
@@ -160,12 +188,68 @@ template <>
 struct Store<kStoreF32> {
     const float* f;  // [27][N] post-collision, pre-streaming populations
     long long N;
+    __host__ __device__ Store(const Pop& p, long long n) : f(p.f), N(n) {}
+    __host__ __device__ Store(const float* p, long long n) : f(p), N(n) {}
     // population a of (storage) fluid k stored at node idx
     __device__ __forceinline__ float get(int k, int a, int idx) const
     {
         return __ldg(f + (long long)(k * kQ + a) * N + idx);
     }
 };
+
+template <int STORE>
+struct Store16 {
+    const float* rho;
+    const uint4* off;
+    long long N;
+    __host__ __device__ Store16(const Pop& p, long long n) : rho(p.rho), off(p.off), N(n) {}
+    __device__ __forceinline__ float offset(int k, int a, int idx) const
+    {
+        return dec16<STORE>(__ldg(reinterpret_cast<const unsigned short*>(off + (long long)k * N + idx) + (a - 1)));
+    }
+    __device__ __forceinline__ float get(int k, int a, int idx) const
+    {
+        const float r = __ldg(rho + (long long)k * N + idx);
+        if (a > 0) return wq(a) * r + offset(k, a, idx);
+        const uint4 w = __ldg(off + (long long)k * N + idx);
+        const unsigned u[4] = {w.x, w.y, w.z, w.w};
+        float s = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+            s += dec16<STORE>((unsigned short)(u[j] & 0xffffu)) + dec16<STORE>((unsigned short)(u[j] >> 16));
+        return wq(0) * r - s;
+    }
+};
+template <>
+struct Store<kStoreF16> : Store16<kStoreF16> {
+    using Store16<kStoreF16>::Store16;
+};
+template <>
+struct Store<kStoreBF16> : Store16<kStoreBF16> {
+    using Store16<kStoreBF16>::Store16;
+};
+
+// write the 27 post-collision populations v[k*9+a] of node i into an output buffer
+template <int STORE>
+__device__ __forceinline__ void store_node(const Pop& out, long long N, int i, const float v[27])
+{
+    if constexpr (STORE == kStoreF32) {
+#pragma unroll
+        for (int j = 0; j < 27; j++) out.f[(long long)j * N + i] = v[j];
+    } else {
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            const float* q = v + 9 * k;
+            const float r = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+            unsigned short h[8];
+#pragma unroll
+            for (int a = 1; a < kQ; a++) h[a - 1] = enc16<STORE>(q[a] - wq(a) * r);
+            out.rho[(long long)k * N + i] = r;
+            out.off[(long long)k * N + i] = make_uint4(h[0] | ((unsigned)h[1] << 16), h[2] | ((unsigned)h[3] << 16),
+                                                       h[4] | ((unsigned)h[5] << 16), h[6] | ((unsigned)h[7] << 16));
+        }
+    }
+}
 
 // Pull the post-streaming populations of the fluid node at unwrapped (X, Y) from global
 // memory (labels in the frame of that unwrapped position), Eq.(16) with halfway bounce-back,
@@ -198,28 +282,27 @@ __device__ void pull_global(const Params& P, const S& st, const uint8_t* __restr
     if (outlet) zou_he(P, p, false);
 }
 
-// ---- kernel launchers (lbm3_step.cu) ----
-void launch_wet(const Params& P, int nw, const int* widx, const double* wnrm, const float* wang,
-                const float* f, const uint8_t* type, double* Cw, cudaStream_t s);
-void launch_wet_init(const Params& P, int nw, const int* widx, const float* f,
+// ---- kernel launchers (lbm3_step.cu); `store` is kStoreF32 / kStoreF16 / kStoreBF16 ----
+void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
+                const float* wang, const Pop& f, const uint8_t* type, double* Cw, cudaStream_t s);
+void launch_wet_init(int store, const Params& P, int nw, const int* widx, const Pop& f,
                      const uint8_t* type, double* Cw, cudaStream_t s);
 // tile of the fused step kernel (interior nodes per CTA)
 constexpr int kTX = 32, kTY = 8;
 // tiles: list of tile indices ty * ceil(nx / kTX) + tx; pure = every listed tile is free of solid
 // nodes within 3 nodes of it and away from the domain edges
-void launch_step_f32(const Params& P, const int* tiles, int ntiles, bool pure, const float* fin,
-                     float* fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s);
-void launch_init_f32(const Params& P, const double* rho, const uint8_t* type, float* f,
-                     cudaStream_t s);
-void launch_fields_f32(const Params& P, const float* f, const uint8_t* type, float* rho_out,
-                       cudaStream_t s);
-void launch_get_state_f32(const Params& P, const float* f, const uint8_t* type, float* post,
-                          cudaStream_t s);
-void launch_set_state_f32(const Params& P, const double* post, const uint8_t* type, float* f,
-                          cudaStream_t s);
+void launch_step(int store, const Params& P, const int* tiles, int ntiles, bool pure, const Pop& fin,
+                 const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s);
+void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,
+                 cudaStream_t s);
+void launch_fields(int store, const Params& P, const Pop& f, const uint8_t* type, float* rho_out,
+                   cudaStream_t s);
+void launch_get_state(int store, const Params& P, const Pop& f, const uint8_t* type, float* post,
+                      cudaStream_t s);
+void launch_set_state(int store, const Params& P, const double* post, const uint8_t* type,
+                      const Pop& f, cudaStream_t s);
 int diag_blocks(const Params& P);
-void launch_diag_f32(const Params& P, const float* f, const uint8_t* type, const float* u,
-                     double* partials, double* out, cudaStream_t s);
-const char* step_kernel_name();
+void launch_diag(int store, const Params& P, const Pop& f, const uint8_t* type, const float* u,
+                 double* partials, double* out, cudaStream_t s);
 
 }  // namespace lbm3k

@@ -236,7 +236,8 @@ __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const
     const double cp = th <= 90.0 ? fmax(cd, other) : fmin(cd, other);
     const double cg = __shfl_xor_sync(0xffffffffu, cp, 2);
     if (valid && (g & 3) == 0) {
-        double c0 = cp, c1 = cg;
+        // fractions stay in [0, 1] (a no-op unless 16-bit storage rounded a density below 0)
+        double c0 = fmin(fmax(cp, 0.0), 1.0), c1 = fmin(fmax(cg, 0.0), 1.0);
         const double s = c0 + c1;
         if (s > 1.0) {
             c0 /= s;
@@ -342,7 +343,9 @@ __device__ __forceinline__ void pair_stress(R sig, R ck, R cl, R gkx, R gky, R g
     const R Gy = cl * gky - ck * gly;
     const R G2 = Gx * Gx + Gy * Gy;
     if (G2 > kG2Eps) {
-        const R A = fmin(1e6f * ck * cl * rho2, R(1.0));
+        // A_kl lies in [0, 1]; the clamp at 0 matters only for the reduced storage, where an
+        // absent fluid can reconstruct to a density of -1e-5 that 1e6 would amplify
+        const R A = fmin(fmax(R(1e6) * ck * cl * rho2, R(0.0)), R(1.0));
         const R s = sig * A * rsqrt(G2);
         Txx += s * Gy * Gy;
         Txy -= s * Gx * Gy;
@@ -409,13 +412,12 @@ __device__ __forceinline__ void grad9_f(const float (*c)[W], int cx, int cy, flo
 // Tiles whose halo-3 region stays inside the domain take arithmetic source indices and skip the
 // bounce-back tests at C_FI nodes; only tiles whose halo-2 region holds a C_SB node carry the
 // float-float phase fields (the wetting feedback at contact lines needs them, see above).
-template <int TX, int TY, bool PURE>
-__global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const int* __restrict__ tiles,
-                                                      const float* __restrict__ fin,
-                                                      float* __restrict__ fout,
-                                                      const uint8_t* __restrict__ type,
-                                                      const double* __restrict__ Cw,
-                                                      float* __restrict__ uout)
+template <int TX, int TY, bool PURE, int STORE>
+__global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __restrict__ tiles,
+                                                  const Pop fin, const Pop fout,
+                                                  const uint8_t* __restrict__ type,
+                                                  const double* __restrict__ Cw,
+                                                  float* __restrict__ uout)
 {
     constexpr int NT = TX * TY;
     constexpr int HX = TX + 6, HY = TY + 6;  // geometry region (halo 3)
@@ -473,30 +475,62 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const int* 
         const uint8_t t = PURE ? (uint8_t)kFI : s_t[hy][hx];
         if (inner) {
             const int i = (y0 + hy - 3) * nx + (x0 + hx - 3);
-            const float* b = fin + i;
-            if (PURE || (t & 3) == kFI) {
+            const bool fi = PURE || (t & 3) == kFI;
+            if constexpr (STORE == kStoreF32) {
+                const float* b = fin.f + i;
+                if (fi) {
 #pragma unroll
-                for (int a = 0; a < kQ; a++)
+                    for (int a = 0; a < kQ; a++)
 #pragma unroll
-                    for (int k = 0; k < kNF; k++) q[9 * k + a] = __ldg(b + P.off_pull[k * kQ + a]);
+                        for (int k = 0; k < kNF; k++) q[9 * k + a] = __ldg(b + P.off_pull[k * kQ + a]);
+                } else {
+#pragma unroll
+                    for (int a = 0; a < kQ; a++) {
+                        const bool bb = s_t[hy - ey(a)][hx - ex(a)] & 2;
+#pragma unroll
+                        for (int k = 0; k < kNF; k++)
+                            q[9 * k + a] = __ldg(b + (bb ? P.off_plane[k * kQ + opp(a)] : P.off_pull[k * kQ + a]));
+                    }
+                }
             } else {
+                // own record: rho_k and the 8 offsets (the rest population and any bounce-back)
+                const float* rb = fin.rho + i;
+                const uint4* ob = fin.off + i;
 #pragma unroll
-                for (int a = 0; a < kQ; a++) {
-                    const bool bb = s_t[hy - ey(a)][hx - ex(a)] & 2;
+                for (int k = 0; k < kNF; k++) {
+                    const float rk = __ldg(rb + k * N);
+                    const uint4 w = __ldg(ob + k * N);
+                    const unsigned u[4] = {w.x, w.y, w.z, w.w};
+                    float d[kQ];
 #pragma unroll
-                    for (int k = 0; k < kNF; k++)
-                        q[9 * k + a] = __ldg(b + (bb ? P.off_plane[k * kQ + opp(a)] : P.off_pull[k * kQ + a]));
+                    for (int j = 0; j < 4; j++) {
+                        d[2 * j + 1] = dec16<STORE>((unsigned short)(u[j] & 0xffffu));
+                        d[2 * j + 2] = dec16<STORE>((unsigned short)(u[j] >> 16));
+                    }
+                    const float ds = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+                    q[9 * k] = wq(0) * rk - ds;
+#pragma unroll
+                    for (int a = 1; a < kQ; a++) {
+                        const bool bb = !fi && (s_t[hy - ey(a)][hx - ex(a)] & 2);
+                        if (bb) {
+                            q[9 * k + a] = wq(opp(a)) * rk + d[opp(a)];
+                        } else {
+                            const int o = P.off_pull16[k * kQ + a];
+                            q[9 * k + a] = wq(a) * __ldg(fin.rho + i + o) +
+                                           dec16<STORE>(__ldg(reinterpret_cast<const unsigned short*>(fin.off + i + o) + (a - 1)));
+                        }
+                    }
                 }
             }
             return;
         }
         if (t & 8) {
             // ghost beyond an open side: copy of the boundary-column node (zero gradient)
-            const Store<kStoreF32> st{fin, P.N};
+            const Store<STORE> st(fin, P.N);
             pull_global(P, st, type, x0 + hx - 3, y0 + hy - 3, q);
             return;
         }
-        const Store<kStoreF32> st{fin, P.N};
+        const Store<STORE> st(fin, P.N);
         const bool pn = s_par[hx];
         const int in = s_idx[hy][hx];
         bool inl = false, outl = false;
@@ -726,14 +760,24 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const int* 
     const float V2x = -b02 * n02x - b12 * n12x, V2y = -b02 * n02y - b12 * n12y;
     const float Cs[3] = {c0, c1, c2};
     const float Vx[3] = {V0x, V1x, V2x}, Vy[3] = {V0y, V1y, V2y};
-    float* o = fout + i;
+    if constexpr (STORE == kStoreF32) {
+        float* o = fout.f + i;
 #pragma unroll
-    for (int k = 0; k < kNF; k++) {
+        for (int k = 0; k < kNF; k++) {
 #pragma unroll
-        for (int a = 0; a < kQ; a++) {
-            const float v = Cs[k] * f[a] + wq(a) * (Vx[k] * (float)ex(a) + Vy[k] * (float)ey(a));
-            o[P.off_plane[k * kQ + a]] = v;
+            for (int a = 0; a < kQ; a++) {
+                const float v = Cs[k] * f[a] + wq(a) * (Vx[k] * (float)ex(a) + Vy[k] * (float)ey(a));
+                o[P.off_plane[k * kQ + a]] = v;
+            }
         }
+    } else {
+        float v[27];
+#pragma unroll
+        for (int k = 0; k < kNF; k++)
+#pragma unroll
+            for (int a = 0; a < kQ; a++)
+                v[9 * k + a] = Cs[k] * f[a] + wq(a) * (Vx[k] * (float)ex(a) + Vy[k] * (float)ey(a));
+        store_node<STORE>(fout, P.N, i, v);
     }
 }
 
@@ -744,28 +788,31 @@ __global__ void __launch_bounds__(TX* TY) k_step_f32(const Params P, const int* 
 // ------------------------------------------------------------------------------------------
 // Stored populations whose pull gives f_ak(x) = w_a rho_k(x): population a of node y is
 // w_a rho_k at its destination y + e_a (or at y itself when the destination is solid).
-__global__ void k_init_f32(const Params P, const double* __restrict__ rho,
-                           const uint8_t* __restrict__ type, float* __restrict__ f)
+template <int STORE>
+__global__ void k_init(const Params P, const double* __restrict__ rho,
+                       const uint8_t* __restrict__ type, const Pop f)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const int x = i % P.nx, y = i / P.nx;
     const bool solid = type[i] & 2;
+    float v[27];
 #pragma unroll
     for (int a = 0; a < kQ; a++) {
         const Loc d = locate(P, x + ex(a), y + ey(a));
 #pragma unroll
         for (int k = 0; k < kNF; k++) {
-            float v = 0.0f;
+            float val = 0.0f;
             if (!solid) {
                 if (d.kind == 1 || (d.kind == 0 && (type[d.idx] & 2)))
-                    v = wq(a) * (float)rho[(long long)k * P.N + i];
+                    val = wq(a) * (float)rho[(long long)k * P.N + i];
                 else if (d.kind == 0)
-                    v = wq(a) * (float)rho[(long long)relabel(k, d.par) * P.N + d.idx];
+                    val = wq(a) * (float)rho[(long long)relabel(k, d.par) * P.N + d.idx];
             }
-            f[(long long)(k * kQ + a) * P.N + i] = v;
+            v[9 * k + a] = val;
         }
     }
+    store_node<STORE>(f, P.N, i, v);
 }
 
 template <class S>
@@ -807,28 +854,31 @@ __global__ void k_get_state(const Params P, const S st, const uint8_t* __restric
 
 // stored populations whose pull reproduces the post-streaming state `post`: population a of
 // node y is post_a at its destination y + e_a, or post_opp(a) at y when that destination is solid
-__global__ void k_set_state_f32(const Params P, const double* __restrict__ post,
-                                const uint8_t* __restrict__ type, float* __restrict__ f)
+template <int STORE>
+__global__ void k_set_state(const Params P, const double* __restrict__ post,
+                            const uint8_t* __restrict__ type, const Pop f)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= P.N) return;
     const int x = i % P.nx, y = i / P.nx;
     const bool solid = type[i] & 2;
+    float v[27];
 #pragma unroll
     for (int a = 0; a < kQ; a++) {
         const Loc d = locate(P, x + ex(a), y + ey(a));
 #pragma unroll
         for (int k = 0; k < kNF; k++) {
-            float v = 0.0f;
+            float val = 0.0f;
             if (!solid) {
                 if (d.kind == 1 || (d.kind == 0 && (type[d.idx] & 2)))
-                    v = (float)post[(long long)(k * kQ + opp(a)) * P.N + i];
+                    val = (float)post[(long long)(k * kQ + opp(a)) * P.N + i];
                 else if (d.kind == 0)
-                    v = (float)post[(long long)(relabel(k, d.par) * kQ + a) * P.N + d.idx];
+                    val = (float)post[(long long)(relabel(k, d.par) * kQ + a) * P.N + d.idx];
             }
-            f[(long long)(k * kQ + a) * P.N + i] = v;
+            v[9 * k + a] = val;
         }
     }
+    store_node<STORE>(f, P.N, i, v);
 }
 
 constexpr int kDiagThreads = 256;
@@ -900,57 +950,97 @@ __global__ void k_diag_final(const int nb, const double* __restrict__ partials, 
 // ------------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------------
-void launch_wet(const Params& P, int nw, const int* widx, const double* wnrm, const float* wang,
-                const float* f, const uint8_t* type, double* Cw, cudaStream_t s)
+// call fn with the Store type of the storage format
+template <class Fn>
+void with_store(int store, const Pop& p, long long N, Fn fn)
 {
-    if (nw <= 0) return;
-    const Store<kStoreF32> st{f, P.N};
-    const long long threads = 4LL * nw;
-    k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw);
+    if (store == kStoreF32)
+        fn(Store<kStoreF32>(p, N));
+    else if (store == kStoreF16)
+        fn(Store<kStoreF16>(p, N));
+    else
+        fn(Store<kStoreBF16>(p, N));
 }
 
-void launch_wet_init(const Params& P, int nw, const int* widx, const float* f,
+void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
+                const float* wang, const Pop& f, const uint8_t* type, double* Cw, cudaStream_t s)
+{
+    if (nw <= 0) return;
+    const long long threads = 4LL * nw;
+    with_store(store, f, P.N, [&](auto st) {
+        k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw);
+    });
+}
+
+void launch_wet_init(int store, const Params& P, int nw, const int* widx, const Pop& f,
                      const uint8_t* type, double* Cw, cudaStream_t s)
 {
     if (nw <= 0) return;
-    const Store<kStoreF32> st{f, P.N};
-    k_wet_init<<<(nw + 127) / 128, 128, 0, s>>>(P, nw, widx, st, type, Cw);
+    with_store(store, f, P.N, [&](auto st) {
+        k_wet_init<<<(nw + 127) / 128, 128, 0, s>>>(P, nw, widx, st, type, Cw);
+    });
 }
 
-void launch_step_f32(const Params& P, const int* tiles, int ntiles, bool pure, const float* fin,
-                     float* fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
+template <int STORE>
+static void launch_step_t(const Params& P, const int* tiles, int ntiles, bool pure, const Pop& fin,
+                          const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
+{
+    if (pure)
+        k_step<kTX, kTY, true, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+    else
+        k_step<kTX, kTY, false, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+}
+
+void launch_step(int store, const Params& P, const int* tiles, int ntiles, bool pure, const Pop& fin,
+                 const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
 {
     if (ntiles <= 0) return;
-    if (pure)
-        k_step_f32<kTX, kTY, true><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+    if (store == kStoreF32)
+        launch_step_t<kStoreF32>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
+    else if (store == kStoreF16)
+        launch_step_t<kStoreF16>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
     else
-        k_step_f32<kTX, kTY, false><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+        launch_step_t<kStoreBF16>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
 }
 
-void launch_init_f32(const Params& P, const double* rho, const uint8_t* type, float* f,
-                     cudaStream_t s)
+void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,
+                 cudaStream_t s)
 {
-    k_init_f32<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, rho, type, f);
+    const unsigned nb = (unsigned)((P.N + 255) / 256);
+    if (store == kStoreF32)
+        k_init<kStoreF32><<<nb, 256, 0, s>>>(P, rho, type, f);
+    else if (store == kStoreF16)
+        k_init<kStoreF16><<<nb, 256, 0, s>>>(P, rho, type, f);
+    else
+        k_init<kStoreBF16><<<nb, 256, 0, s>>>(P, rho, type, f);
 }
 
-void launch_fields_f32(const Params& P, const float* f, const uint8_t* type, float* rho_out,
-                       cudaStream_t s)
+void launch_fields(int store, const Params& P, const Pop& f, const uint8_t* type, float* rho_out,
+                   cudaStream_t s)
 {
-    const Store<kStoreF32> st{f, P.N};
-    k_fields<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, st, type, rho_out);
+    with_store(store, f, P.N, [&](auto st) {
+        k_fields<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, st, type, rho_out);
+    });
 }
 
-void launch_get_state_f32(const Params& P, const float* f, const uint8_t* type, float* post,
-                          cudaStream_t s)
+void launch_get_state(int store, const Params& P, const Pop& f, const uint8_t* type, float* post,
+                      cudaStream_t s)
 {
-    const Store<kStoreF32> st{f, P.N};
-    k_get_state<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, st, type, post);
+    with_store(store, f, P.N, [&](auto st) {
+        k_get_state<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, st, type, post);
+    });
 }
 
-void launch_set_state_f32(const Params& P, const double* post, const uint8_t* type, float* f,
-                          cudaStream_t s)
+void launch_set_state(int store, const Params& P, const double* post, const uint8_t* type,
+                      const Pop& f, cudaStream_t s)
 {
-    k_set_state_f32<<<(unsigned)((P.N + 255) / 256), 256, 0, s>>>(P, post, type, f);
+    const unsigned nb = (unsigned)((P.N + 255) / 256);
+    if (store == kStoreF32)
+        k_set_state<kStoreF32><<<nb, 256, 0, s>>>(P, post, type, f);
+    else if (store == kStoreF16)
+        k_set_state<kStoreF16><<<nb, 256, 0, s>>>(P, post, type, f);
+    else
+        k_set_state<kStoreBF16><<<nb, 256, 0, s>>>(P, post, type, f);
 }
 
 int diag_blocks(const Params& P)
@@ -959,15 +1049,14 @@ int diag_blocks(const Params& P)
     return (int)(b < 1216 ? b : 1216);
 }
 
-void launch_diag_f32(const Params& P, const float* f, const uint8_t* type, const float* u,
-                     double* partials, double* out, cudaStream_t s)
+void launch_diag(int store, const Params& P, const Pop& f, const uint8_t* type, const float* u,
+                 double* partials, double* out, cudaStream_t s)
 {
-    const Store<kStoreF32> st{f, P.N};
     const int nb = diag_blocks(P);
-    k_diag<<<nb, kDiagThreads, 0, s>>>(P, st, type, u, partials);
+    with_store(store, f, P.N, [&](auto st) {
+        k_diag<<<nb, kDiagThreads, 0, s>>>(P, st, type, u, partials);
+    });
     k_diag_final<<<1, 32, 0, s>>>(nb, partials, out);
 }
-
-const char* step_kernel_name() { return "k_step_f32"; }
 
 }  // namespace lbm3k
