@@ -126,6 +126,26 @@ int lbm3_wall_values(lbm3* h, double* c, int32_t cap);
 int lbm3_get_state(lbm3* h, double* f_post, double* wall_c);
 int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c);
 
+/* Replace the wall-angle triples (theta_01, theta_20, theta_12) in degrees of every C_SB node,
+ * host [n_wall][3] in lbm3_wall_nodes order (each in (0, 180)). */
+int lbm3_set_wall_angles(lbm3* h, const double* angles_deg);
+
+/* Replace the Zou-He inlet velocity (|u_in| < 0.3; LBM3_BC_ZOUHE only). */
+int lbm3_set_inflow(lbm3* h, double u_in);
+
+/* Adjoint (reverse-mode) gradient.  Runs nsteps timesteps from the current state, evaluates
+ * J = sum_x x rho_0(x) / sum_x rho_0(x), the x-centroid of fluid 0 over the post-streaming fluid
+ * nodes of the final state, and returns dJ/d(theta_01, theta_20, theta_12) for every C_SB node
+ * (host [n_wall][3], lbm3_wall_nodes order) and dJ/du_in (0 unless LBM3_BC_ZOUHE).  The states
+ * at every checkpoint_every-th step are kept on the device; each segment is recomputed forward
+ * by the step kernels and then traversed backward by the adjoint kernels (vector-Jacobian
+ * products of Eq.1-16, 21, 22 and the characteristic lines, FP32 with FP64 accumulators).
+ * FP32 storage only, not with LBM3_BC_MODPER.  On return the simulation holds its final state.
+ * Device memory: about nsteps / checkpoint_every + checkpoint_every states (132 B per node each)
+ * plus ~300 B per node of work arrays, allocated and released by the call.  Synchronises. */
+int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, double* J_out,
+                          double* dJ_dangles, double* dJ_du);
+
 /* Size facts: out[0] = fluid nodes, out[1] = C_SB nodes, out[2] = algorithmic HBM bytes of the
  * fused step per timestep (216 B per fluid node + 1 class byte per node), out[3] = fused-step
  * launches per timestep, out[4] = wetting launches per timestep, out[5] = device bytes held by

@@ -1,0 +1,949 @@
+// lbm3_adjoint.cu -- reverse-mode (adjoint) kernels of one timestep of the three-phase MRT
+// colour-gradient step with characteristic-line wetting (arXiv:2102.04709, Section II), for the
+// gradient of an objective of the final state with respect to the wall-angle triples of
+// Eq.(17)/(21) and the Zou-He inflow velocity.
+//
+// The forward state of each step (stored populations + lagged wall values) comes from the
+// production kernels.  The adjoint first recomputes the intermediates of that step, unfused, into
+// global arrays (post-streaming populations, phase fields, wall values with the decisions of the
+// characteristic lines, gradients, stress, force), then applies the vector-Jacobian products in
+// reverse order:  collision + recolouring (Eq.1-15), divergence (Eq.10, 12), stress (Eq.10),
+// gradients (Eq.12), wetting (Eq.21, 22, characteristic lines), fractions, pull-streaming with
+// halfway bounce-back and Zou-He (Eq.16).  All in FP32, gradient accumulators in FP64.
+// Supported: periodic, wall and Zou-He x boundaries (not the modified periodic seam).
+//
+// Padded arrays carry one ghost column on each side of the grid (index y * (nx + 2) + x + 1),
+// used for the zero-gradient copies beyond the open Zou-He columns.
+#include <cmath>
+#include <utility>
+
+#include "lbm3_common.cuh"
+#include "lbm3_device.cuh"
+
+namespace lbm3k {
+
+namespace {
+
+struct Adj {
+    int nxp;  // nx + 2
+    // forward intermediates
+    float* fpost;  // [27][N]
+    float* C;      // [3][NP]
+    float* rho;    // [NP]
+    float* g;      // [6][NP]   (dC0/dx, dC0/dy, dC1/dx, ...)
+    float* T;      // [3][NP]
+    float* F;      // [2][N]
+    // wetting decisions, lane = 2 k + side
+    int* wkind;    // [4][Nw]
+    int* wa;       // [4][Nw] in-domain node index of the first bracketing node
+    int* wb;       // [4][Nw]
+    float* wfr;    // [4][Nw]
+    float* wdfr;   // [4][Nw] d fr / d theta_k (deg)
+    float* wcd;    // [4][Nw]
+    float* wth;    // [2][Nw] theta_k
+    float* wraw;   // [2][Nw] C_P of fluid k before the normalisation
+    int* wsel;     // [2][Nw] side chosen by Eq.(22)
+    // adjoint fields
+    float* l_fpost;  // [27][N]
+    float* l_F;      // [2][N]
+    float* l_g;      // [6][NP]
+    float* l_T;      // [3][NP]
+    float* l_C;      // [3][NP]
+    float* l_rho;    // [NP]
+    float* l_fs;     // [27][N] adjoint of the stored populations
+    float* l_cw;     // [3][N]  adjoint of the lagged wall values (input, from the next step)
+    float* l_cw2;    // [3][N]  adjoint of the lagged wall values (output, for the previous step)
+    double* d_ang;   // [3][Nw] dJ/d(theta_01, theta_20, theta_12)
+    double* d_u;     // [1] dJ/dU
+};
+
+__device__ __forceinline__ int pad(const Adj& A, int x, int y) { return y * A.nxp + x + 1; }
+
+// position of C / rho seen from an unwrapped lattice position: kind 0 = an in-domain node
+// (padded index), 1 = solid beyond a wall side; beyond an open side: the boundary-column node
+__device__ __forceinline__ int cpos(const Params& P, const Adj& A, int X, int Y, int& kind)
+{
+    const Loc L = locate(P, X, Y);
+    kind = L.kind == 1 ? 1 : 0;
+    if (kind) return 0;
+    return pad(A, L.idx % P.nx, L.idx / P.nx);
+}
+
+// position of T seen from an unwrapped lattice position: the ghost columns are their own slots
+__device__ __forceinline__ int tpos(const Params& P, const Adj& A, int X, int Y)
+{
+    if (P.bc_x == kZouHe && (X == -1 || X == P.nx)) {
+        const Loc L = locate(P, 0, Y);
+        return pad(A, X, L.idx / P.nx);
+    }
+    const Loc L = locate(P, X, Y);
+    return pad(A, L.idx % P.nx, L.idx / P.nx);
+}
+
+// ------------------------------------------------------------------------------------------
+// forward intermediates
+// ------------------------------------------------------------------------------------------
+// A1: post-streaming populations, densities and fractions (fluid nodes and ghost columns)
+__global__ void a_dens(const Params P, const Adj A, const float* __restrict__ fs,
+                       const uint8_t* __restrict__ type)
+{
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, y = blockIdx.y;
+    if (gx > P.nx || y >= P.ny) return;
+    const int p = pad(A, gx, y);
+    const bool ghost = gx < 0 || gx >= P.nx;
+    if (ghost && P.bc_x != kZouHe) return;
+    const int x = gx < 0 ? 0 : (gx >= P.nx ? P.nx - 1 : gx);
+    const int i = y * P.nx + x;
+    const uint8_t t = type[i];
+    if (t & 2) {
+        A.rho[p] = (t & 3) == kSB ? 1.0f : 0.0f;
+        if ((t & 3) == kSI)
+            for (int k = 0; k < kNF; k++) A.C[k * (P.ny * A.nxp) + p] = 0.0f;
+        return;
+    }
+    float q[27];
+    const Store<kStoreF32> st(fs, P.N);
+    pull_global(P, st, type, x, y, q);
+    float r[kNF];
+    for (int k = 0; k < kNF; k++) {
+        float s = 0.f;
+        for (int a = 0; a < kQ; a++) s += q[9 * k + a];
+        r[k] = s;
+    }
+    const float rho = r[0] + r[1] + r[2];
+    for (int k = 0; k < kNF; k++) A.C[k * (P.ny * A.nxp) + p] = r[k] / rho;
+    A.rho[p] = rho;
+    if (!ghost)
+        for (int j = 0; j < 27; j++) A.fpost[(long long)j * P.N + i] = q[j];
+}
+
+// A2: wetting with its decisions, 4 lanes per C_SB node (the same computation as k_wet)
+__global__ void a_wet(const Params P, const Adj A, int nw, const int* __restrict__ widx,
+                      const double* __restrict__ wnrm, const float* __restrict__ wang,
+                      const float* __restrict__ fs, const uint8_t* __restrict__ type,
+                      const double* __restrict__ cw_lag)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = g >> 2, lane = g & 3;
+    const int k = lane >> 1, side = lane & 1;
+    const bool valid = w < nw;
+    const Store<kStoreF32> st(fs, P.N);
+    int i = 0, px = 0, py = 0;
+    double th = 90.0, dfr = 0.0;
+    Crossing cr{0, 0, 0, 0, 0, 0.0};
+    if (valid) {
+        i = widx[w];
+        px = i % P.nx;
+        py = i / P.nx;
+        const double Cr = cw_lag[i], Cg = cw_lag[P.N + i], Cb = cw_lag[2 * P.N + i];
+        const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
+        th = k == 0 ? local_angle(Cb, 180.0 - t_br, Cg, t_rg) : local_angle(Cb, t_gb, Cr, 180.0 - t_rg);
+        const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
+        const double dev = fabs(90.0 - th);
+        const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
+        const double sg = side ? -1.0 : 1.0;
+        double sn, cs;
+        sincos(phi, &sn, &cs);
+        const double dx = cs * nx_ - sg * sn * ny_, dy = cs * ny_ + sg * sn * nx_;
+        cr = characteristic_line<Store<kStoreF32>>(P, type, px, py, dx, dy);
+        if (cr.kind == 2 && dev >= kPhiSnap) {
+            // d(position along the crossed line)/d phi, then d phi / d theta_k
+            const double ddx = -sn * nx_ - sg * cs * ny_, ddy = -sn * ny_ + sg * cs * nx_;
+            double ds;
+            if (cr.ax == cr.bx)
+                ds = (double)(cr.ax - px) * (ddy * dx - dy * ddx) / (dx * dx);
+            else
+                ds = (double)(cr.ay - py) * (ddx * dy - dx * ddy) / (dy * dy);
+            dfr = ds * (90.0 - th > 0 ? -1.0 : 1.0) * (M_PI / 180.0);
+        }
+    }
+    double ca = 0.0, cb = 0.0;
+    if (valid && cr.kind >= 1) ca = node_C(P, st, type, cr.ax, cr.ay, k);
+    if (valid && cr.kind == 2) cb = node_C(P, st, type, cr.bx, cr.by, k);
+    if (valid && cr.kind == 0) ca = neighbour_mean(P, st, type, px, py, k);
+    const double cd = cr.kind == 2 ? ca + cr.fr * (cb - ca) : ca;
+    const double other = __shfl_xor_sync(0xffffffffu, cd, 1);
+    const bool takes_max = th <= 90.0;
+    const double cp = takes_max ? fmax(cd, other) : fmin(cd, other);
+    // the chosen side (ties: side 0)
+    const int sel = (takes_max ? (cd > other || (cd == other && side == 0)) : (cd < other || (cd == other && side == 0))) ? side : 1 - side;
+    const double cg = __shfl_xor_sync(0xffffffffu, cp, 2);
+    if (valid) {
+        const int j = lane * nw + w;
+        A.wkind[j] = cr.kind;
+        int kk;
+        A.wa[j] = cr.kind >= 1 ? cpos(P, A, cr.ax, cr.ay, kk) : 0;
+        A.wb[j] = cr.kind == 2 ? cpos(P, A, cr.bx, cr.by, kk) : 0;
+        A.wfr[j] = (float)cr.fr;
+        A.wdfr[j] = (float)dfr;
+        A.wcd[j] = (float)cd;
+        if (side == 0) {
+            A.wth[k * nw + w] = (float)th;
+            A.wraw[k * nw + w] = (float)cp;
+            A.wsel[k * nw + w] = sel;
+        }
+        if (lane == 0) {
+            double c0 = fmin(fmax(cp, 0.0), 1.0), c1 = fmin(fmax(cg, 0.0), 1.0);
+            const double s = c0 + c1;
+            if (s > 1.0) {
+                c0 /= s;
+                c1 /= s;
+            }
+            const int p = pad(A, px, py);
+            const int NP = P.ny * A.nxp;
+            A.C[p] = (float)c0;
+            A.C[NP + p] = (float)c1;
+            A.C[2 * NP + p] = (float)fmax(0.0, 1.0 - c0 - c1);
+        }
+    }
+}
+
+__device__ __forceinline__ bool is_active(const Params& P, const Adj& A, const uint8_t* type, int gx,
+                                          int y, int& cls)
+{
+    // fluid or C_SB node in the domain, or a ghost column of an open side
+    if (gx < 0 || gx >= P.nx) {
+        cls = kFI;
+        return P.bc_x == kZouHe;
+    }
+    cls = type[y * P.nx + gx] & 3;
+    return cls != kSI;
+}
+
+// gather of the 9-point stencil of C_k around the position (gx, gy) (in-domain or ghost);
+// v[a] and the padded position src[a] the value came from (C_SI / wall-side neighbours of a
+// C_SB centre take the centre's own value)
+__device__ __forceinline__ void stencil_C(const Params& P, const Adj& A, const uint8_t* type, int gx,
+                                          int gy, int cls, int k, float v[kQ], int src[kQ])
+{
+    const int NP = P.ny * A.nxp;
+    int kind;
+    const int pc = cpos(P, A, gx, gy, kind);
+    for (int a = 0; a < kQ; a++) {
+        int kd;
+        int q = cpos(P, A, gx + ex(a), gy + ey(a), kd);
+        if (cls == kSB && a > 0) {
+            bool si = kd == 1;
+            if (!si) {
+                const int qx = q % A.nxp - 1, qy = q / A.nxp;
+                si = (type[qy * P.nx + qx] & 3) == kSI;
+            }
+            if (si) q = pc;
+        }
+        src[a] = q;
+        v[a] = A.C[k * NP + q];
+    }
+}
+
+// A3: gradients (Eq.12) and the Eq.(10) stress at fluid, C_SB and ghost positions
+__global__ void a_grad_stress(const Params P, const Adj A, const uint8_t* __restrict__ type,
+                              const float sig01, const float sig02, const float sig12)
+{
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, y = blockIdx.y;
+    if (gx > P.nx || y >= P.ny) return;
+    int cls;
+    if (!is_active(P, A, type, gx, y, cls)) return;
+    const int NP = P.ny * A.nxp;
+    const int p = pad(A, gx, y);
+    float c[kNF], gxk[kNF], gyk[kNF];
+    for (int k = 0; k < kNF; k++) {
+        float v[kQ];
+        int src[kQ];
+        stencil_C(P, A, type, gx, y, cls, k, v, src);
+        c[k] = v[0];
+        gxk[k] = (1.0f / 3.0f) * (v[1] - v[3]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[8] - v[6]));
+        gyk[k] = (1.0f / 3.0f) * (v[2] - v[4]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[6] - v[8]));
+        A.g[(2 * k) * NP + p] = gxk[k];
+        A.g[(2 * k + 1) * NP + p] = gyk[k];
+    }
+    const float rho = A.rho[p];
+    float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
+    const float rho2 = rho * rho;
+    pair_stress(sig01, c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
+    pair_stress(sig02, c[0], c[2], gxk[0], gyk[0], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+    pair_stress(sig12, c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+    A.T[p] = Txx;
+    A.T[NP + p] = Txy;
+    A.T[2 * NP + p] = Tyy;
+}
+
+// A4: force F = div T at fluid nodes
+__global__ void a_force(const Params P, const Adj A, const uint8_t* __restrict__ type)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int i = y * P.nx + x;
+    if (type[i] & 2) return;
+    const int NP = P.ny * A.nxp;
+    float Fx = 0.f, Fy = 0.f;
+    for (int a = 1; a < kQ; a++) {
+        const int q = tpos(P, A, x + ex(a), y + ey(a));
+        const float c = 3.0f * wq(a);
+        Fx += c * (A.T[q] * ex(a) + A.T[NP + q] * ey(a));
+        Fy += c * (A.T[NP + q] * ex(a) + A.T[2 * NP + q] * ey(a));
+    }
+    A.F[i] = Fx;
+    A.F[P.N + i] = Fy;
+}
+
+// ------------------------------------------------------------------------------------------
+// reverse
+// ------------------------------------------------------------------------------------------
+// B1: VJP of the MRT collision with forcing and the recolouring at a fluid node
+__global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict__ type)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int i = y * P.nx + x;
+    if (type[i] & 2) return;
+    const int NP = P.ny * A.nxp;
+    const int p = pad(A, x, y);
+    // ---- forward recompute ----
+    float q[27], f[kQ], r[kNF];
+    for (int j = 0; j < 27; j++) q[j] = A.fpost[(long long)j * P.N + i];
+    for (int k = 0; k < kNF; k++) {
+        float s = 0.f;
+        for (int a = 0; a < kQ; a++) s += q[9 * k + a];
+        r[k] = s;
+    }
+    for (int a = 0; a < kQ; a++) f[a] = q[a] + q[9 + a] + q[18 + a];
+    const float rho = r[0] + r[1] + r[2];
+    const float Fx = A.F[i], Fy = A.F[P.N + i];
+    float g[6];
+    for (int j = 0; j < 6; j++) g[j] = A.g[j * NP + p];
+    float C[kNF];
+    for (int k = 0; k < kNF; k++) C[k] = r[k] / rho;
+    // moments
+    const float e = -4.f * f[0] - (f[1] + f[2] + f[3] + f[4]) + 2.f * (f[5] + f[6] + f[7] + f[8]);
+    const float eps = 4.f * f[0] - 2.f * (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
+    const float jx = f[1] - f[3] + f[5] - f[6] - f[7] + f[8];
+    const float qx = -2.f * (f[1] - f[3]) + f[5] - f[6] - f[7] + f[8];
+    const float jy = f[2] - f[4] + f[5] + f[6] - f[7] - f[8];
+    const float qy = -2.f * (f[2] - f[4]) + f[5] + f[6] - f[7] - f[8];
+    const float pxx = f[1] - f[2] + f[3] - f[4];
+    const float pxy = f[5] - f[6] + f[7] - f[8];
+    const float ux = (jx + 0.5f * Fx) / rho, uy = (jy + 0.5f * Fy) / rho;
+    const float u2 = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
+    const float D = r[0] * P.inv_nu0 + r[1] * P.inv_nu1 + r[2] * P.inv_nu2;
+    const float s1 = D / (0.5f * D + 3.0f);
+    const float s4 = 8.0f * (2.0f - s1) / (8.0f - s1);
+    const float h1 = 1.0f - 0.5f * s1, h4 = 1.0f - 0.5f * s4;
+    const float XE = e + 2.f * rho - 3.f * rho * u2, XEps = eps - rho + 3.f * rho * u2;
+    const float Xqx = qx + rho * ux, Xqy = qy + rho * uy;
+    const float Xpxx = pxx - rho * (ux * ux - uy * uy), Xpxy = pxy - rho * ux * uy;
+    const float dE = -s1 * XE + h1 * 6.f * uF, dEps = -s1 * XEps - h1 * 6.f * uF;
+    const float dqx = -s4 * Xqx - h4 * Fx, dqy = -s4 * Xqy - h4 * Fy;
+    const float dpxx = -s1 * Xpxx + h1 * 2.f * (ux * Fx - uy * Fy);
+    const float dpxy = -s1 * Xpxy + h1 * (ux * Fy + uy * Fx);
+    // f_dag = f + M^-1 dm
+    float fd[kQ];
+    {
+        const float c0 = (dEps - dE) / 9.f;
+        const float ca = -dE / 36.f - dEps / 18.f, cd = dE / 18.f + dEps / 36.f;
+        const float X1 = (Fx - dqx) / 6.f, Y1 = (Fy - dqy) / 6.f;
+        const float X2 = Fx / 6.f + dqx / 12.f, Y2 = Fy / 6.f + dqy / 12.f;
+        const float P4 = 0.25f * dpxx, Q4 = 0.25f * dpxy;
+        fd[0] = f[0] + c0;
+        fd[1] = f[1] + ca + X1 + P4;
+        fd[2] = f[2] + ca + Y1 - P4;
+        fd[3] = f[3] + ca - X1 + P4;
+        fd[4] = f[4] + ca - Y1 - P4;
+        fd[5] = f[5] + cd + X2 + Y2 + Q4;
+        fd[6] = f[6] + cd - X2 + Y2 - Q4;
+        fd[7] = f[7] + cd - X2 - Y2 + Q4;
+        fd[8] = f[8] + cd + X2 - Y2 - Q4;
+    }
+    // normals
+    const float gg[3][2] = {{g[0], g[1]}, {g[2], g[3]}, {g[4], g[5]}};
+    const int pk[3] = {0, 0, 1}, pl[3] = {1, 2, 2};
+    float nxp_[3], nyp_[3], Gx[3], Gy[3], Gn[3];
+    bool act[3];
+    for (int m = 0; m < 3; m++) {
+        const int k = pk[m], l = pl[m];
+        Gx[m] = C[l] * gg[k][0] - C[k] * gg[l][0];
+        Gy[m] = C[l] * gg[k][1] - C[k] * gg[l][1];
+        const float G2 = Gx[m] * Gx[m] + Gy[m] * Gy[m];
+        act[m] = G2 > 1e-24f;
+        Gn[m] = act[m] ? sqrtf(G2) : 1.f;
+        nxp_[m] = act[m] ? Gx[m] / Gn[m] : 0.f;
+        nyp_[m] = act[m] ? Gy[m] / Gn[m] : 0.f;
+    }
+    const float gX[3] = {P.g01, P.g02, P.g12};
+    const float T3 = 35.f * r[0] * r[1] * r[2] / (rho * rho * rho);
+    const float trip = fminf(T3, 1.0f);
+    float b[3];
+    for (int m = 0; m < 3; m++) b[m] = P.beta0 * (1.f + trip * gX[m]) * r[pk[m]] * r[pl[m]] / rho;
+
+    // ---- reverse ----
+    float lo[27];
+    for (int j = 0; j < 27; j++) lo[j] = A.l_fs[(long long)j * P.N + i];
+    float lC[kNF] = {0, 0, 0}, lfd[kQ] = {0}, lV[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int k = 0; k < kNF; k++)
+        for (int a = 0; a < kQ; a++) {
+            const float l = lo[9 * k + a];
+            lC[k] += l * fd[a];
+            lfd[a] += l * C[k];
+            lV[k][0] += l * wq(a) * ex(a);
+            lV[k][1] += l * wq(a) * ey(a);
+        }
+    // V0 = b01 n01 + b02 n02, V1 = -b01 n01 + b12 n12, V2 = -b02 n02 - b12 n12
+    const float dV[3][2] = {{lV[0][0] - lV[1][0], lV[0][1] - lV[1][1]},
+                            {lV[0][0] - lV[2][0], lV[0][1] - lV[2][1]},
+                            {lV[1][0] - lV[2][0], lV[1][1] - lV[2][1]}};
+    float lb[3], lg[3][2] = {{0, 0}, {0, 0}, {0, 0}};
+    for (int m = 0; m < 3; m++) {
+        lb[m] = dV[m][0] * nxp_[m] + dV[m][1] * nyp_[m];
+        if (!act[m]) continue;
+        const float lnx = b[m] * dV[m][0], lny = b[m] * dV[m][1];
+        const float dot = nxp_[m] * lnx + nyp_[m] * lny;
+        const float lGx = (lnx - nxp_[m] * dot) / Gn[m], lGy = (lny - nyp_[m] * dot) / Gn[m];
+        const int k = pk[m], l = pl[m];
+        lg[k][0] += C[l] * lGx;
+        lg[k][1] += C[l] * lGy;
+        lg[l][0] -= C[k] * lGx;
+        lg[l][1] -= C[k] * lGy;
+        lC[l] += gg[k][0] * lGx + gg[k][1] * lGy;
+        lC[k] -= gg[l][0] * lGx + gg[l][1] * lGy;
+    }
+    // b_m = beta0 (1 + trip g_m) r_k r_l / rho
+    float lr[kNF] = {0, 0, 0}, lrho = 0.f, ltrip = 0.f;
+    for (int m = 0; m < 3; m++) {
+        const int k = pk[m], l = pl[m];
+        const float base = P.beta0 * (1.f + trip * gX[m]);
+        ltrip += lb[m] * P.beta0 * gX[m] * r[k] * r[l] / rho;
+        lr[k] += lb[m] * base * r[l] / rho;
+        lr[l] += lb[m] * base * r[k] / rho;
+        lrho -= lb[m] * b[m] / rho;
+    }
+    if (T3 < 1.0f) {
+        lr[0] += ltrip * 35.f * r[1] * r[2] / (rho * rho * rho);
+        lr[1] += ltrip * 35.f * r[0] * r[2] / (rho * rho * rho);
+        lr[2] += ltrip * 35.f * r[0] * r[1] / (rho * rho * rho);
+        lrho -= ltrip * 3.f * T3 / rho;
+    }
+    // collision: f_dag = f + M^-1 dm
+    float lf[kQ];
+    for (int a = 0; a < kQ; a++) lf[a] = lfd[a];
+    // lambda of the moment changes = (M^-1)^T lfd
+    const float ldE = (-lfd[0] / 9.f) + (-(lfd[1] + lfd[2] + lfd[3] + lfd[4]) / 36.f) + ((lfd[5] + lfd[6] + lfd[7] + lfd[8]) / 18.f);
+    const float ldEps = (lfd[0] / 9.f) + (-(lfd[1] + lfd[2] + lfd[3] + lfd[4]) / 18.f) + ((lfd[5] + lfd[6] + lfd[7] + lfd[8]) / 36.f);
+    const float lX1 = (lfd[1] - lfd[3]) / 6.f, lY1 = (lfd[2] - lfd[4]) / 6.f;
+    const float lX2 = (lfd[5] - lfd[6] - lfd[7] + lfd[8]), lY2 = (lfd[5] + lfd[6] - lfd[7] - lfd[8]);
+    // X1 = (Fx - dqx)/6, X2 = Fx/6 + dqx/12
+    const float ldqx = -lX1 + lX2 / 12.f, ldqy = -lY1 + lY2 / 12.f;
+    float lFx = lX1 + lX2 / 6.f, lFy = lY1 + lY2 / 6.f;
+    const float ldpxx = 0.25f * (lfd[1] - lfd[2] + lfd[3] - lfd[4]);
+    const float ldpxy = 0.25f * (lfd[5] - lfd[6] + lfd[7] - lfd[8]);
+    // moment changes -> moments, rho, u, F, s1, s4
+    const float le = -s1 * ldE, leps = -s1 * ldEps, lqx = -s4 * ldqx, lqy = -s4 * ldqy;
+    const float lpxx = -s1 * ldpxx, lpxy = -s1 * ldpxy;
+    lrho += -s1 * (2.f - 3.f * u2) * ldE - s1 * (-1.f + 3.f * u2) * ldEps - s4 * ux * ldqx - s4 * uy * ldqy +
+            s1 * (ux * ux - uy * uy) * ldpxx + s1 * ux * uy * ldpxy;
+    float lux = (6.f * s1 * rho * ux + 6.f * h1 * Fx) * ldE + (-6.f * s1 * rho * ux - 6.f * h1 * Fx) * ldEps -
+                s4 * rho * ldqx + (2.f * s1 * rho * ux + 2.f * h1 * Fx) * ldpxx + (s1 * rho * uy + h1 * Fy) * ldpxy;
+    float luy = (6.f * s1 * rho * uy + 6.f * h1 * Fy) * ldE + (-6.f * s1 * rho * uy - 6.f * h1 * Fy) * ldEps -
+                s4 * rho * ldqy + (-2.f * s1 * rho * uy - 2.f * h1 * Fy) * ldpxx + (s1 * rho * ux + h1 * Fx) * ldpxy;
+    lFx += 6.f * h1 * ux * ldE - 6.f * h1 * ux * ldEps - h4 * ldqx + 2.f * h1 * ux * ldpxx + h1 * uy * ldpxy;
+    lFy += 6.f * h1 * uy * ldE - 6.f * h1 * uy * ldEps - h4 * ldqy - 2.f * h1 * uy * ldpxx + h1 * ux * ldpxy;
+    float ls1 = (-XE - 3.f * uF) * ldE + (-XEps + 3.f * uF) * ldEps + (-Xpxx - (ux * Fx - uy * Fy)) * ldpxx +
+                (-Xpxy - 0.5f * (ux * Fy + uy * Fx)) * ldpxy;
+    const float ls4 = (-Xqx + 0.5f * Fx) * ldqx + (-Xqy + 0.5f * Fy) * ldqy;
+    ls1 += ls4 * (-48.f / ((8.f - s1) * (8.f - s1)));
+    const float lD = ls1 * 3.f / ((0.5f * D + 3.f) * (0.5f * D + 3.f));
+    lr[0] += lD * P.inv_nu0;
+    lr[1] += lD * P.inv_nu1;
+    lr[2] += lD * P.inv_nu2;
+    // u = (j + F/2)/rho
+    const float ljx = lux / rho, ljy = luy / rho;
+    lFx += 0.5f * lux / rho;
+    lFy += 0.5f * luy / rho;
+    lrho -= (lux * ux + luy * uy) / rho;
+    // moments -> populations (rows of M)
+    for (int a = 0; a < kQ; a++) {
+        const int e2 = ex(a) * ex(a) + ey(a) * ey(a);
+        const float me = (float)(-4 + 3 * e2);
+        const float meps = e2 == 0 ? 4.f : (e2 == 1 ? -2.f : 1.f);
+        const float mqx = (float)(ex(a) * (3 * e2 - 5)), mqy = (float)(ey(a) * (3 * e2 - 5));
+        const float mpxx = (float)(ex(a) * ex(a) - ey(a) * ey(a)), mpxy = (float)(ex(a) * ey(a));
+        lf[a] += le * me + leps * meps + ljx * ex(a) + lqx * mqx + ljy * ey(a) + lqy * mqy + lpxx * mpxx +
+                 lpxy * mpxy + lrho;
+    }
+    // C_k = r_k / rho
+    float sc = 0.f;
+    for (int k = 0; k < kNF; k++) sc += lC[k] * C[k];
+    for (int k = 0; k < kNF; k++) lr[k] += (lC[k] - sc) / rho;
+    for (int k = 0; k < kNF; k++)
+        for (int a = 0; a < kQ; a++) A.l_fpost[(long long)(9 * k + a) * P.N + i] = lf[a] + lr[k];
+    A.l_F[i] = lFx;
+    A.l_F[P.N + i] = lFy;
+    for (int k = 0; k < kNF; k++) {
+        A.l_g[(2 * k) * NP + p] += lg[k][0];
+        A.l_g[(2 * k + 1) * NP + p] += lg[k][1];
+    }
+}
+
+// B2: adjoint of the divergence: lambda_T at fluid / C_SB / ghost positions
+__global__ void b_div(const Params P, const Adj A, const uint8_t* __restrict__ type)
+{
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, y = blockIdx.y;
+    if (gx > P.nx || y >= P.ny) return;
+    int cls;
+    if (!is_active(P, A, type, gx, y, cls)) return;
+    const int NP = P.ny * A.nxp;
+    const int p = pad(A, gx, y);
+    float lxx = 0.f, lxy = 0.f, lyy = 0.f;
+    for (int a = 1; a < kQ; a++) {
+        // the fluid node q = p - e_a looked up T at p in direction a
+        const Loc L = locate(P, gx - ex(a), y - ey(a));
+        if (L.kind != 0 || (type[L.idx] & 2)) continue;
+        const int qx = L.idx % P.nx, qy = L.idx / P.nx;
+        if (tpos(P, A, qx + ex(a), qy + ey(a)) != p) continue;
+        const float c = 3.0f * wq(a);
+        const float lFx = A.l_F[L.idx], lFy = A.l_F[P.N + L.idx];
+        lxx += c * ex(a) * lFx;
+        lxy += c * (ey(a) * lFx + ex(a) * lFy);
+        lyy += c * ey(a) * lFy;
+    }
+    A.l_T[p] = lxx;
+    A.l_T[NP + p] = lxy;
+    A.l_T[2 * NP + p] = lyy;
+}
+
+// VJP of one pair's stress sigma A (|G|^2 I - G G)/|G|
+__device__ __forceinline__ void pair_stress_vjp(float sig, float ck, float cl, float gkx, float gky,
+                                                float glx, float gly, float rho, const float lT[3],
+                                                float& lck, float& lcl, float lgk[2], float lgl[2],
+                                                float& lrho)
+{
+    const float Gx = cl * gkx - ck * glx, Gy = cl * gky - ck * gly;
+    const float G2 = Gx * Gx + Gy * Gy;
+    if (!(G2 > 1e-24f)) return;
+    const float Gn = sqrtf(G2), iG = 1.0f / Gn, iG3 = iG * iG * iG;
+    const float Ar = 1e6f * ck * cl * rho * rho;
+    const float A = fminf(fmaxf(Ar, 0.0f), 1.0f);
+    const float sA = sig * A;
+    // T = sA (Gy^2, -Gx Gy, Gx^2) / |G|
+    const float dTxx_dGx = -sA * Gy * Gy * Gx * iG3, dTxx_dGy = sA * (2.f * Gy * iG - Gy * Gy * Gy * iG3);
+    const float dTxy_dGx = -sA * (Gy * iG - Gx * Gx * Gy * iG3), dTxy_dGy = -sA * (Gx * iG - Gx * Gy * Gy * iG3);
+    const float dTyy_dGx = sA * (2.f * Gx * iG - Gx * Gx * Gx * iG3), dTyy_dGy = -sA * Gx * Gx * Gy * iG3;
+    const float lGx = lT[0] * dTxx_dGx + lT[1] * dTxy_dGx + lT[2] * dTyy_dGx;
+    const float lGy = lT[0] * dTxx_dGy + lT[1] * dTxy_dGy + lT[2] * dTyy_dGy;
+    if (Ar > 0.0f && Ar < 1.0f) {
+        const float lA = sig * (Gy * Gy * lT[0] - Gx * Gy * lT[1] + Gx * Gx * lT[2]) * iG;
+        lck += lA * 1e6f * cl * rho * rho;
+        lcl += lA * 1e6f * ck * rho * rho;
+        lrho += lA * 2e6f * ck * cl * rho;
+    }
+    lgk[0] += cl * lGx;
+    lgk[1] += cl * lGy;
+    lgl[0] -= ck * lGx;
+    lgl[1] -= ck * lGy;
+    lcl += gkx * lGx + gky * lGy;
+    lck -= glx * lGx + gly * lGy;
+}
+
+// B3: adjoint of the stress (local part) and of the gradient stencil (scatter into lambda_C)
+__global__ void b_stress_grad(const Params P, const Adj A, const uint8_t* __restrict__ type,
+                              const float sig01, const float sig02, const float sig12)
+{
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, y = blockIdx.y;
+    if (gx > P.nx || y >= P.ny) return;
+    int cls;
+    if (!is_active(P, A, type, gx, y, cls)) return;
+    const int NP = P.ny * A.nxp;
+    const int p = pad(A, gx, y);
+    int kind;
+    const int pc = cpos(P, A, gx, y, kind);  // where this position's own C lives
+    float c[kNF], g[kNF][2], lc[kNF] = {0, 0, 0}, lg[kNF][2];
+    for (int k = 0; k < kNF; k++) {
+        c[k] = A.C[k * NP + pc];
+        g[k][0] = A.g[(2 * k) * NP + p];
+        g[k][1] = A.g[(2 * k + 1) * NP + p];
+        lg[k][0] = A.l_g[(2 * k) * NP + p];
+        lg[k][1] = A.l_g[(2 * k + 1) * NP + p];
+    }
+    const float lT[3] = {A.l_T[p], A.l_T[NP + p], A.l_T[2 * NP + p]};
+    float lrho = 0.f;
+    const float rho = A.rho[pc];
+    pair_stress_vjp(sig01, c[0], c[1], g[0][0], g[0][1], g[1][0], g[1][1], rho, lT, lc[0], lc[1], lg[0], lg[1], lrho);
+    pair_stress_vjp(sig02, c[0], c[2], g[0][0], g[0][1], g[2][0], g[2][1], rho, lT, lc[0], lc[2], lg[0], lg[2], lrho);
+    pair_stress_vjp(sig12, c[1], c[2], g[1][0], g[1][1], g[2][0], g[2][1], rho, lT, lc[1], lc[2], lg[1], lg[2], lrho);
+    for (int k = 0; k < kNF; k++) {
+        if (lc[k] != 0.f) atomicAdd(&A.l_C[k * NP + pc], lc[k]);
+        // gradient stencil transpose
+        float v[kQ];
+        int src[kQ];
+        stencil_C(P, A, type, gx, y, cls, k, v, src);
+        for (int a = 1; a < kQ; a++) {
+            const float w = 3.0f * wq(a) * (ex(a) * lg[k][0] + ey(a) * lg[k][1]);
+            if (w != 0.f) atomicAdd(&A.l_C[k * NP + src[a]], w);
+        }
+    }
+    // rho is 1 at C_SB nodes (no dependence); at fluid and ghost positions it is the pulled total
+    if (cls != kSB && lrho != 0.f) atomicAdd(&A.l_rho[pc], lrho);
+}
+
+// B5: adjoint of the wetting pass, one thread per C_SB node
+__global__ void b_wet(const Params P, const Adj A, int nw, const int* __restrict__ widx,
+                      const float* __restrict__ wang, const double* __restrict__ cw_lag,
+                      const uint8_t* __restrict__ type)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    const int NP = P.ny * A.nxp;
+    const int i = widx[w];
+    const int px = i % P.nx, py = i / P.nx;
+    const int p = pad(A, px, py);
+    // adjoint of the wall values: from this step's stress and gradients, and from Eq.(21) of the
+    // next step
+    float l0 = A.l_C[p] + A.l_cw[i], l1 = A.l_C[NP + p] + A.l_cw[P.N + i], l2 = A.l_C[2 * NP + p] + A.l_cw[2 * P.N + i];
+    const float c0r = A.wraw[w], c1r = A.wraw[nw + w];
+    float c0 = fminf(fmaxf(c0r, 0.f), 1.f), c1 = fminf(fmaxf(c1r, 0.f), 1.f);
+    const float s = c0 + c1;
+    if (1.f - (s > 1.f ? 1.f : s) > 0.f) {  // c2 = 1 - c0 - c1 > 0
+        l0 -= l2;
+        l1 -= l2;
+    }
+    float lc0 = l0, lc1 = l1;
+    if (s > 1.f) {
+        lc0 = l0 * (1.f / s - c0 / (s * s)) + l1 * (-c1 / (s * s));
+        lc1 = l0 * (-c0 / (s * s)) + l1 * (1.f / s - c1 / (s * s));
+    }
+    if (!(c0r >= 0.f && c0r <= 1.f)) lc0 = 0.f;
+    if (!(c1r >= 0.f && c1r <= 1.f)) lc1 = 0.f;
+    const float lk[2] = {lc0, lc1};
+    const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
+    const double Cr = cw_lag[i], Cg = cw_lag[P.N + i], Cb = cw_lag[2 * P.N + i];
+    double l_rg = 0.0, l_br = 0.0, l_gb = 0.0, lCr = 0.0, lCg = 0.0, lCb = 0.0;
+    for (int k = 0; k < 2; k++) {
+        if (lk[k] == 0.f) continue;
+        const int j = (2 * k + A.wsel[k * nw + w]) * nw + w;
+        const int kind = A.wkind[j];
+        double lth = 0.0;
+        if (kind == 1) {
+            atomicAdd(&A.l_C[k * NP + A.wa[j]], lk[k]);
+        } else if (kind == 2) {
+            const float fr = A.wfr[j];
+            atomicAdd(&A.l_C[k * NP + A.wa[j]], (1.f - fr) * lk[k]);
+            atomicAdd(&A.l_C[k * NP + A.wb[j]], fr * lk[k]);
+            const float ca = A.C[k * NP + A.wa[j]], cb = A.C[k * NP + A.wb[j]];
+            lth = (double)lk[k] * (cb - ca) * A.wdfr[j];
+        } else {
+            // w-weighted mean of the fluid neighbours
+            double ws = 0.0;
+            for (int a = 1; a < kQ; a++)
+                if (node_is_fluid<Store<kStoreF32>>(P, type, px + ex(a), py + ey(a))) ws += a < 5 ? 1.0 / 9.0 : 1.0 / 36.0;
+            for (int a = 1; a < kQ; a++) {
+                if (!node_is_fluid<Store<kStoreF32>>(P, type, px + ex(a), py + ey(a))) continue;
+                int kd;
+                const int q = cpos(P, A, px + ex(a), py + ey(a), kd);
+                atomicAdd(&A.l_C[k * NP + q], (float)((a < 5 ? 1.0 / 9.0 : 1.0 / 36.0) / ws * lk[k]));
+            }
+        }
+        if (lth == 0.0) continue;
+        // Eq.(21) in the convex-combination form
+        if (k == 0) {
+            // theta_r = t_rg + r (t_rb - t_rg), r = Cb / (Cb + Cg), t_rb = 180 - t_br
+            const double den = Cb + Cg;
+            if (den < 1e-12) {
+                l_rg += 0.5 * lth;
+                l_br -= 0.5 * lth;
+            } else {
+                const double r = Cb / den, t_rb = 180.0 - t_br;
+                l_rg += (1.0 - r) * lth;
+                l_br -= r * lth;
+                lCb += lth * (t_rb - t_rg) * Cg / (den * den);
+                lCg -= lth * (t_rb - t_rg) * Cb / (den * den);
+            }
+        } else {
+            // theta_g = t_gr + r (t_gb - t_gr), r = Cb / (Cb + Cr), t_gr = 180 - t_rg
+            const double den = Cb + Cr;
+            if (den < 1e-12) {
+                l_gb += 0.5 * lth;
+                l_rg -= 0.5 * lth;
+            } else {
+                const double r = Cb / den, t_gr = 180.0 - t_rg;
+                l_rg -= (1.0 - r) * lth;
+                l_gb += r * lth;
+                lCb += lth * (t_gb - t_gr) * Cr / (den * den);
+                lCr -= lth * (t_gb - t_gr) * Cb / (den * den);
+            }
+        }
+    }
+    A.d_ang[w] += l_rg;
+    A.d_ang[nw + w] += l_br;
+    A.d_ang[2 * nw + w] += l_gb;
+    A.l_cw2[i] = (float)lCr;
+    A.l_cw2[P.N + i] = (float)lCg;
+    A.l_cw2[2 * P.N + i] = (float)lCb;
+}
+
+// B6: adjoint of rho_k, C_k at fluid nodes (and of the ghost copies) into lambda_fpost
+__global__ void b_frac(const Params P, const Adj A, const uint8_t* __restrict__ type)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int i = y * P.nx + x;
+    if (type[i] & 2) return;
+    const int NP = P.ny * A.nxp;
+    const int p = pad(A, x, y);
+    float lC[kNF], C[kNF];
+    for (int k = 0; k < kNF; k++) {
+        lC[k] = A.l_C[k * NP + p];
+        C[k] = A.C[k * NP + p];
+    }
+    // (the ghost-column copies already sent their adjoint to this node)
+    const float lrho = A.l_rho[p];
+    const float rho = A.rho[p];
+    float sc = 0.f;
+    for (int k = 0; k < kNF; k++) sc += lC[k] * C[k];
+    for (int k = 0; k < kNF; k++) {
+        const float lr = (lC[k] - sc) / rho + lrho;
+        for (int a = 0; a < kQ; a++) A.l_fpost[(long long)(9 * k + a) * P.N + i] += lr;
+    }
+}
+
+// B7a: adjoint of the Zou-He completion at the open columns (lambda of the known populations
+// and of the inflow velocity)
+__global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__ type)
+{
+    const int y = blockIdx.x * blockDim.x + threadIdx.x;
+    if (y >= P.ny || P.bc_x != kZouHe) return;
+    auto L = [&](int k, int a, int i) -> float& { return A.l_fpost[(long long)(9 * k + a) * P.N + i]; };
+    auto Fv = [&](int k, int a, int i) { return A.fpost[(long long)(9 * k + a) * P.N + i]; };
+    {
+        // inlet x = 0: unknown a = 1, 5, 8 (fluid 2)
+        const int i = y * P.nx;
+        float f[kQ];
+        for (int a = 0; a < kQ; a++) f[a] = Fv(0, a, i) + Fv(1, a, i) + Fv(2, a, i);
+        const float U = P.u_in;
+        const float rho = (f[0] + f[2] + f[4] + 2.f * (f[3] + f[6] + f[7])) / (1.f - U);
+        const float L1 = L(2, 1, i), L5 = L(2, 5, i), L8 = L(2, 8, i);
+        const float lrho = (2.f / 3.f) * U * L1 + (U / 6.f) * (L5 + L8);
+        float lf[kQ] = {0};
+        lf[3] += L1;
+        lf[7] += L5;
+        lf[6] += L8;
+        lf[2] += -0.5f * L5 + 0.5f * L8;
+        lf[4] += 0.5f * L5 - 0.5f * L8;
+        const float ir = 1.f / (1.f - U);
+        lf[0] += lrho * ir;
+        lf[2] += lrho * ir;
+        lf[4] += lrho * ir;
+        lf[3] += 2.f * lrho * ir;
+        lf[6] += 2.f * lrho * ir;
+        lf[7] += 2.f * lrho * ir;
+        const double lU = (double)L1 * (2.0 / 3.0) * rho + (double)(L5 + L8) * rho / 6.0 + (double)lrho * rho / (1.0 - U);
+        atomicAdd(A.d_u, lU);
+        for (int k = 0; k < kNF; k++)
+            for (int a : {0, 2, 3, 4, 6, 7}) L(k, a, i) += lf[a];
+        for (int k = 0; k < kNF; k++)
+            for (int a : {1, 5, 8}) L(k, a, i) = 0.f;
+    }
+    {
+        // outlet x = nx-1: unknown a = 3, 6, 7, split by the known fractions
+        const int i = y * P.nx + P.nx - 1;
+        float f[kQ], part[kNF], tot = 0.f;
+        for (int a = 0; a < kQ; a++) f[a] = Fv(0, a, i) + Fv(1, a, i) + Fv(2, a, i);
+        for (int k = 0; k < kNF; k++) {
+            part[k] = Fv(k, 0, i) + Fv(k, 1, i) + Fv(k, 2, i) + Fv(k, 4, i) + Fv(k, 5, i) + Fv(k, 8, i);
+            tot += part[k];
+        }
+        const float ro = P.rho_out;
+        const float S = f[0] + f[2] + f[4] + 2.f * (f[1] + f[5] + f[8]);
+        const float h3 = f[1] - (2.f / 3.f) * (S - ro);
+        const float h7 = f[5] + 0.5f * (f[2] - f[4]) - (S - ro) / 6.f;
+        const float h6 = f[8] - 0.5f * (f[2] - f[4]) - (S - ro) / 6.f;
+        float lh3 = 0.f, lh6 = 0.f, lh7 = 0.f, lpart[kNF], acc = 0.f;
+        for (int k = 0; k < kNF; k++) {
+            const float a3 = L(k, 3, i), a6 = L(k, 6, i), a7 = L(k, 7, i);
+            lh3 += a3 * part[k] / tot;
+            lh6 += a6 * part[k] / tot;
+            lh7 += a7 * part[k] / tot;
+            lpart[k] = (a3 * h3 + a6 * h6 + a7 * h7) / tot;
+            acc += lpart[k] * part[k] / tot;
+        }
+        for (int k = 0; k < kNF; k++) lpart[k] -= acc;
+        float lf[kQ] = {0};
+        // h3 = f1 - (2/3)(S - ro), h7 = f5 + (f2 - f4)/2 - (S - ro)/6, h6 = f8 - (f2 - f4)/2 - (S - ro)/6
+        lf[1] += lh3 * (1.f - 4.f / 3.f);
+        lf[0] += lh3 * (-2.f / 3.f);
+        lf[2] += lh3 * (-2.f / 3.f);
+        lf[4] += lh3 * (-2.f / 3.f);
+        lf[5] += lh3 * (-4.f / 3.f);
+        lf[8] += lh3 * (-4.f / 3.f);
+        lf[5] += lh7 * (1.f - 1.f / 3.f);
+        lf[2] += lh7 * (0.5f - 1.f / 6.f);
+        lf[4] += lh7 * (-0.5f - 1.f / 6.f);
+        lf[0] += lh7 * (-1.f / 6.f);
+        lf[1] += lh7 * (-1.f / 3.f);
+        lf[8] += lh7 * (-1.f / 3.f);
+        lf[8] += lh6 * (1.f - 1.f / 3.f);
+        lf[2] += lh6 * (-0.5f - 1.f / 6.f);
+        lf[4] += lh6 * (0.5f - 1.f / 6.f);
+        lf[0] += lh6 * (-1.f / 6.f);
+        lf[1] += lh6 * (-1.f / 3.f);
+        lf[5] += lh6 * (-1.f / 3.f);
+        for (int k = 0; k < kNF; k++)
+            for (int a : {0, 1, 2, 4, 5, 8}) L(k, a, i) += lf[a] + lpart[k];
+        for (int k = 0; k < kNF; k++)
+            for (int a : {3, 6, 7}) L(k, a, i) = 0.f;
+    }
+}
+
+// B7b: adjoint of the pull: the stored population (s, a) was read by exactly one puller
+__global__ void b_pull(const Params P, const Adj A, const uint8_t* __restrict__ type)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int i = y * P.nx + x;
+    const bool solid = type[i] & 2;
+    for (int a = 0; a < kQ; a++) {
+        const Loc d = locate(P, x + ex(a), y + ey(a));
+        for (int k = 0; k < kNF; k++) {
+            float v = 0.f;
+            if (!solid) {
+                if (d.kind == 1 || (d.kind == 0 && (type[d.idx] & 2)))
+                    v = A.l_fpost[(long long)(9 * k + opp(a)) * P.N + i];
+                else if (d.kind == 0)
+                    v = A.l_fpost[(long long)(9 * k + a) * P.N + d.idx];
+            }
+            A.l_fs[(long long)(9 * k + a) * P.N + i] = v;
+        }
+    }
+}
+
+// objective: x-centroid of fluid 0, J = sum x rho_0 / sum rho_0 over the post-streaming state;
+// seed lambda_fpost = dJ/dfpost
+__global__ void b_seed(const Params P, const Adj A, const uint8_t* __restrict__ type, double J, double M0)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int i = y * P.nx + x;
+    const bool fluid = !(type[i] & 2);
+    for (int k = 0; k < kNF; k++)
+        for (int a = 0; a < kQ; a++)
+            A.l_fpost[(long long)(9 * k + a) * P.N + i] = (fluid && k == 0) ? (float)(((double)x - J) / M0) : 0.f;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------
+// host-side driver of one reverse step and of the seed
+// ------------------------------------------------------------------------------------------
+struct AdjointWork {
+    Adj A;
+    size_t bytes = 0;
+};
+
+static cudaError_t amalloc(void** p, size_t b, size_t& tot)
+{
+    tot += b;
+    return cudaMalloc(p, b ? b : 16);
+}
+
+cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out)
+{
+    AdjointWork* W = new AdjointWork();
+    Adj& A = W->A;
+    A.nxp = P.nx + 2;
+    const size_t N = (size_t)P.N, NP = (size_t)P.ny * A.nxp;
+    const size_t nwz = nw > 0 ? (size_t)nw : 1;
+    size_t& t = W->bytes;
+    cudaError_t e = cudaSuccess;
+    auto M = [&](void** p, size_t b) {
+        if (e == cudaSuccess) e = amalloc(p, b, t);
+        if (e == cudaSuccess) e = cudaMemset(*p, 0, b ? b : 16);
+    };
+    M((void**)&A.fpost, 27 * N * 4);
+    M((void**)&A.C, 3 * NP * 4);
+    M((void**)&A.rho, NP * 4);
+    M((void**)&A.g, 6 * NP * 4);
+    M((void**)&A.T, 3 * NP * 4);
+    M((void**)&A.F, 2 * N * 4);
+    M((void**)&A.wkind, 4 * nwz * 4);
+    M((void**)&A.wa, 4 * nwz * 4);
+    M((void**)&A.wb, 4 * nwz * 4);
+    M((void**)&A.wfr, 4 * nwz * 4);
+    M((void**)&A.wdfr, 4 * nwz * 4);
+    M((void**)&A.wcd, 4 * nwz * 4);
+    M((void**)&A.wth, 2 * nwz * 4);
+    M((void**)&A.wraw, 2 * nwz * 4);
+    M((void**)&A.wsel, 2 * nwz * 4);
+    M((void**)&A.l_fpost, 27 * N * 4);
+    M((void**)&A.l_F, 2 * N * 4);
+    M((void**)&A.l_g, 6 * NP * 4);
+    M((void**)&A.l_T, 3 * NP * 4);
+    M((void**)&A.l_C, 3 * NP * 4);
+    M((void**)&A.l_rho, NP * 4);
+    M((void**)&A.l_fs, 27 * N * 4);
+    M((void**)&A.l_cw, 3 * N * 4);
+    M((void**)&A.l_cw2, 3 * N * 4);
+    M((void**)&A.d_ang, 3 * nwz * 8);
+    M((void**)&A.d_u, 8);
+    *out = W;
+    return e;
+}
+
+void adjoint_free(AdjointWork* W)
+{
+    if (!W) return;
+    Adj& A = W->A;
+    void* ptrs[] = {A.fpost, A.C, A.rho, A.g, A.T, A.F, A.wkind, A.wa, A.wb, A.wfr, A.wdfr, A.wcd,
+                    A.wth, A.wraw, A.wsel, A.l_fpost, A.l_F, A.l_g, A.l_T, A.l_C, A.l_rho, A.l_fs,
+                    A.l_cw, A.l_cw2, A.d_ang, A.d_u};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete W;
+}
+
+size_t adjoint_bytes(const AdjointWork* W) { return W ? W->bytes : 0; }
+
+double* adjoint_dang(AdjointWork* W) { return W->A.d_ang; }
+double* adjoint_du(AdjointWork* W) { return W->A.d_u; }
+
+// seed the adjoint from the final stored populations: lambda_fs = pull^T (dJ/dfpost)
+void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, double J,
+                  double M0, cudaStream_t s)
+{
+    Adj& A = W->A;
+    const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
+    a_dens<<<gp, 128, 0, s>>>(P, A, fs, type);
+    b_seed<<<gn, 128, 0, s>>>(P, A, type, J, M0);
+    b_zouhe<<<(P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
+    b_pull<<<gn, 128, 0, s>>>(P, A, type);
+    cudaMemsetAsync(A.l_cw, 0, sizeof(float) * 3 * (size_t)P.N, s);
+}
+
+// one reverse step: fs / cw_lag are the stored populations and lagged wall values at the start
+// of the step; on entry A.l_fs, A.l_cw hold the adjoint of the step's outputs, on exit of its inputs
+void adjoint_step(const Params& P, AdjointWork* W, int nw, const int* widx, const double* wnrm,
+                  const float* wang, const float* fs, const double* cw_lag, const uint8_t* type,
+                  cudaStream_t s)
+{
+    Adj& A = W->A;
+    const size_t NP = (size_t)P.ny * A.nxp;
+    const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
+    // forward intermediates
+    a_dens<<<gp, 128, 0, s>>>(P, A, fs, type);
+    if (nw > 0)
+        a_wet<<<(unsigned)((4LL * nw + 127) / 128), 128, 0, s>>>(P, A, nw, widx, wnrm, wang, fs, type, cw_lag);
+    a_grad_stress<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
+    a_force<<<gn, 128, 0, s>>>(P, A, type);
+    // reverse
+    cudaMemsetAsync(A.l_g, 0, sizeof(float) * 6 * NP, s);
+    cudaMemsetAsync(A.l_C, 0, sizeof(float) * 3 * NP, s);
+    cudaMemsetAsync(A.l_rho, 0, sizeof(float) * NP, s);
+    cudaMemsetAsync(A.l_fpost, 0, sizeof(float) * 27 * (size_t)P.N, s);
+    b_collide<<<gn, 128, 0, s>>>(P, A, type);
+    b_div<<<gp, 128, 0, s>>>(P, A, type);
+    b_stress_grad<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
+    cudaMemsetAsync(A.l_cw2, 0, sizeof(float) * 3 * (size_t)P.N, s);
+    if (nw > 0) b_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, A, nw, widx, wang, cw_lag, type);
+    b_frac<<<gn, 128, 0, s>>>(P, A, type);
+    b_zouhe<<<(P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
+    b_pull<<<gn, 128, 0, s>>>(P, A, type);
+    std::swap(A.l_cw, A.l_cw2);
+}
+
+}  // namespace lbm3k

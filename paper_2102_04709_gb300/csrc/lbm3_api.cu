@@ -528,6 +528,123 @@ int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c)
     return LBM3_OK;
 }
 
+int lbm3_set_wall_angles(lbm3* h, const double* angles)
+{
+    if (!h || (!angles && h->nw > 0)) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    std::vector<float> a(3 * (size_t)h->nw);
+    for (size_t j = 0; j < a.size(); j++) {
+        if (!(angles[j] > 0.0 && angles[j] < 180.0))
+            return fail(h, LBM3_ERR_INVALID, "wall angles must lie in (0, 180) degrees");
+        a[j] = (float)angles[j];
+    }
+    if (!a.empty())
+        CUDA_TRY(h, cudaMemcpyAsync(h->wang, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    return LBM3_OK;
+}
+
+int lbm3_set_inflow(lbm3* h, double u_in)
+{
+    if (!h) return fail(h, LBM3_ERR_INVALID, "NULL handle");
+    if (h->P.bc_x != kZouHe) return fail(h, LBM3_ERR_INVALID, "no Zou-He inlet");
+    if (!(std::fabs(u_in) < 0.3)) return fail(h, LBM3_ERR_INVALID, "|u_in| must be < 0.3");
+    h->P.u_in = (float)u_in;
+    return LBM3_OK;
+}
+
+int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, double* dJ_dangles,
+                          double* dJ_du)
+{
+    if (!h || !J_out || !dJ_du || (!dJ_dangles && h->nw > 0)) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    if (nsteps < 1 || K < 1) return fail(h, LBM3_ERR_INVALID, "nsteps and checkpoint_every must be >= 1");
+    if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
+    if (h->precision != LBM3_FP32) return fail(h, LBM3_ERR_INVALID, "the adjoint needs FP32 storage");
+    if (h->P.bc_x == kModPer) return fail(h, LBM3_ERR_INVALID, "the adjoint does not support the modified periodic boundary");
+    const size_t N = (size_t)h->P.N;
+    const size_t fb = 27 * N * sizeof(float), cb = 3 * N * sizeof(double);
+    const int nseg = (nsteps + K - 1) / K;
+    const int seglen = std::min(K, nsteps);
+    float *ck_f = nullptr, *sg_f = nullptr, *fin_f = nullptr;
+    double *ck_c = nullptr, *sg_c = nullptr, *fin_c = nullptr;
+    AdjointWork* W = nullptr;
+    auto cleanup = [&]() {
+        void* ptrs[] = {ck_f, sg_f, fin_f, ck_c, sg_c, fin_c};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        adjoint_free(W);
+    };
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_f, fb * nseg);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_c, cb * nseg);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sg_f, fb * seglen);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&sg_c, cb * seglen);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&fin_f, fb);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&fin_c, cb);
+    if (e == cudaSuccess) e = adjoint_alloc(h->P, h->nw, &W);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(h, e == cudaErrorMemoryAllocation ? LBM3_ERR_OOM : LBM3_ERR_CUDA,
+                    std::string("adjoint set-up: ") + cudaGetErrorString(e));
+    }
+    cudaStream_t s = h->stream;
+    auto save = [&](float* df, double* dc) {
+        cudaMemcpyAsync(df, h->pop[h->cur].f, fb, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(dc, h->Cw, cb, cudaMemcpyDeviceToDevice, s);
+    };
+    auto restore = [&](const float* df, const double* dc) {
+        h->cur = 0;
+        cudaMemcpyAsync(h->pop[0].f, df, fb, cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(h->Cw, dc, cb, cudaMemcpyDeviceToDevice, s);
+    };
+    // forward with checkpoints
+    for (int t = 0; t < nsteps; t++) {
+        if (t % K == 0) save(ck_f + (size_t)(t / K) * 27 * N, ck_c + (size_t)(t / K) * 3 * N);
+        if ((e = enqueue_step(h, t == nsteps - 1, nullptr)) != cudaSuccess) break;
+    }
+    double d[8];
+    if (e == cudaSuccess) {
+        launch_diag(h->precision, h->P, h->pop[h->cur], h->type, h->u, h->partials, h->dout, s);
+        e = cudaMemcpyAsync(d, h->dout, sizeof d, cudaMemcpyDeviceToHost, s);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(h, LBM3_ERR_CUDA, std::string("adjoint forward: ") + cudaGetErrorString(e));
+    }
+    const double M0 = d[0], J = d[3] / d[0];
+    save(fin_f, fin_c);
+    cudaMemsetAsync(adjoint_dang(W), 0, sizeof(double) * 3 * (size_t)std::max(h->nw, 1), s);
+    cudaMemsetAsync(adjoint_du(W), 0, sizeof(double), s);
+    adjoint_seed(h->P, W, h->pop[h->cur].f, h->type, J, M0, s);
+    // backward over the segments, each recomputed from its checkpoint
+    for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; seg--) {
+        const int t0 = seg * K, t1 = std::min(nsteps, t0 + K);
+        restore(ck_f + (size_t)seg * 27 * N, ck_c + (size_t)seg * 3 * N);
+        for (int t = t0; t < t1; t++) {
+            save(sg_f + (size_t)(t - t0) * 27 * N, sg_c + (size_t)(t - t0) * 3 * N);
+            if (t < t1 - 1 && (e = enqueue_step(h, false, nullptr)) != cudaSuccess) break;
+        }
+        for (int t = t1 - 1; t >= t0 && e == cudaSuccess; t--) {
+            adjoint_step(h->P, W, h->nw, h->widx, h->wnrm, h->wang, sg_f + (size_t)(t - t0) * 27 * N,
+                         sg_c + (size_t)(t - t0) * 3 * N, h->type, s);
+            e = cudaGetLastError();
+        }
+    }
+    std::vector<double> dang(3 * (size_t)std::max(h->nw, 1));
+    double du = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dang.data(), adjoint_dang(W), sizeof(double) * dang.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&du, adjoint_du(W), sizeof(double), cudaMemcpyDeviceToHost, s);
+    restore(fin_f, fin_c);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cleanup();
+    if (e != cudaSuccess) return fail(h, LBM3_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(e));
+    *J_out = J;
+    for (int w = 0; w < h->nw; w++)
+        for (int j = 0; j < 3; j++) dJ_dangles[3 * w + j] = dang[(size_t)j * h->nw + w];
+    *dJ_du = h->P.bc_x == kZouHe ? du : 0.0;
+    return LBM3_OK;
+}
+
 int lbm3_info(const lbm3* h, int64_t out[8])
 {
     if (!h || !out) return LBM3_ERR_INVALID;

@@ -302,6 +302,18 @@ void launch_get_state(int store, const Params& P, const Pop& f, const uint8_t* t
 void launch_set_state(int store, const Params& P, const double* post, const uint8_t* type,
                       const Pop& f, cudaStream_t s);
 int diag_blocks(const Params& P);
+// adjoint (lbm3_adjoint.cu)
+struct AdjointWork;
+cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out);
+void adjoint_free(AdjointWork* W);
+size_t adjoint_bytes(const AdjointWork* W);
+double* adjoint_dang(AdjointWork* W);
+double* adjoint_du(AdjointWork* W);
+void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, double J,
+                  double M0, cudaStream_t s);
+void adjoint_step(const Params& P, AdjointWork* W, int nw, const int* widx, const double* wnrm,
+                  const float* wang, const float* fs, const double* cw_lag, const uint8_t* type,
+                  cudaStream_t s);
 void launch_diag(int store, const Params& P, const Pop& f, const uint8_t* type, const float* u,
                  double* partials, double* out, cudaStream_t s);
 

@@ -26,8 +26,8 @@ LBM3_FP32, LBM3_FP16, LBM3_BF16 = 0, 1, 2
 # every entry point declared in include/lbm3.h
 EXPORTS = ("lbm3_create", "lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields",
            "lbm3_diag", "lbm3_n_wall", "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state",
-           "lbm3_set_state", "lbm3_info", "lbm3_set_stream", "lbm3_sync", "lbm3_destroy",
-           "lbm3_last_error")
+           "lbm3_set_state", "lbm3_set_wall_angles", "lbm3_set_inflow", "lbm3_adjoint_centroid",
+           "lbm3_info", "lbm3_set_stream", "lbm3_sync", "lbm3_destroy", "lbm3_last_error")
 
 
 class lbm3_grid(ctypes.Structure):
@@ -70,6 +70,9 @@ def load(path: str | None = None):
     L.lbm3_wall_values.argtypes = [vp, _D, ctypes.c_int32]
     L.lbm3_get_state.argtypes = [vp, _D, _D]
     L.lbm3_set_state.argtypes = [vp, _D, _D]
+    L.lbm3_set_wall_angles.argtypes = [vp, _D]
+    L.lbm3_set_inflow.argtypes = [vp, ctypes.c_double]
+    L.lbm3_adjoint_centroid.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, _D, _D, _D]
     L.lbm3_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.lbm3_set_stream.argtypes = [vp, vp]
     L.lbm3_sync.argtypes = [vp]
@@ -129,6 +132,7 @@ class Lbm3:
         if code < 0:
             raise Lbm3Error(code, L.lbm3_last_error(None).decode())
         self._h = h
+        self.bc_x = int(bc_x)
         self.warning = L.lbm3_last_error(h).decode() if code > 0 else ""
 
     @classmethod
@@ -199,6 +203,26 @@ class Lbm3:
         if f.size != 27 * self.n or c.size != 3 * self.n:
             raise ValueError("f_post must be [3, 9, ny, nx] and wall_c [3, ny, nx]")
         _check(self._h, load().lbm3_set_state(self._h, _dp(f), _dp(c)))
+
+    def set_wall_angles(self, angles):
+        """angles: [n_wall, 3] (theta_01, theta_20, theta_12) in degrees, lbm3_wall_nodes order."""
+        a = np.ascontiguousarray(angles, dtype=np.float64).reshape(-1)
+        if a.size != 3 * load().lbm3_n_wall(self._h):
+            raise ValueError("angles must be [n_wall, 3]")
+        _check(self._h, load().lbm3_set_wall_angles(self._h, _dp(a)))
+
+    def set_inflow(self, u_in):
+        _check(self._h, load().lbm3_set_inflow(self._h, float(u_in)))
+
+    def adjoint_centroid(self, nsteps, checkpoint_every=100):
+        """(J, dJ/d angles [n_wall, 3], dJ/du_in) for J = x-centroid of fluid 0 after nsteps."""
+        n = load().lbm3_n_wall(self._h)
+        J = np.zeros(1)
+        dang = np.zeros(3 * max(n, 1))
+        du = np.zeros(1)
+        _check(self._h, load().lbm3_adjoint_centroid(self._h, int(nsteps), int(checkpoint_every),
+                                                     _dp(J), _dp(dang), _dp(du)))
+        return float(J[0]), dang[:3 * n].reshape(n, 3), float(du[0])
 
     def info(self):
         out = np.zeros(8, np.int64)
