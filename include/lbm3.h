@@ -38,6 +38,7 @@ typedef struct lbm3 lbm3;
 #define LBM3_ERR_OOM (-3)        /* device allocation failed */
 #define LBM3_ERR_DIVERGED (-4)   /* non-finite or non-positive density found by lbm3_diag */
 #define LBM3_ERR_STATE (-5)      /* call out of order (e.g. lbm3_step before lbm3_set_fields) */
+#define LBM3_ERR_TOO_LARGE (-6)  /* grid larger than lbm3_diag_fields accepts */
 
 /* x boundary (bc_x) */
 #define LBM3_BC_PERIODIC 0       /* periodic */
@@ -161,6 +162,36 @@ int lbm3_sync(lbm3* h);
 
 /* Release all device memory of the handle (NULL is ignored). */
 void lbm3_destroy(lbm3* h);
+
+/* Allocation-free diagnostics of caller-owned device fields.  The paper has no counterpart:
+ * this is the reduction of lbm3_diag (same out[0..7], same FP64 accumulation) applied to fields
+ * that the caller already holds on the device, for callers that must not allocate at the call:
+ * a monitor running inside a host framework whose caching allocator has reserved the device's
+ * memory (a cudaMalloc there can fail, and a cudaFree synchronises the device), or a loop that
+ * must not synchronise.  The call allocates nothing on the device or the host: the block
+ * partials live in one fixed device array of LBM3_DIAG_FIELDS_MAX_BLOCKS x 8 doubles (64 KiB)
+ * inside the library, and the reduction strides over the grid with at most that many blocks,
+ * so any grid up to LBM3_DIAG_FIELDS_MAX_NODES nodes fits; larger grids return
+ * LBM3_ERR_TOO_LARGE without launching anything.  Nothing in that array has to start at zero
+ * (each block writes its partials before the final pass reads them).
+ *   rho    device float [3][ny][nx]  densities rho_k (e.g. lbm3_fields' output, in FP32)
+ *   u      device float [2][ny][nx]  velocity (u_x, u_y)
+ *   solid  device uint8 [ny][nx]     1 = solid node (skipped), 0 = fluid
+ *   out    device double [8]         written when the enqueued work completes
+ *   stream cudaStream_t (NULL = legacy default stream) of the current device, which must be the
+ *          device holding the four buffers
+ * The call only enqueues two kernels and returns: it does not synchronise and does not check
+ * the results for divergence.  Ownership of every buffer stays with the caller.  The first call
+ * on each device looks up the address of the fixed array (cudaGetSymbolAddress) once, with that
+ * device current; callers that begin stream capture make that first call before the capture
+ * starts.  Calls that overlap in time on the same device (on different streams, or from
+ * different threads without ordering) share the array and race; calls ordered on one stream do
+ * not.  Returns LBM3_ERR_INVALID for a NULL pointer or nx, ny <= 0, LBM3_ERR_TOO_LARGE for
+ * nx * ny > LBM3_DIAG_FIELDS_MAX_NODES, LBM3_ERR_CUDA if the lookup or a launch fails. */
+#define LBM3_DIAG_FIELDS_MAX_BLOCKS 1024
+#define LBM3_DIAG_FIELDS_MAX_NODES 2147483647LL
+int lbm3_diag_fields(const float* rho, const float* u, const uint8_t* solid, int32_t nx,
+                     int32_t ny, double* out, void* stream);
 
 /* Text of the last error or warning of the handle (or of the last failed lbm3_create when
  * h == NULL). Valid until the next call on the same handle. */

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblbm3.so")
-SOURCES = ["lbm3_api.cu", "lbm3_step.cu", "lbm3_adjoint.cu"]
+SOURCES = ["lbm3_api.cu", "lbm3_step.cu", "lbm3_adjoint.cu", "lbm3_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

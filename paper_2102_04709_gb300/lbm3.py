@@ -21,13 +21,15 @@ LBM3_ERR_CUDA = -2
 LBM3_ERR_OOM = -3
 LBM3_ERR_DIVERGED = -4
 LBM3_ERR_STATE = -5
+LBM3_ERR_TOO_LARGE = -6
 LBM3_FP32, LBM3_FP16, LBM3_BF16 = 0, 1, 2
 
 # every entry point declared in include/lbm3.h
 EXPORTS = ("lbm3_create", "lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields",
            "lbm3_diag", "lbm3_n_wall", "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state",
            "lbm3_set_state", "lbm3_set_wall_angles", "lbm3_set_inflow", "lbm3_adjoint_centroid",
-           "lbm3_info", "lbm3_set_stream", "lbm3_sync", "lbm3_destroy", "lbm3_last_error")
+           "lbm3_info", "lbm3_set_stream", "lbm3_sync", "lbm3_destroy", "lbm3_last_error",
+           "lbm3_diag_fields")
 
 
 class lbm3_grid(ctypes.Structure):
@@ -79,6 +81,7 @@ def load(path: str | None = None):
     L.lbm3_destroy.argtypes = [vp]
     L.lbm3_destroy.restype = None
     L.lbm3_last_error.argtypes = [vp]
+    L.lbm3_diag_fields.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
     L.lbm3_last_error.restype = ctypes.c_char_p
     for name in ("lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields", "lbm3_diag", "lbm3_n_wall",
                  "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state", "lbm3_set_state", "lbm3_info", "lbm3_set_stream", "lbm3_sync"):
@@ -106,6 +109,19 @@ def _torch_stream():
     except ImportError:
         pass
     return ctypes.c_void_p(None)
+
+
+def diag_fields(rho, u, solid, nx, ny, out, stream=None):
+    """``lbm3_diag_fields`` on caller-owned device buffers given as integer addresses (float
+    rho [3][ny][nx], float u [2][ny][nx], uint8 solid [ny][nx], double out [8]); enqueues on
+    ``stream`` (default: torch's current stream) and returns without synchronising."""
+    s = _torch_stream() if stream is None else ctypes.c_void_p(stream)
+    code = load().lbm3_diag_fields(rho, u, solid, int(nx), int(ny), out, s)
+    if code < 0:
+        raise Lbm3Error(code, {LBM3_ERR_INVALID: "NULL buffer or nx, ny <= 0",
+                               LBM3_ERR_TOO_LARGE: "grid larger than the fixed scratch accepts",
+                               LBM3_ERR_CUDA: "scratch lookup or launch failed"}.get(code, ""))
+    return code
 
 
 class Lbm3:

@@ -95,3 +95,13 @@ def test_null_handle_calls(lib):
     assert lib.lbm3_step(None, 1) == -1
     assert lib.lbm3_n_wall(None) == -1
     lib.lbm3_destroy(None)
+
+
+def test_diag_fields_argument_checks(lib):
+    """lbm3_diag_fields rejects NULL buffers, empty grids and grids beyond its fixed scratch
+    before it touches the GPU."""
+    from paper_2102_04709_gb300 import lbm3
+    fake = 256  # never dereferenced: every case below is rejected first
+    assert lib.lbm3_diag_fields(None, fake, fake, 8, 8, fake, None) == lbm3.LBM3_ERR_INVALID
+    assert lib.lbm3_diag_fields(fake, fake, fake, 0, 8, fake, None) == lbm3.LBM3_ERR_INVALID
+    assert lib.lbm3_diag_fields(fake, fake, fake, 65536, 65536, fake, None) == lbm3.LBM3_ERR_TOO_LARGE
