@@ -42,12 +42,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--theta", type=float, default=90.0)
+    ap.add_argument("--workload", choices=["pillars_4096x2048", "pillars_2048x1024"],
+                    default="pillars_4096x2048",
+                    help="the half-size case exists for detailed kernel profiles")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
                     help="population storage of the headline run")
     ap.add_argument("--no-alt-storage", action="store_true",
                     help="skip the extra FP16 / BF16 storage timings")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the adjoint timing (512 x 256, 6 pillars, 2000 steps, K = 100)")
     return ap.parse_args()
 
 
@@ -225,7 +230,7 @@ def run_ours(args):
     build.build()
     lbm3.load()
 
-    w = W.config4(args.theta)
+    w = W.config4(args.theta) if args.workload == "pillars_4096x2048" else W.pillars_half(args.theta)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     prec = PRECISIONS[args.precision]
@@ -298,6 +303,33 @@ def run_ours(args):
                          "bytes_per_fluid_node": 216 if p == 0 else 120,
                          "pure_kernel_gbs": ainfo["pure_bytes"] / (msp / n_alt * 1e-3) / 1e9}
 
+    # adjoint: J = x-centroid of fluid 0 after 2000 steps of the 512 x 256 six-pillar case,
+    # gradients for every wall-node angle and the inflow velocity, checkpoints every 100 steps
+    adj = None
+    if not args.no_adjoint:
+        w5 = W.config5()
+        s5 = lbm3.Lbm3.from_workload(w5, stream=stream.cuda_stream)
+        s5.adjoint_centroid(200, 100)          # warm-up
+        s5.set_fields(w5.rho)
+        barrier()
+        ta = time.perf_counter()
+        J, dang, du = s5.adjoint_centroid(w5.steps, 100)
+        barrier()
+        tb = time.perf_counter()
+        s5.set_fields(w5.rho)
+        barrier()
+        tc = time.perf_counter()
+        s5.step(w5.steps)
+        barrier()
+        td = time.perf_counter()
+        adj = {"workload": w5.name, "steps": w5.steps, "checkpoint_every": 100,
+               "wall_nodes": int(dang.shape[0]),
+               "steps_per_s": w5.steps / (tb - ta), "unit": "adjoint steps/s (forward + recompute + reverse)",
+               "ms_per_step": (tb - ta) / w5.steps * 1e3,
+               "forward_only_ms_per_step": (td - tc) / w5.steps * 1e3,
+               "J": J, "dJ_du": du, "grad_angles_norm": float(np.linalg.norm(dang))}
+        del s5
+
     if rank != 0:
         return
     value = w.n * args.steps * ws / (ms * 1e-3) / 1e6
@@ -313,7 +345,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "fluid_nodes": info["n_fluid"],
                    "wall_nodes": info["n_wall"], "storage": args.precision,
-                   "alt_storage": alt,
+                   "alt_storage": alt, "adjoint": adj,
                    "mflups": info["n_fluid"] * args.steps * ws / (ms * 1e-3) / 1e6,
                    "l2": "populations 2 x 0.91 GB > 129 MB L2: no flush between steps",
                    "replicas": ws, "ms_wet_per_step": ms_wet / args.steps,

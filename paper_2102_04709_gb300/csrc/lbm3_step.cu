@@ -201,6 +201,17 @@ __device__ __forceinline__ void grad9_df(const float (*h)[W], const float (*l)[W
     gy = hy + ly_;
 }
 
+// A C_SB node whose wall values are not all within kMixEps of one pure fluid: a fluid-fluid
+// interface reaches the wall there (a contact line, or one within a few nodes of it), where the
+// lagged wetting feedback amplifies the rounding of single-precision phase fields.  Away from
+// such nodes the phase fields near walls are those of one fluid and a float suffices.
+constexpr double kMixEps = 1e-6;
+__device__ __forceinline__ bool mixed_wall(const double* __restrict__ Cw, long long N, long long i)
+{
+    const double m = fmax(fmax(Cw[i], Cw[N + i]), Cw[2 * N + i]);
+    return m < 1.0 - kMixEps;
+}
+
 // Eq.(12) derivative of a float field held in shared memory
 template <int W>
 __device__ __forceinline__ void grad9_f(const float (*c)[W], int cx, int cy, float& gx, float& gy)
@@ -220,8 +231,9 @@ __device__ __forceinline__ void grad9_f(const float (*c)[W], int cx, int cy, flo
 //   phase 2: the Eq.(10) stress tensor on the halo-1 region
 //   phase 3: force, velocity, MRT collision with forcing, recolouring, 27 stores per node
 // Tiles whose halo-3 region stays inside the domain take arithmetic source indices and skip the
-// bounce-back tests at C_FI nodes; only tiles whose halo-2 region holds a C_SB node carry the
-// float-float phase fields (the wetting feedback at contact lines needs them, see above).
+// bounce-back tests at C_FI nodes; only tiles whose halo-2 region holds a C_SB node with mixed
+// wall values (a contact line at or near it) carry the float-float phase fields, decided anew
+// every step from the wall values of this step's wetting pass.
 template <int TX, int TY, bool PURE, int STORE>
 __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __restrict__ tiles,
                                                   const Pop fin, const Pop fout,
@@ -259,7 +271,9 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
             const int hx = j % HX, hy = j / HX;
             const uint8_t t = __ldg(type + (y0 + hy - 3) * nx + (x0 + hx - 3));
             s_t[hy][hx] = t;
-            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY) wall = 1;
+            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY &&
+                mixed_wall(Cw, P.N, (y0 + hy - 3) * nx + (x0 + hx - 3)))
+                wall = 1;
         }
     } else {
         for (int j = tid; j < HX * HY; j += NT) {
@@ -274,7 +288,8 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
             s_t[hy][hx] = t;
             s_idx[hy][hx] = L.idx;
             if (hy == 0) s_par[hx] = parity_x(P, X);
-            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY) wall = 1;
+            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY && mixed_wall(Cw, P.N, L.idx))
+                wall = 1;
         }
     }
     const bool df = PURE ? false : __syncthreads_or(wall);
@@ -473,14 +488,15 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
             if (!PURE && (t & 3) == kSB) {
                 // solid node: a solid-interior neighbour takes the node's own value
 #pragma unroll
+                // (the lo words exist only in float-float tiles)
                 for (int k = 0; k < kNF; k++) {
                     float v[kQ], vl[kQ];
-                    const float ch = s_ch[k][cy][cx], cl = s_cl[k][cy][cx];
+                    const float ch = s_ch[k][cy][cx], cl = df ? s_cl[k][cy][cx] : 0.0f;
 #pragma unroll
                     for (int a = 1; a < kQ; a++) {
                         const bool si = (s_t[hy + ey(a)][hx + ex(a)] & 3) == kSI;
                         v[a] = si ? ch : s_ch[k][cy + ey(a)][cx + ex(a)];
-                        vl[a] = si ? cl : s_cl[k][cy + ey(a)][cx + ex(a)];
+                        vl[a] = si || !df ? cl : s_cl[k][cy + ey(a)][cx + ex(a)];
                     }
                     gxk[k] = (1.0f / 3.0f) * (v[1] - v[3]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[8] - v[6])) +
                              ((1.0f / 3.0f) * (vl[1] - vl[3]) + (1.0f / 12.0f) * ((vl[5] - vl[7]) + (vl[8] - vl[6])));

@@ -246,6 +246,15 @@ def config4(theta=90.0):
     return pillars(theta=theta, name=f"pillars_4096x2048_theta{int(theta)}")
 
 
+def pillars_half(theta=90.0):
+    """The pillar case at half the linear size (2048x1024, 60 pillars of radius 20-40, droplet
+    core 60 / shell 100): 0.23 GB per population buffer, still above L2; used for detailed
+    profiles of the step kernel."""
+    return pillars(nx=2048, ny=1024, count=60, r_lo=20.0, r_hi=40.0, x_lo=450.0, x_hi=1950.0,
+                   gap=4.0, drop=(200.0, 512.0), r_core=60.0, r_shell=100.0, theta=theta,
+                   name=f"pillars_2048x1024_theta{int(theta)}")
+
+
 def config5():
     """Adjoint case: 512x256, 6 seeded pillars, droplet scaled by 1/4, per-node theta in
     U[60, 120], 2000 steps."""

@@ -96,6 +96,67 @@ def test_adjoint_matches_fd_of_oracle(gpu, oracle_mod, case):
         assert abs(u.grad.item() - fdu) <= 1e-3 * abs(fdu)
 
 
+def small_case():
+    """64 x 32, one pillar wetted by the shell of a compound droplet, Zou-He inflow, per-node
+    angles in [60, 120], generic (1e-6 perturbed) initial densities."""
+    w = W.pillars(nx=64, ny=32, count=1, r_lo=5.0, r_hi=6.0, x_lo=30.0, x_hi=36.0, gap=4.0,
+                  seed=3, drop=(20.0, 16.0), r_core=4.0, r_shell=9.0,
+                  theta_range=(60.0, 120.0), u_in=0.02)
+    rng = np.random.default_rng(2)
+    w.rho = w.rho * (1.0 + 1e-6 * rng.standard_normal(w.rho.shape))
+    return w
+
+
+def _fd_component(job):
+    """Central difference of the oracle's J in one wall angle (or in u_in when comp < 0)."""
+    from oracle import oracle as om
+    w, idx, a0, steps, node, comp, h = job
+    if comp < 0:
+        jp = oracle_J(om, w, a0, idx, w.u_in + h, steps)
+        jm = oracle_J(om, w, a0, idx, w.u_in - h, steps)
+    else:
+        ap = a0.copy()
+        ap[node, comp] += h
+        am = a0.copy()
+        am[node, comp] -= h
+        jp = oracle_J(om, w, ap, idx, w.u_in, steps)
+        jm = oracle_J(om, w, am, idx, w.u_in, steps)
+    return (jp - jm) / (2 * h)
+
+
+def test_adjoint_full_gradient_small_case(gpu):
+    """Every component of dJ/d(angles) and dJ/du_in on the 64 x 32, 200-step case against a
+    central difference of the FP64 oracle per component (a process pool of spawned workers
+    runs the 2 (3 n_wall + 1) oracle runs)."""
+    import multiprocessing as mp
+    import os
+    import torch
+    from paper_2102_04709_gb300 import adjoint
+
+    w = small_case()
+    steps, K = 200, 64
+    sim = gpu.Lbm3.from_workload(w)
+    idx = sim.wall_nodes()
+    a0 = w.angles.reshape(-1, 3)[idx].copy()
+    ang = torch.tensor(a0, dtype=torch.float64, requires_grad=True)
+    u = torch.tensor(w.u_in, dtype=torch.float64, requires_grad=True)
+    J = adjoint.centroid(sim, ang, u, w.rho, steps, K)
+    J.backward()
+    g = ang.grad.numpy()
+    jobs = [(w, idx, a0, steps, i, c, 1e-3) for i in range(len(idx)) for c in range(3)]
+    jobs.append((w, idx, a0, steps, 0, -1, 1e-6))
+    with mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+        fd = np.array(pool.map(_fd_component, jobs))
+    fd_ang, fd_u = fd[:-1].reshape(-1, 3), fd[-1]
+    scale = np.abs(fd_ang).max()
+    err = np.abs(g - fd_ang).max()
+    print(f"full gradient: {len(idx)} wall nodes, max |dJ/dangle| {scale:.3e}, "
+          f"max error {err:.3e}; dJ/du adjoint {u.grad.item():.6e} fd {fd_u:.6e}")
+    assert scale > 1e-7
+    assert err <= 1e-3 * scale
+    assert abs(u.grad.item() - fd_u) <= 1e-3 * abs(fd_u)
+
+
 def test_adjoint_leaves_final_state(gpu):
     """After lbm3_adjoint_centroid the simulation holds the same state as after lbm3_step."""
     w = pillar_case()
