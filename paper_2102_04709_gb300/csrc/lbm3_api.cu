@@ -651,7 +651,6 @@ int lbm3_info(const lbm3* h, int64_t out[8])
     for (int j = 0; j < 8; j++) out[j] = 0;
     out[0] = h->n_fluid;
     out[1] = h->nw;
-    // 27 FP32 populations read and written per fluid node, plus one class byte per node
     // populations read and written per fluid node: 27 FP32 (216 B), or per fluid an FP32 density
     // and 8 16-bit offsets (120 B); plus one class byte per node
     const long long per = h->precision == LBM3_FP32 ? 216 : 120;
