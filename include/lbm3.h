@@ -148,11 +148,13 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, dou
                           double* dJ_dangles, double* dJ_du);
 
 /* Size facts: out[0] = fluid nodes, out[1] = C_SB nodes, out[2] = algorithmic HBM bytes of the
- * fused step per timestep (216 B per fluid node + 1 class byte per node), out[3] = fused-step
- * launches per timestep, out[4] = wetting launches per timestep, out[5] = device bytes held by
- * the handle, out[6] = algorithmic bytes of the pure-tile launch (216 B per node), out[7] = nodes
- * in pure tiles. */
-int lbm3_info(const lbm3* h, int64_t out[8]);
+ * fused step per timestep (216 B per fluid node with FP32 storage, 120 B with 16-bit offsets,
+ * + 1 class byte per node), out[3] = fused-step launches per timestep, out[4] = wetting launches
+ * per timestep, out[5] = device bytes held by the handle, out[6] = algorithmic bytes of the
+ * pure-tile launch, out[7] = nodes in pure tiles, out[8] = 1 if the pure tiles move their
+ * populations with bulk tensor copies (FP32 storage, nx a multiple of 4, not disabled by
+ * LBM3_DISABLE_TMA=1 in the environment at lbm3_create), else 0. */
+int lbm3_info(const lbm3* h, int64_t out[9]);
 
 /* Change the stream used by later calls (cudaStream_t). */
 int lbm3_set_stream(lbm3* h, void* stream);

@@ -8,6 +8,8 @@
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/lbm3.h"
 #include "lbm3_common.cuh"
 
@@ -26,6 +28,12 @@ struct lbm3 {
     float* scratch = nullptr;      // 3N floats for fields
     double* partials = nullptr;    // diagnostics block partials
     double* dout = nullptr;        // 8 doubles
+    int* err_flag = nullptr;       // error bits set by kernels (Params::err)
+    // bulk-tensor-copy path of the pure tiles (FP32 storage, nx a multiple of 4): tensor maps
+    // of each population buffer as the source box and as the destination tile
+    bool tma = false;
+    int tma_blocks = 0;  // persistent blocks of that kernel: two per SM
+    CUtensorMap tm_in[2], tm_out[2];
     int* widx = nullptr;
     double* wnrm = nullptr;
     float* wang = nullptr;
@@ -110,13 +118,42 @@ void release(lbm3* h)
 {
     void* ptrs[] = {h->pop[0].f, h->pop[1].f, h->pop[0].rho, h->pop[1].rho, h->pop[0].off,
                     h->pop[1].off, h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
-                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen};
+                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->pop[0] = h->pop[1] = Pop{nullptr, nullptr, nullptr};
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->side) cudaStreamDestroy(h->side);
+}
+
+// Tensor maps of one [27][ny][nx] FP32 population buffer: as the pull-source box of a pure tile
+// (kTX + 8) x (kTY + 6) x 27 and as its destination tile kTX x kTY x 27.  false if the driver
+// has no encoder or refuses the layout (the plain kernel is used then).
+bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in, CUtensorMap* out)
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !fn) {
+            cudaGetLastError();
+            return false;
+        }
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 27};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.nx * sizeof(float), (cuuint64_t)P.N * sizeof(float)};
+    const cuuint32_t box_in[3] = {kTX + 8, kTY + 6, 27}, box_out[3] = {kTX, kTY, 27};
+    const cuuint32_t unit[3] = {1, 1, 1};
+    return encode(in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box_in, unit,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+           encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box_out, unit,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
@@ -131,7 +168,11 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
-    launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, true, fin, fo, h->type, h->Cw, u, h->stream);
+    if (h->tma)
+        launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in[h->cur],
+                        h->tm_out[1 - h->cur], h->stream);
+    else
+        launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, true, fin, fo, h->type, h->Cw, u, h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (ev) cudaEventRecord(ev[2], h->side);
     launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->side);
@@ -341,6 +382,9 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (e == cudaSuccess) e = dmalloc((void**)&h->scratch, 3 * N * sizeof(float));
     if (e == cudaSuccess) e = dmalloc((void**)&h->partials, (size_t)diag_blocks(P) * 8 * sizeof(double));
     if (e == cudaSuccess) e = dmalloc((void**)&h->dout, 8 * sizeof(double));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->err_flag, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->err_flag, 0, sizeof(int));
+    P.err = h->err_flag;
     if (e == cudaSuccess) e = dmalloc((void**)&h->widx, widx.size() * sizeof(int));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wnrm, wnrm.size() * sizeof(double));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wang, wang.size() * sizeof(float));
@@ -361,6 +405,20 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (e == cudaSuccess && !wang.empty()) e = cudaMemcpy(h->wang, wang.data(), wang.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->Cw, 0, 3 * N * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(h->u, 0, 2 * N * sizeof(float));
+    // pure FP32 tiles through bulk tensor copies where the layout allows them (row pitch a
+    // multiple of 16 bytes); LBM3_DISABLE_TMA=1 in the environment keeps the plain kernel
+    if (e == cudaSuccess && g->precision == LBM3_FP32 && nx % 4 == 0 && h->n_pure > 0) {
+        const char* off = std::getenv("LBM3_DISABLE_TMA");
+        if (!(off && off[0] == '1') && make_tensor_maps(P, h->pop[0].f, &h->tm_in[0], &h->tm_out[0]) &&
+            make_tensor_maps(P, h->pop[1].f, &h->tm_in[1], &h->tm_out[1])) {
+            int dev = 0, sms = 0;
+            e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = step_tma_prepare();
+            h->tma_blocks = 2 * sms;
+            h->tma = e == cudaSuccess && sms > 0;
+        }
+    }
     if (e != cudaSuccess) {
         const int code = e == cudaErrorMemoryAllocation ? LBM3_ERR_OOM : LBM3_ERR_CUDA;
         release(h);
@@ -456,7 +514,10 @@ int lbm3_diag(lbm3* h, double out[8])
     launch_diag(h->precision, h->P, h->pop[h->cur], h->type, h->u, h->partials, h->dout, h->stream);
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaMemcpyAsync(out, h->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    int bits = 0;
+    CUDA_TRY(h, cudaMemcpyAsync(&bits, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (bits & 1) return fail(h, LBM3_ERR_CUDA, "a bulk tensor copy of the step kernel did not complete in time");
     if (out[7] > 0.0 || !(out[6] > 0.0)) return fail(h, LBM3_ERR_DIVERGED, "non-finite or non-positive density");
     return LBM3_OK;
 }
@@ -645,10 +706,10 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
     return LBM3_OK;
 }
 
-int lbm3_info(const lbm3* h, int64_t out[8])
+int lbm3_info(const lbm3* h, int64_t out[9])
 {
     if (!h || !out) return LBM3_ERR_INVALID;
-    for (int j = 0; j < 8; j++) out[j] = 0;
+    for (int j = 0; j < 9; j++) out[j] = 0;
     out[0] = h->n_fluid;
     out[1] = h->nw;
     // populations read and written per fluid node: 27 FP32 (216 B), or per fluid an FP32 density
@@ -661,6 +722,7 @@ int lbm3_info(const lbm3* h, int64_t out[8])
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes
     out[6] = h->pure_fluid * per;
     out[7] = h->pure_fluid;
+    out[8] = h->tma ? 1 : 0;
     return LBM3_OK;
 }
 

@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -59,6 +60,8 @@ struct Params {
     // reduced storage: element offsets k * N - e_ax - e_ay * nx of the pull sources in the rho and
     // offset-record planes
     int off_pull16[27];
+    // device word of error bits set by kernels (bit 0: a bulk tensor copy did not complete)
+    int* err;
 };
 
 // One population buffer.  FP32 storage: f[27][N], plane k*9+a, the post-collision populations
@@ -291,6 +294,13 @@ void launch_wet_init(int store, const Params& P, int nw, const int* widx, const 
 constexpr int kTX = 32, kTY = 8;
 // tiles: list of tile indices ty * ceil(nx / kTX) + tx; pure = every listed tile is free of solid
 // nodes within 3 nodes of it and away from the domain edges
+// pure FP32 tiles through bulk tensor copies (persistent, nblocks blocks): the dynamic shared
+// memory they need, the one-time attribute set-up, and the launch with tensor maps of fin
+// (box (kTX + 8, kTY + 6, 27)) and fout (box (kTX, kTY, 27)) over the [27][ny][nx] buffers
+size_t step_tma_smem_bytes();
+cudaError_t step_tma_prepare();
+void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
+                     const CUtensorMap& tin, const CUtensorMap& tout, cudaStream_t s);
 void launch_step(int store, const Params& P, const int* tiles, int ntiles, bool pure, const Pop& fin,
                  const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s);
 void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,

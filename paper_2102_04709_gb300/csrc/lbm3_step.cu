@@ -201,6 +201,64 @@ __device__ __forceinline__ void grad9_df(const float (*h)[W], const float (*l)[W
     gy = hy + ly_;
 }
 
+// ---- tensor memory accelerator (bulk tensor copies) and mbarrier, inline PTX ----
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// 3-D tiled load of a box at (x, y, z) into shared memory, completing on the mbarrier; x times
+// the element size must be a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src)
+{
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
+                 "r"(x), "r"(y), "r"(z), "r"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until the committed bulk stores have read their shared-memory source
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// make this thread's shared-memory writes visible to the bulk copy engine
+__device__ __forceinline__ void fence_proxy_async_smem()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// polls of an mbarrier before a block gives up on a bulk copy (each poll may suspend the thread
+// for a short time; a completed copy takes a few microseconds)
+constexpr int kWaitLimit = 1 << 22;
+
 // A C_SB node whose wall values are not all within kMixEps of one pure fluid: a fluid-fluid
 // interface reaches the wall there (a contact line, or one within a few nodes of it), where the
 // lagged wetting feedback amplifies the rounding of single-precision phase fields.  Away from
@@ -220,6 +278,67 @@ __device__ __forceinline__ void grad9_f(const float (*c)[W], int cx, int cy, flo
     const float c5 = c[cy + 1][cx + 1], c6 = c[cy + 1][cx - 1], c7 = c[cy - 1][cx - 1], c8 = c[cy - 1][cx + 1];
     gx = (1.0f / 3.0f) * (c1 - c3) + (1.0f / 12.0f) * ((c5 - c7) + (c8 - c6));
     gy = (1.0f / 3.0f) * (c2 - c4) + (1.0f / 12.0f) * ((c5 - c7) + (c6 - c8));
+}
+
+// F_s = div T at (rx, ry) of the stress region: Eq.(10) with the Eq.(12) derivative
+template <int RX>
+__device__ __forceinline__ void div_stress(const float (*txx)[RX], const float (*txy)[RX],
+                                           const float (*tyy)[RX], int rx, int ry, float& Fx, float& Fy)
+{
+    Fx = (1.0f / 3.0f) * (txx[ry][rx + 1] - txx[ry][rx - 1]) +
+         (1.0f / 12.0f) * ((txx[ry + 1][rx + 1] - txx[ry - 1][rx - 1]) + (txx[ry - 1][rx + 1] - txx[ry + 1][rx - 1])) +
+         (1.0f / 3.0f) * (txy[ry + 1][rx] - txy[ry - 1][rx]) +
+         (1.0f / 12.0f) * ((txy[ry + 1][rx + 1] - txy[ry - 1][rx - 1]) + (txy[ry + 1][rx - 1] - txy[ry - 1][rx + 1]));
+    Fy = (1.0f / 3.0f) * (txy[ry][rx + 1] - txy[ry][rx - 1]) +
+         (1.0f / 12.0f) * ((txy[ry + 1][rx + 1] - txy[ry - 1][rx - 1]) + (txy[ry - 1][rx + 1] - txy[ry + 1][rx - 1])) +
+         (1.0f / 3.0f) * (tyy[ry + 1][rx] - tyy[ry - 1][rx]) +
+         (1.0f / 12.0f) * ((tyy[ry + 1][rx + 1] - tyy[ry - 1][rx - 1]) + (tyy[ry + 1][rx - 1] - tyy[ry - 1][rx + 1]));
+}
+
+// the recoloured post-collision populations of one node are C_k f_a + w_a (Vx_k e_ax + Vy_k e_ay)
+struct Recolour {
+    float C[kNF], Vx[kNF], Vy[kNF];
+};
+
+// One node: velocity (Eq.11), mixture relaxation (Eq.7), MRT collision with forcing (Eq.1-9)
+// applied in place to the 9 post-streaming totals f, and the recolouring coefficients of
+// Eq.(13)-(15) from the fluid densities r0..r2 and the colour gradients g = (d C_k / dx, dy).
+__device__ __forceinline__ Recolour collide_node(const Params& P, float f[kQ], float r0, float r1, float r2,
+                                                 float Fx, float Fy, const float g[6], float& ux, float& uy)
+{
+    const float rho = (r0 + r1) + r2;
+    const float ir = __fdividef(1.0f, rho);
+    // fractions as the quotient corrected by its exact FMA residual: a node that holds one fluid
+    // gets exactly C = 1, so the recolouring leaves its mass unscaled (r * fl(1/r) can round
+    // below 1 every step)
+    auto frac = [&](float r) {
+        const float q = r * ir;
+        return fmaf(fmaf(-q, rho, r), ir, q);
+    };
+    const float c0 = frac(r0), c1 = frac(r1), c2 = frac(r2);
+    float n01x, n01y, n02x, n02y, n12x, n12y;
+    pair_normal(c0, c1, g[0], g[1], g[2], g[3], n01x, n01y);
+    pair_normal(c0, c2, g[0], g[1], g[4], g[5], n02x, n02y);
+    pair_normal(c1, c2, g[2], g[3], g[4], g[5], n12x, n12y);
+    // tau = 1/2 + 3 / sum(rho_k / nu_k), so 1/tau = D / (D/2 + 3)
+    const float D = (r0 * P.inv_nu0 + r1 * P.inv_nu1) + r2 * P.inv_nu2;
+    const float s1 = __fdividef(D, 0.5f * D + 3.0f);
+    collide_mrt(f, rho, Fx, Fy, s1, ux, uy);
+    const float trip = fminf(35.0f * r0 * r1 * r2 * ir * ir * ir, 1.0f);
+    const float b01 = P.beta0 * (1.0f + trip * P.g01) * r0 * r1 * ir;
+    const float b02 = P.beta0 * (1.0f + trip * P.g02) * r0 * r2 * ir;
+    const float b12 = P.beta0 * (1.0f + trip * P.g12) * r1 * r2 * ir;
+    Recolour rc;
+    rc.C[0] = c0;
+    rc.C[1] = c1;
+    rc.C[2] = c2;
+    rc.Vx[0] = b01 * n01x + b02 * n02x;
+    rc.Vy[0] = b01 * n01y + b02 * n02y;
+    rc.Vx[1] = -b01 * n01x + b12 * n12x;
+    rc.Vy[1] = -b01 * n01y + b12 * n12y;
+    rc.Vx[2] = -b02 * n02x - b12 * n12x;
+    rc.Vy[2] = -b02 * n02y - b12 * n12y;
+    return rc;
 }
 
 // One CTA per TX x TY tile of interior nodes.
@@ -531,61 +650,21 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
     if (!own_fluid || gx >= P.nx || gy >= P.ny) return;
 
     // ---- interfacial force F_s = div T (Eq.10 with Eq.12) ----
-    const int rx = lx + 1, ry = ly + 1;
-    const float Fx = (1.0f / 3.0f) * (s_txx[ry][rx + 1] - s_txx[ry][rx - 1]) +
-                     (1.0f / 12.0f) * ((s_txx[ry + 1][rx + 1] - s_txx[ry - 1][rx - 1]) +
-                                       (s_txx[ry - 1][rx + 1] - s_txx[ry + 1][rx - 1])) +
-                     (1.0f / 3.0f) * (s_txy[ry + 1][rx] - s_txy[ry - 1][rx]) +
-                     (1.0f / 12.0f) * ((s_txy[ry + 1][rx + 1] - s_txy[ry - 1][rx - 1]) +
-                                       (s_txy[ry + 1][rx - 1] - s_txy[ry - 1][rx + 1]));
-    const float Fy = (1.0f / 3.0f) * (s_txy[ry][rx + 1] - s_txy[ry][rx - 1]) +
-                     (1.0f / 12.0f) * ((s_txy[ry + 1][rx + 1] - s_txy[ry - 1][rx - 1]) +
-                                       (s_txy[ry - 1][rx + 1] - s_txy[ry + 1][rx - 1])) +
-                     (1.0f / 3.0f) * (s_tyy[ry + 1][rx] - s_tyy[ry - 1][rx]) +
-                     (1.0f / 12.0f) * ((s_tyy[ry + 1][rx + 1] - s_tyy[ry - 1][rx - 1]) +
-                                       (s_tyy[ry + 1][rx - 1] - s_tyy[ry - 1][rx + 1]));
-
-    // ---- own colour gradients (from phase 2) and pair normals ----
-    const float rho = (r0 + r1) + r2;
-    const float ir = __fdividef(1.0f, rho);
-    // fractions as the quotient corrected by its exact FMA residual: a node that holds one fluid
-    // gets exactly C = 1, so the recolouring below leaves its mass unscaled (r * fl(1/r) can
-    // round below 1 every step)
-    auto frac = [&](float r) {
-        const float q = r * ir;
-        return fmaf(fmaf(-q, rho, r), ir, q);
-    };
-    const float c0 = frac(r0), c1 = frac(r1), c2 = frac(r2);
-    const float g0x = s_g[0][ly][lx], g0y = s_g[1][ly][lx];
-    const float g1x = s_g[2][ly][lx], g1y = s_g[3][ly][lx];
-    const float g2x = s_g[4][ly][lx], g2y = s_g[5][ly][lx];
-    float n01x, n01y, n02x, n02y, n12x, n12y;
-    pair_normal(c0, c1, g0x, g0y, g1x, g1y, n01x, n01y);
-    pair_normal(c0, c2, g0x, g0y, g2x, g2y, n02x, n02y);
-    pair_normal(c1, c2, g1x, g1y, g2x, g2y, n12x, n12y);
-
-    // ---- MRT collision with forcing (Eq.1-9, 11), mixture tau of Eq.(7) ----
-    // tau = 1/2 + 3 / sum(rho_k / nu_k), so 1/tau = D / (D/2 + 3)
-    const float D = (r0 * P.inv_nu0 + r1 * P.inv_nu1) + r2 * P.inv_nu2;
-    const float s1 = __fdividef(D, 0.5f * D + 3.0f);
+    float Fx, Fy;
+    div_stress<RX>(s_txx, s_txy, s_tyy, lx + 1, ly + 1, Fx, Fy);
+    // ---- velocity, MRT collision with forcing, recolouring coefficients ----
+    const float g[6] = {s_g[0][ly][lx], s_g[1][ly][lx], s_g[2][ly][lx],
+                        s_g[3][ly][lx], s_g[4][ly][lx], s_g[5][ly][lx]};
     float ux, uy;
-    collide_mrt(f, rho, Fx, Fy, s1, ux, uy);
+    const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, g, ux, uy);
     const int i = gy * nx + gx;
     if (uout) {
         uout[i] = ux;
         uout[N + i] = uy;
     }
-
-    // ---- recolouring, Eq.(13)-(15) ----
-    const float trip = fminf(35.0f * r0 * r1 * r2 * ir * ir * ir, 1.0f);
-    const float b01 = P.beta0 * (1.0f + trip * P.g01) * r0 * r1 * ir;
-    const float b02 = P.beta0 * (1.0f + trip * P.g02) * r0 * r2 * ir;
-    const float b12 = P.beta0 * (1.0f + trip * P.g12) * r1 * r2 * ir;
-    const float V0x = b01 * n01x + b02 * n02x, V0y = b01 * n01y + b02 * n02y;
-    const float V1x = -b01 * n01x + b12 * n12x, V1y = -b01 * n01y + b12 * n12y;
-    const float V2x = -b02 * n02x - b12 * n12x, V2y = -b02 * n02y - b12 * n12y;
-    const float Cs[3] = {c0, c1, c2};
-    const float Vx[3] = {V0x, V1x, V2x}, Vy[3] = {V0y, V1y, V2y};
+    const float* Cs = rc.C;
+    const float* Vx = rc.Vx;
+    const float* Vy = rc.Vy;
     if constexpr (STORE == kStoreF32) {
         float* o = fout.f + i;
 #pragma unroll
@@ -608,6 +687,202 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
 }
 
 
+
+// Pure FP32 tiles through the tensor memory accelerator, persistent: block b handles tiles
+// b, b + gridDim.x, ...  For each tile the 27 pull-source planes over the (TX + 8) x (TY + 6)
+// box starting at (x0 - 4, y0 - 3) -- x rounded down to a 16-byte boundary -- arrive by one bulk
+// tensor copy completing on an mbarrier, and the pulls read them at compile-time offsets.  The
+// box is needed only for the pulls: as soon as they are done the copy of the next tile's box is
+// issued, so it lands while this tile computes its stress, force, collision and recolouring.
+// The 27 output planes are staged in shared memory and leave by one bulk tensor store.
+// Two blocks per SM (103 KB of shared memory each).  Same arithmetic as k_step<PURE>, so the
+// two give identical results.
+template <int TX, int TY, bool STAGE>
+__global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const int* __restrict__ tiles,
+                                                        const int ntiles, float* __restrict__ fout,
+                                                        float* __restrict__ uout,
+                                                        const __grid_constant__ CUtensorMap tm_in,
+                                                        const __grid_constant__ CUtensorMap tm_out)
+{
+    constexpr int NT = TX * TY;
+    constexpr int CX = TX + 4, CY = TY + 4;  // phase-field region (halo 2)
+    constexpr int RX = TX + 2, RY = TY + 2;  // stress region (halo 1)
+    constexpr int BX = TX + 8, BY = TY + 6;  // pull-source box
+    constexpr int NBOX = kQ * kNF * BY * BX;
+    constexpr int NBOXP = (NBOX + 31) / 32 * 32;  // keeps the staging buffer 128-byte aligned
+    __shared__ float s_ch[kNF][CY][CX];
+    __shared__ float s_rho[CY][CX];
+    __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
+    __shared__ float s_g[2 * kNF][TY][TX];
+    __shared__ __align__(8) uint64_t s_bar;
+    extern __shared__ unsigned char dsm[];
+    float* box = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [27][BY][BX]
+    float* outb = box + NBOXP;                                                              // [27][TY][TX]
+
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int ntx = (P.nx + TX - 1) / TX;
+    const uint32_t bar = smem_u32(&s_bar);
+    if ((int)blockIdx.x >= ntiles) return;
+    auto issue = [&](int t) {
+        const int tile = tiles[t];
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        mbar_arrive_expect_tx(bar, (uint32_t)NBOX * 4u);
+        tma_load_3d(smem_u32(box), &tm_in, x0 - 4, y0 - 3, 0, bar);
+    };
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        issue(blockIdx.x);
+    }
+    __syncthreads();
+
+    // pull of the node at (cx, cy) of the phase-field region from the box
+    auto pull = [&](int cx, int cy, float q[27]) {
+#pragma unroll
+        for (int a = 0; a < kQ; a++)
+#pragma unroll
+            for (int k = 0; k < kNF; k++)
+                q[9 * k + a] = box[((k * kQ + a) * BY + cy + 1 - ey(a)) * BX + cx + 2 - ex(a)];
+    };
+    auto store_phase = [&](int cx, int cy, const float q[27]) {
+        float r[kNF];
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            const float* qk = q + 9 * k;
+            r[k] = ((qk[0] + (qk[1] + qk[3])) + (qk[2] + qk[4])) + ((qk[5] + qk[7]) + (qk[6] + qk[8]));
+        }
+        const float rho = (r[0] + r[1]) + r[2];
+        const float ir = __fdividef(1.0f, rho);
+#pragma unroll
+        for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = r[k] * ir;
+        s_rho[cy][cx] = rho;
+    };
+
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, j++) {
+        const int tile = tiles[t];
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        bool ok = false;
+        for (int it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(bar, j & 1);
+        if (__syncthreads_or(!ok)) {
+            // the copy did not complete in time: record it, give it a second bounded wait so
+            // that it does not land in a later block's shared memory, and stop
+            if (tid == 0) {
+                atomicOr(P.err, 1);
+                for (int it = 0; it < kWaitLimit && !mbar_try_wait(bar, j & 1); it++) {
+                }
+                bulk_wait_read0();
+            }
+            return;
+        }
+
+        // ---- phase 1: pulls, densities and phase fields of the halo-2 region ----
+        {
+            constexpr int NRING = CX * CY - TX * TY;
+            for (int r = tid; r < NRING; r += NT) {
+                int cx, cy;
+                if (r < 2 * CX) {
+                    cx = r % CX;
+                    cy = r / CX;
+                } else if (r < 4 * CX) {
+                    cx = (r - 2 * CX) % CX;
+                    cy = CY - 2 + (r - 2 * CX) / CX;
+                } else {
+                    const int rr0 = r - 4 * CX;  // 4 * TY side nodes
+                    const int side = rr0 / (2 * TY), rr = rr0 % (2 * TY);
+                    cy = 2 + rr / 2;
+                    cx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
+                }
+                float q[27];
+                pull(cx, cy, q);
+                store_phase(cx, cy, q);
+            }
+        }
+        float f[kQ], r0, r1, r2;
+        {
+            float q[27];
+            pull(lx + 2, ly + 2, q);
+            store_phase(lx + 2, ly + 2, q);
+#pragma unroll
+            for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
+            r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+            r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
+            r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+        }
+        __syncthreads();
+        // the box is free: fetch the next tile's while this one computes
+        if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+
+        // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
+        for (int r = tid; r < RX * RY; r += NT) {
+            const int rx = r % RX, ry = r / RX;
+            const int cx = rx + 1, cy = ry + 1;
+            const float rho = s_rho[cy][cx];
+            float c[kNF], gxk[kNF], gyk[kNF];
+#pragma unroll
+            for (int k = 0; k < kNF; k++) {
+                c[k] = s_ch[k][cy][cx];
+                grad9_f<CX>(s_ch[k], cx, cy, gxk[k], gyk[k]);
+            }
+            if (rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) {
+#pragma unroll
+                for (int k = 0; k < kNF; k++) {
+                    s_g[2 * k][ry - 1][rx - 1] = gxk[k];
+                    s_g[2 * k + 1][ry - 1][rx - 1] = gyk[k];
+                }
+            }
+            float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
+            const float rho2 = rho * rho;
+            pair_stress(P.sig01, c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
+            pair_stress(P.sig02, c[0], c[2], gxk[0], gyk[0], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+            pair_stress(P.sig12, c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+            s_txx[ry][rx] = Txx;
+            s_txy[ry][rx] = Txy;
+            s_tyy[ry][rx] = Tyy;
+        }
+        // the previous tile's bulk store must have read the staging buffer before it is refilled
+        if (STAGE && tid == 0) bulk_wait_read0();
+        __syncthreads();
+
+        // ---- phase 3: force, collision, recolouring into the staging buffer ----
+        float Fx, Fy;
+        div_stress<RX>(s_txx, s_txy, s_tyy, lx + 1, ly + 1, Fx, Fy);
+        const float g[6] = {s_g[0][ly][lx], s_g[1][ly][lx], s_g[2][ly][lx],
+                            s_g[3][ly][lx], s_g[4][ly][lx], s_g[5][ly][lx]};
+        float ux, uy;
+        const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, g, ux, uy);
+        if (uout) {
+            const int i = (y0 + ly) * P.nx + x0 + lx;
+            uout[i] = ux;
+            uout[P.N + i] = uy;
+        }
+        if constexpr (STAGE) {
+            float* o = outb + ly * TX + lx;
+#pragma unroll
+            for (int k = 0; k < kNF; k++)
+#pragma unroll
+                for (int a = 0; a < kQ; a++)
+                    o[(k * kQ + a) * TY * TX] =
+                        rc.C[k] * f[a] + wq(a) * (rc.Vx[k] * (float)ex(a) + rc.Vy[k] * (float)ey(a));
+            fence_proxy_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                tma_store_3d(&tm_out, x0, y0, 0, smem_u32(outb));
+                bulk_commit();
+            }
+        } else {
+            float* o = fout + (y0 + ly) * P.nx + x0 + lx;
+#pragma unroll
+            for (int k = 0; k < kNF; k++)
+#pragma unroll
+                for (int a = 0; a < kQ; a++)
+                    o[P.off_plane[k * kQ + a]] =
+                        rc.C[k] * f[a] + wq(a) * (rc.Vx[k] * (float)ex(a) + rc.Vy[k] * (float)ey(a));
+        }
+    }
+    if (STAGE && tid == 0) bulk_wait_read0();
+}
 
 // ------------------------------------------------------------------------------------------
 // initial state, fields, diagnostics
@@ -827,6 +1102,32 @@ void launch_step(int store, const Params& P, const int* tiles, int ntiles, bool 
         launch_step_t<kStoreF16>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
     else
         launch_step_t<kStoreBF16>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
+}
+
+// output path of the TMA kernel: staged in shared memory and written by one bulk tensor store per
+// tile, or written directly (a smaller shared-memory footprint leaves room on each SM for blocks
+// of the wall-tile kernel, which runs concurrently)
+constexpr bool kTmaStage = false;
+
+size_t step_tma_smem_bytes()
+{
+    const size_t nbox = ((size_t)kQ * kNF * (kTY + 6) * (kTX + 8) + 31) / 32 * 32;
+    return (nbox + (kTmaStage ? (size_t)kQ * kNF * kTY * kTX : 0)) * sizeof(float) + 128u;
+}
+
+cudaError_t step_tma_prepare()
+{
+    return cudaFuncSetAttribute(k_step_tma<kTX, kTY, kTmaStage>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_tma_smem_bytes());
+}
+
+void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
+                     const CUtensorMap& tin, const CUtensorMap& tout, cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    const int nb = nblocks < ntiles ? nblocks : ntiles;
+    k_step_tma<kTX, kTY, kTmaStage>
+        <<<nb, dim3(kTX, kTY), step_tma_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin, tout);
 }
 
 void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,
