@@ -1,0 +1,169 @@
+"""The 4096 x 2048 pillar workload in the launch configuration that bench.py times (persistent
+bulk-tensor-copy kernel for the pure tiles, wetting pass and wall tiles on the side stream),
+compared element by element with the FP64 oracle on sampled 64 x 64 windows after 8 steps.
+
+The oracle runs each window with a margin of 20 nodes per step around it: in one step a value
+depends on nodes at most 3 away through the stencils (pull, Eq.12 gradient, Eq.10 divergence)
+and at most 16 away through a characteristic line, so whatever the window's artificial edges
+(periodic wrap, or a Zou-He outlet) do cannot reach the sampled region.  Tolerance as in the
+parity tests: |d rho_k| <= 1e-5, |d u| <= 1e-6."""
+import numpy as np
+import pytest
+
+from paper_2102_04709_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STEPS = 8
+M = 20 * STEPS
+OUT = 64
+
+
+@pytest.fixture(scope="module")
+def full_run():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2102_04709_gb300 import build, lbm3
+    build.build()
+    lbm3.load()
+    w = W.config4()
+    sim = lbm3.Lbm3.from_workload(w)
+    info = sim.info()
+    sim.step(STEPS)
+    rho, u = sim.fields()
+    d = sim.diag()
+    sim.close()
+    return w, info, rho, u, d
+
+
+def oracle_window(oracle_mod, w, x0, y0, zou_he=False, roll_y=0):
+    """Oracle fields on the output region [x0, x0 + OUT) x [y0, y0 + OUT) of w (after rolling
+    w by roll_y rows), from a window with margin M (none on the inlet side for zou_he)."""
+    solid = np.roll(w.solid, roll_y, axis=0)
+    rho = np.roll(w.rho, roll_y, axis=1)
+    ang = np.roll(w.angles, roll_y, axis=0)
+    xa = 0 if zou_he else x0 - M
+    xb = x0 + OUT + M
+    ya, yb = y0 - M, y0 + OUT + M
+    sl = (slice(ya, yb), slice(xa, xb))
+    win = W.Workload("window", xb - xa, yb - ya, 1, W.BC_ZOUHE if zou_he else W.BC_PERIODIC,
+                     solid[sl].copy(), rho[:, sl[0], sl[1]].copy(), ang[sl].copy(), w.sigma, w.nu,
+                     w.beta0, u_in=w.u_in if zou_he else 0.0, rho_out=w.rho_out)
+    o = oracle_mod.Oracle.from_workload(win)
+    o.step(STEPS)
+    r, v = o.fields()
+    ox, oy = x0 - xa, y0 - ya
+    return r[:, oy:oy + OUT, ox:ox + OUT], v[:, oy:oy + OUT, ox:ox + OUT]
+
+
+def gpu_window(field, x0, y0, roll_y=0):
+    f = np.roll(field, roll_y, axis=1)
+    return f[:, y0:y0 + OUT, x0:x0 + OUT]
+
+
+def check(full, oracle_mod, x0, y0, zou_he=False, want_solid=False, want_mixed=False):
+    """Output region [x0, x0 + OUT) x [y0, y0 + OUT) of the periodic-in-y grid (y0 may be
+    negative or close to an edge: the grid is rolled so that the region starts at row M)."""
+    w, _, rho, u, _ = full
+    roll_y = M - y0
+    ro, uo = oracle_window(oracle_mod, w, x0, M, zou_he, roll_y)
+    rg, ug = gpu_window(rho, x0, M, roll_y), gpu_window(u, x0, M, roll_y)
+    if want_solid:
+        assert np.roll(w.solid, roll_y, axis=0)[M:M + OUT, x0:x0 + OUT].any()
+    if want_mixed:  # an interface crosses the window
+        assert ((ro > 0.01) & (ro < 0.99)).any()
+    err, erru = np.abs(rg - ro).max(), np.abs(ug - uo).max()
+    assert err <= 1e-5, f"max |d rho_k| = {err:.3e}"
+    assert erru <= 1e-6, f"max |d u| = {erru:.3e}"
+
+
+def test_fullsize_launch_configuration(full_run):
+    w, info, _, _, d = full_run
+    assert (w.nx, w.ny) == (4096, 2048)
+    assert info["tma"] and info["pure_nodes"] > 0.9 * info["n_fluid"]
+    assert d[7] == 0 and d[6] > 0.9
+
+
+def test_fullsize_shell_interface(full_run, oracle_mod):
+    check(full_run, oracle_mod, 568, 992, want_mixed=True)
+
+
+def test_fullsize_core_interface(full_run, oracle_mod):
+    check(full_run, oracle_mod, 488, 992, want_mixed=True)
+
+
+def test_fullsize_first_pillar(full_run, oracle_mod):
+    w = full_run[0]
+    ys, xs = np.nonzero(w.solid)
+    j = np.argmin(xs)
+    check(full_run, oracle_mod, int(xs[j]) - 32, int(ys[j]) - 32, want_solid=True)
+
+
+def test_fullsize_zou_he_inlet(full_run, oracle_mod):
+    check(full_run, oracle_mod, 0, 992, zou_he=True)
+
+
+def test_fullsize_periodic_seam(full_run, oracle_mod):
+    """Rows 2016..2047 and 0..31: the y seam."""
+    check(full_run, oracle_mod, 1500, -32)
+
+
+def test_largest_grid_the_abi_accepts(oracle_mod):
+    """8192 x 9700: 27 nx ny = 2,145,484,800, just below the 2^31 limit of the 32-bit population
+    offsets (17 GB of FP32 populations).  A Janus droplet against a disc at the far corner of the
+    periodic box, where any overflow of the index arithmetic would show: a 64 x 64 window there
+    against the oracle after 8 steps, per-fluid mass over the whole grid, no non-finite value."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2102_04709_gb300 import build, lbm3
+    build.build()
+    lbm3.load()
+    nx, ny = 8192, 9700
+    assert 27 * nx * ny < 2 ** 31 <= 27 * nx * (ny + 10)
+    cx, cy = nx - 100, ny - 100
+    solid = np.zeros((ny, nx), np.uint8)
+    yy, xx = np.ogrid[cy - 40:cy + 41, cx - 40:cx + 41]
+    solid[cy - 40:cy + 41, cx - 40:cx + 41] = ((xx - cx) ** 2 + (yy - cy) ** 2 <= 30 ** 2)
+    rho = np.zeros((3, ny, nx))
+    rho[2] = 1.0
+    dx0, r = cx - 75, 45
+    yy, xx = np.ogrid[cy - r:cy + r + 1, dx0 - r:dx0 + r + 1]
+    disc = (xx - dx0) ** 2 + (yy - cy) ** 2 <= r * r
+    left = np.broadcast_to(xx < dx0, disc.shape)
+    sub = (slice(cy - r, cy + r + 1), slice(dx0 - r, dx0 + r + 1))
+    rho[2][sub][disc] = 0.0
+    rho[0][sub][disc & left] = 1.0
+    rho[1][sub][disc & ~left] = 1.0
+    rho[:, solid.astype(bool)] = 0.0
+    angles = np.broadcast_to(np.array([90.0, 60.0, 120.0]), (ny, nx, 3))
+    w = W.Workload("largest", nx, ny, 1, W.BC_PERIODIC, solid, rho, angles, (0.01, 0.01, 0.01),
+                   (0.1, 0.1, 0.1))
+    sim = lbm3.Lbm3.from_workload(w)
+    assert sim.info()["tma"]
+    d0 = sim.diag()
+    sim.step(STEPS)
+    d1 = sim.diag()
+    rg, ug = sim.fields()
+    sim.close()
+    assert d1[7] == 0
+    assert np.all(np.abs(d1[:3] - d0[:3]) <= 1e-6 * np.maximum(d0[:3], 1.0))
+    # the window [x0, x0 + 64) x [y0, y0 + 64) around the contact of droplet and disc, with the
+    # grid rolled so that its oracle window (margin M) does not wrap
+    x0, y0 = cx - 62, cy - 32
+    rx, ry = M - x0, M - y0
+    sl = (slice(0, OUT + 2 * M), slice(0, OUT + 2 * M))
+    win = W.Workload("largest_window", OUT + 2 * M, OUT + 2 * M, 1, W.BC_PERIODIC,
+                     np.roll(solid, (ry, rx), (0, 1))[sl].copy(),
+                     np.roll(rho, (ry, rx), (1, 2))[:, sl[0], sl[1]].copy(),
+                     np.ascontiguousarray(angles[:OUT + 2 * M, :OUT + 2 * M]), w.sigma, w.nu)
+    o = oracle_mod.Oracle.from_workload(win)
+    o.step(STEPS)
+    ro, uo = o.fields()
+    ro, uo = ro[:, M:M + OUT, M:M + OUT], uo[:, M:M + OUT, M:M + OUT]
+    rg = np.roll(rg, (ry, rx), (1, 2))[:, M:M + OUT, M:M + OUT]
+    ug = np.roll(ug, (ry, rx), (1, 2))[:, M:M + OUT, M:M + OUT]
+    assert ((ro > 0.01) & (ro < 0.99)).any()
+    assert np.abs(rg - ro).max() <= 1e-5
+    assert np.abs(ug - uo).max() <= 1e-6
