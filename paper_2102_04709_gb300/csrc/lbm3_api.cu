@@ -32,7 +32,7 @@ struct lbm3 {
     // bulk-tensor-copy path of the pure tiles (FP32 storage, nx a multiple of 4): tensor maps
     // of each population buffer as the source box and as the destination tile
     bool tma = false;
-    int tma_blocks = 0;  // persistent blocks of that kernel: two per SM
+    int tma_blocks = 0;  // persistent blocks of that kernel: kTmaBlocksPerSm per SM
     CUtensorMap tm_in[2], tm_out[2];
     int* widx = nullptr;
     double* wnrm = nullptr;
@@ -45,6 +45,7 @@ struct lbm3 {
     int* tiles_pure = nullptr;
     int* tiles_gen = nullptr;
     int n_pure = 0, n_gen = 0;
+    int n_walltiles = 0;  // tiles_gen lists the inner wall tiles first, then the edge tiles
     long long pure_fluid = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -172,12 +173,16 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
         launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in[h->cur],
                         h->tm_out[1 - h->cur], h->stream);
     else
-        launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, true, fin, fo, h->type, h->Cw, u, h->stream);
+        launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, kTilesPure, fin, fo, h->type, h->Cw, u,
+                    h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (ev) cudaEventRecord(ev[2], h->side);
     launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->side);
     if (ev) cudaEventRecord(ev[3], h->side);
-    launch_step(h->precision, h->P, h->tiles_gen, h->n_gen, false, fin, fo, h->type, h->Cw, u, h->side);
+    launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
+                h->side);
+    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge, fin,
+                fo, h->type, h->Cw, u, h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
@@ -296,7 +301,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     }
 
     // ---- tiles of the fused step kernel (2-D prefix sums of the solid mask)
-    std::vector<int> tp, tg;
+    std::vector<int> tp, tg, te;
     long long pure_fluid = 0;
     {
         std::vector<long long> ps((size_t)(nx + 1) * (ny + 1), 0);
@@ -318,11 +323,15 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                 if (inner && box(x0 - 3, y0 - 3, x0 + kTX + 3, y0 + kTY + 3) == 0) {
                     tp.push_back(ty * ntx + tx);
                     pure_fluid += (long long)kTX * kTY;
-                } else {
+                } else if (inner) {
                     tg.push_back(ty * ntx + tx);
+                } else {
+                    te.push_back(ty * ntx + tx);
                 }
             }
     }
+    const int n_wall_tiles = (int)tg.size();
+    tg.insert(tg.end(), te.begin(), te.end());
 
     // ---- parameters
     lbm3* h = new lbm3();
@@ -358,6 +367,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     h->n_fluid = n_fluid;
     h->n_pure = (int)tp.size();
     h->n_gen = (int)tg.size();
+    h->n_walltiles = n_wall_tiles;
     h->pure_fluid = pure_fluid;
     h->wall_host = widx;
 
@@ -415,7 +425,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
             e = cudaGetDevice(&dev);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
             if (e == cudaSuccess) e = step_tma_prepare();
-            h->tma_blocks = 2 * sms;
+            h->tma_blocks = kTmaBlocksPerSm * sms;
             h->tma = e == cudaSuccess && sms > 0;
         }
     }
@@ -716,7 +726,7 @@ int lbm3_info(const lbm3* h, int64_t out[9])
     // and 8 16-bit offsets (120 B); plus one class byte per node
     const long long per = h->precision == LBM3_FP32 ? 216 : 120;
     out[2] = h->n_fluid * per + h->P.N;
-    out[3] = (h->n_pure > 0) + (h->n_gen > 0);
+    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_gen > h->n_walltiles);
     out[4] = h->nw > 0 ? 1 : 0;
     out[5] = (int64_t)h->bytes;
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes

@@ -297,11 +297,16 @@ constexpr int kTX = 32, kTY = 8;
 // pure FP32 tiles through bulk tensor copies (persistent, nblocks blocks): the dynamic shared
 // memory they need, the one-time attribute set-up, and the launch with tensor maps of fin
 // (box (kTX + 8, kTY + 6, 27)) and fout (box (kTX, kTY, 27)) over the [27][ny][nx] buffers
+constexpr int kTmaBlocksPerSm = 2;  // resident blocks of the persistent pure-tile kernel per SM
 size_t step_tma_smem_bytes();
 cudaError_t step_tma_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
                      const CUtensorMap& tin, const CUtensorMap& tout, cudaStream_t s);
-void launch_step(int store, const Params& P, const int* tiles, int ntiles, bool pure, const Pop& fin,
+// tile lists of the fused step: pure tiles (no solid within 3 nodes, away from the domain
+// edge), wall tiles (solids near, halo inside the domain) and edge tiles (halo crossing the
+// domain edge: wrap, ghost columns, seam)
+constexpr int kTilesPure = 0, kTilesWall = 1, kTilesEdge = 2;
+void launch_step(int store, const Params& P, const int* tiles, int ntiles, int kind, const Pop& fin,
                  const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s);
 void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,
                  cudaStream_t s);

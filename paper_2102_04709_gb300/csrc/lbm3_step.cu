@@ -280,6 +280,19 @@ __device__ __forceinline__ void grad9_f(const float (*c)[W], int cx, int cy, flo
     gy = (1.0f / 3.0f) * (c2 - c4) + (1.0f / 12.0f) * ((c5 - c7) + (c6 - c8));
 }
 
+// Block-wide barrier that also reports how many of the three fluids occur in the block's
+// phase-field region (present: bit k set where a node holds rho_k != 0).  Where only one fluid
+// occurs, the two absent fluids have C_l = 0 exactly at every node, so every pair
+// G_kl = C_l grad C_k - C_k grad C_l of Eq.(10) and (13) vanishes: no stress, no force and no
+// recolouring term, and skipping the stress phase leaves every bit of the result unchanged.
+__device__ __forceinline__ int single_fluid_or(int present)
+{
+    const int f0 = __syncthreads_or(present & 1);
+    const int f1 = __syncthreads_or(present & 2);
+    const int f2 = __syncthreads_or(present & 4);
+    return (f0 != 0) + (f1 != 0) + (f2 != 0);
+}
+
 // F_s = div T at (rx, ry) of the stress region: Eq.(10) with the Eq.(12) derivative
 template <int RX>
 __device__ __forceinline__ void div_stress(const float (*txx)[RX], const float (*txy)[RX],
@@ -353,7 +366,7 @@ __device__ __forceinline__ Recolour collide_node(const Params& P, float f[kQ], f
 // bounce-back tests at C_FI nodes; only tiles whose halo-2 region holds a C_SB node with mixed
 // wall values (a contact line at or near it) carry the float-float phase fields, decided anew
 // every step from the wall values of this step's wetting pass.
-template <int TX, int TY, bool PURE, int STORE>
+template <int TX, int TY, bool PURE, bool INNER, int STORE>
 __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __restrict__ tiles,
                                                   const Pop fin, const Pop fout,
                                                   const uint8_t* __restrict__ type,
@@ -378,9 +391,9 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
     const int nx = P.nx;
     const int N = (int)P.N;
-    // halo-3 region inside the domain: no wrap, no ghost, no seam.  A PURE tile is also free
-    // of solid nodes in that region (every node it touches is in C_FI).
-    const bool inner = PURE || (x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= P.nx && y0 + TY + 3 <= P.ny);
+    // halo-3 region inside the domain: no wrap, no ghost, no seam (INNER: every listed tile).
+    // A PURE tile is also free of solid nodes in that region (every node it touches is in C_FI).
+    const bool inner = PURE || INNER || (x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= P.nx && y0 + TY + 3 <= P.ny);
 
     // ---- phase 0: geometry of the halo-3 region ----
     int wall = 0;
@@ -499,7 +512,9 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
         if (inl) zou_he(P, q, true);
         if (outl) zou_he(P, q, false);
     };
-    // densities / phase fields of the position (cx, cy) of the phase-field region from q
+    // densities / phase fields of the position (cx, cy) of the phase-field region from q; in
+    // pure tiles also which fluids occur in the region (bit k: some rho_k != 0)
+    int present = 0;
     auto store_phase = [&](int cx, int cy, const float q[27]) {
         if (df) {
             float rh[kNF], rl[kNF];
@@ -521,6 +536,8 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
                 const float* qk = q + 9 * k;
                 r[k] = ((qk[0] + (qk[1] + qk[3])) + (qk[2] + qk[4])) + ((qk[5] + qk[7]) + (qk[6] + qk[8]));
             }
+            if constexpr (PURE)
+                present |= (r[0] != 0.0f ? 1 : 0) | (r[1] != 0.0f ? 2 : 0) | (r[2] != 0.0f ? 4 : 0);
             const float rho = (r[0] + r[1]) + r[2];
             const float ir = __fdividef(1.0f, rho);
 #pragma unroll
@@ -591,10 +608,14 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
         r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
         r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
     }
-    __syncthreads();
+    bool mixed = true;
+    if constexpr (PURE)
+        mixed = single_fluid_or(present) != 1;
+    else
+        __syncthreads();
 
     // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
-    for (int j = tid; j < RX * RY; j += NT) {
+    for (int j = mixed ? tid : RX * RY; j < RX * RY; j += NT) {
         const int rx = j % RX, ry = j / RX;
         const int cx = rx + 1, cy = ry + 1, hx = rx + 2, hy = ry + 2;
         float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
@@ -650,11 +671,14 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
     if (!own_fluid || gx >= P.nx || gy >= P.ny) return;
 
     // ---- interfacial force F_s = div T (Eq.10 with Eq.12) ----
-    float Fx, Fy;
-    div_stress<RX>(s_txx, s_txy, s_tyy, lx + 1, ly + 1, Fx, Fy);
+    float Fx = 0.0f, Fy = 0.0f, g[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    if (mixed) {
+        div_stress<RX>(s_txx, s_txy, s_tyy, lx + 1, ly + 1, Fx, Fy);
+        // own colour gradients from phase 2
+#pragma unroll
+        for (int k = 0; k < 6; k++) g[k] = s_g[k][ly][lx];
+    }
     // ---- velocity, MRT collision with forcing, recolouring coefficients ----
-    const float g[6] = {s_g[0][ly][lx], s_g[1][ly][lx], s_g[2][ly][lx],
-                        s_g[3][ly][lx], s_g[4][ly][lx], s_g[5][ly][lx]};
     float ux, uy;
     const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, g, ux, uy);
     const int i = gy * nx + gx;
@@ -694,11 +718,12 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
 // tensor copy completing on an mbarrier, and the pulls read them at compile-time offsets.  The
 // box is needed only for the pulls: as soon as they are done the copy of the next tile's box is
 // issued, so it lands while this tile computes its stress, force, collision and recolouring.
-// The 27 output planes are staged in shared memory and leave by one bulk tensor store.
-// Two blocks per SM (103 KB of shared memory each).  Same arithmetic as k_step<PURE>, so the
-// two give identical results.
+// The 27 output planes are written directly (STAGE = false: 72 KB of shared memory per block)
+// or staged in shared memory and written by one bulk tensor store per tile (STAGE = true,
+// 100 KB).  kTmaBlocksPerSm = 2 blocks per SM: three (the most that fit) measured slower.
+// Same arithmetic as k_step<PURE>, so the two give identical results.
 template <int TX, int TY, bool STAGE>
-__global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const int* __restrict__ tiles,
+__global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Params P, const int* __restrict__ tiles,
                                                         const int ntiles, float* __restrict__ fout,
                                                         float* __restrict__ uout,
                                                         const __grid_constant__ CUtensorMap tm_in,
@@ -713,7 +738,6 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
     __shared__ float s_ch[kNF][CY][CX];
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
-    __shared__ float s_g[2 * kNF][TY][TX];
     __shared__ __align__(8) uint64_t s_bar;
     extern __shared__ unsigned char dsm[];
     float* box = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [27][BY][BX]
@@ -724,16 +748,16 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
     const int ntx = (P.nx + TX - 1) / TX;
     const uint32_t bar = smem_u32(&s_bar);
     if ((int)blockIdx.x >= ntiles) return;
-    auto issue = [&](int t) {
-        const int tile = tiles[t];
+    auto issue = [&](int tile) {
         const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
         mbar_arrive_expect_tx(bar, (uint32_t)NBOX * 4u);
         tma_load_3d(smem_u32(box), &tm_in, x0 - 4, y0 - 3, 0, bar);
     };
+    int tile = tiles[blockIdx.x];
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
-        issue(blockIdx.x);
+        issue(tile);
     }
     __syncthreads();
 
@@ -745,6 +769,7 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
             for (int k = 0; k < kNF; k++)
                 q[9 * k + a] = box[((k * kQ + a) * BY + cy + 1 - ey(a)) * BX + cx + 2 - ex(a)];
     };
+    // densities and phase fields of one node; returns which fluids it holds (bit k: rho_k != 0)
     auto store_phase = [&](int cx, int cy, const float q[27]) {
         float r[kNF];
 #pragma unroll
@@ -757,11 +782,14 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
 #pragma unroll
         for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = r[k] * ir;
         s_rho[cy][cx] = rho;
+        return (r[0] != 0.0f ? 1 : 0) | (r[1] != 0.0f ? 2 : 0) | (r[2] != 0.0f ? 4 : 0);
     };
 
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, j++) {
-        const int tile = tiles[t];
+        // the next tile's index is read now and used after the pulls
+        const bool more = t + (int)gridDim.x < ntiles;
+        const int next = more ? tiles[t + gridDim.x] : 0;
         const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
         bool ok = false;
         for (int it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(bar, j & 1);
@@ -778,6 +806,7 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
         }
 
         // ---- phase 1: pulls, densities and phase fields of the halo-2 region ----
+        int present = 0;
         {
             constexpr int NRING = CX * CY - TX * TY;
             for (int r = tid; r < NRING; r += NT) {
@@ -796,26 +825,26 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
                 }
                 float q[27];
                 pull(cx, cy, q);
-                store_phase(cx, cy, q);
+                present |= store_phase(cx, cy, q);
             }
         }
         float f[kQ], r0, r1, r2;
         {
             float q[27];
             pull(lx + 2, ly + 2, q);
-            store_phase(lx + 2, ly + 2, q);
+            present |= store_phase(lx + 2, ly + 2, q);
 #pragma unroll
             for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
             r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
             r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
             r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
         }
-        __syncthreads();
+        const bool mixed = single_fluid_or(present) != 1;
         // the box is free: fetch the next tile's while this one computes
-        if (tid == 0 && t + (int)gridDim.x < ntiles) issue(t + gridDim.x);
+        if (tid == 0 && more) issue(next);
 
         // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
-        for (int r = tid; r < RX * RY; r += NT) {
+        for (int r = mixed ? tid : RX * RY; r < RX * RY; r += NT) {
             const int rx = r % RX, ry = r / RX;
             const int cx = rx + 1, cy = ry + 1;
             const float rho = s_rho[cy][cx];
@@ -824,13 +853,6 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
             for (int k = 0; k < kNF; k++) {
                 c[k] = s_ch[k][cy][cx];
                 grad9_f<CX>(s_ch[k], cx, cy, gxk[k], gyk[k]);
-            }
-            if (rx >= 1 && rx <= TX && ry >= 1 && ry <= TY) {
-#pragma unroll
-                for (int k = 0; k < kNF; k++) {
-                    s_g[2 * k][ry - 1][rx - 1] = gxk[k];
-                    s_g[2 * k + 1][ry - 1][rx - 1] = gyk[k];
-                }
             }
             float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
             const float rho2 = rho * rho;
@@ -846,10 +868,14 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
         __syncthreads();
 
         // ---- phase 3: force, collision, recolouring into the staging buffer ----
-        float Fx, Fy;
-        div_stress<RX>(s_txx, s_txy, s_tyy, lx + 1, ly + 1, Fx, Fy);
-        const float g[6] = {s_g[0][ly][lx], s_g[1][ly][lx], s_g[2][ly][lx],
-                            s_g[3][ly][lx], s_g[4][ly][lx], s_g[5][ly][lx]};
+        float Fx = 0.0f, Fy = 0.0f, g[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (mixed) {
+            div_stress<RX>(s_txx, s_txy, s_tyy, lx + 1, ly + 1, Fx, Fy);
+            // own colour gradients, the same stencil as phase 2 on the same phase fields (the
+            // next tile overwrites them only after the barrier at the top of the loop)
+#pragma unroll
+            for (int k = 0; k < kNF; k++) grad9_f<CX>(s_ch[k], lx + 2, ly + 2, g[2 * k], g[2 * k + 1]);
+        }
         float ux, uy;
         const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, g, ux, uy);
         if (uout) {
@@ -857,6 +883,7 @@ __global__ void __launch_bounds__(TX* TY, 2) k_step_tma(const Params P, const in
             uout[i] = ux;
             uout[P.N + i] = uy;
         }
+        tile = next;
         if constexpr (STAGE) {
             float* o = outb + ly * TX + lx;
 #pragma unroll
@@ -1083,25 +1110,27 @@ void launch_wet_init(int store, const Params& P, int nw, const int* widx, const 
 }
 
 template <int STORE>
-static void launch_step_t(const Params& P, const int* tiles, int ntiles, bool pure, const Pop& fin,
+static void launch_step_t(const Params& P, const int* tiles, int ntiles, int kind, const Pop& fin,
                           const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
 {
-    if (pure)
-        k_step<kTX, kTY, true, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+    if (kind == kTilesPure)
+        k_step<kTX, kTY, true, true, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+    else if (kind == kTilesWall)
+        k_step<kTX, kTY, false, true, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
     else
-        k_step<kTX, kTY, false, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+        k_step<kTX, kTY, false, false, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
 }
 
-void launch_step(int store, const Params& P, const int* tiles, int ntiles, bool pure, const Pop& fin,
+void launch_step(int store, const Params& P, const int* tiles, int ntiles, int kind, const Pop& fin,
                  const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     if (store == kStoreF32)
-        launch_step_t<kStoreF32>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
+        launch_step_t<kStoreF32>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, s);
     else if (store == kStoreF16)
-        launch_step_t<kStoreF16>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
+        launch_step_t<kStoreF16>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, s);
     else
-        launch_step_t<kStoreBF16>(P, tiles, ntiles, pure, fin, fout, type, Cw, u, s);
+        launch_step_t<kStoreBF16>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, s);
 }
 
 // output path of the TMA kernel: staged in shared memory and written by one bulk tensor store per
