@@ -137,10 +137,21 @@ def measured_peak():
     return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
-def profiled_traffic(n_fluid):
-    """DRAM bytes per step-kernel launch from the committed ncu summary, if it was taken on the
-    current kernel source (hash match), scaled to this workload's fluid nodes."""
-    src = os.path.join(ROOT, "paper_2102_04709_gb300", "csrc", "lbm3_step.cu")
+KERNEL_SOURCES = ("lbm3_step.cu", "lbm3_common.cuh", "lbm3_device.cuh")
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the step kernels' sources."""
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2102_04709_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(pure_nodes):
+    """DRAM bytes of one pure-tile launch from the committed ncu summary, if it was taken on the
+    current kernel sources (hash match), scaled to this workload's pure-tile nodes."""
     path = os.path.join(ROOT, "profiles", "k_step_f32_traffic.txt")
     try:
         d = {}
@@ -149,11 +160,9 @@ def profiled_traffic(n_fluid):
                 if ":" in line and not line.startswith("#"):
                     k, v = line.split(":", 1)
                     d[k.strip()] = v.strip()
-        with open(src, "rb") as fh:
-            h = hashlib.sha256(fh.read()).hexdigest()[:16]
-        if d.get("source_sha256_16") != h:
+        if d.get("source_sha256_16") != kernel_source_hash():
             return None
-        return float(d["dram_bytes_per_fluid_node"]) * n_fluid
+        return float(d["dram_bytes_per_pure_node"]) * pure_nodes
     except (OSError, ValueError, KeyError):
         return None
 
@@ -337,7 +346,7 @@ def run_ours(args):
     bytes_launch = info["pure_bytes"]
     achieved = bytes_launch / (ms_pure / args.steps * 1e-3) / 1e9
     peak, peak_src = measured_peak()
-    traffic = profiled_traffic(info["n_fluid"])
+    traffic = profiled_traffic(info["pure_nodes"])
     clocks = sampler.summary(t0, t1)
     line = {
         "metric": "MLUPS", "value": value, "unit": "MLUPS", "n_gpus": ws, "steps": args.steps,
@@ -357,7 +366,8 @@ def run_ours(args):
                    "max_u": float(d[5])},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "k_step_f32<pure tiles>",
+                     "kernel": "k_step_tma (pure tiles, bulk tensor copies)" if info["tma"]
+                     else "k_step<pure tiles>",
                      "algorithmic_bytes_per_launch": bytes_launch},
         "gpu_launches": (info["step_kernels"] + info["wet_kernels"]) * args.steps,
         "clocks": clocks,
