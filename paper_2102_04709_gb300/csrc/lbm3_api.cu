@@ -33,7 +33,7 @@ struct lbm3 {
     // of each population buffer as the source box and as the destination tile
     bool tma = false;
     int tma_blocks = 0;  // persistent blocks of that kernel: kTmaBlocksPerSm per SM
-    CUtensorMap tm_in[2], tm_out[2];
+    CUtensorMap tm_in_a[2], tm_in_b[2], tm_out[2];
     int* widx = nullptr;
     double* wnrm = nullptr;
     float* wang = nullptr;
@@ -128,10 +128,11 @@ void release(lbm3* h)
     if (h->side) cudaStreamDestroy(h->side);
 }
 
-// Tensor maps of one [27][ny][nx] FP32 population buffer: as the pull-source box of a pure tile
-// (kTX + 8) x (kTY + 6) x 27 and as its destination tile kTX x kTY x 27.  false if the driver
-// has no encoder or refuses the layout (the plain kernel is used then).
-bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in, CUtensorMap* out)
+// Tensor maps of one [27][ny][nx] FP32 population buffer: as the two parts of the pull-source box
+// of a pure tile, (kTX + 8) x (kTY + 6) x kTmaPlanesA and x (27 - kTmaPlanesA) planes, and as its
+// destination tile kTX x kTY x 27.  false if the driver has no encoder or refuses the layout (the
+// plain kernel is used then).
+bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in_a, CUtensorMap* in_b, CUtensorMap* out)
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -147,14 +148,16 @@ bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in, CUtensorMap* o
     }
     const cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 27};
     const cuuint64_t strides[2] = {(cuuint64_t)P.nx * sizeof(float), (cuuint64_t)P.N * sizeof(float)};
-    const cuuint32_t box_in[3] = {kTX + 8, kTY + 6, 27}, box_out[3] = {kTX, kTY, 27};
+    const cuuint32_t box_a[3] = {kTX + 8, kTY + 6, kTmaPlanesA};
+    const cuuint32_t box_b[3] = {kTX + 8, kTY + 6, 27 - kTmaPlanesA};
+    const cuuint32_t box_out[3] = {kTX, kTY, 27};
     const cuuint32_t unit[3] = {1, 1, 1};
-    return encode(in, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box_in, unit,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
-           encode(out, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box_out, unit,
-                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    auto enc = [&](CUtensorMap* m, const cuuint32_t* box) {
+        return encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, box, unit,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    return enc(in_a, box_a) && enc(in_b, box_b) && enc(out, box_out);
 }
 
 // One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
@@ -170,8 +173,8 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->tma)
-        launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in[h->cur],
-                        h->tm_out[1 - h->cur], h->stream);
+        launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
+                        h->tm_in_b[h->cur], h->tm_out[1 - h->cur], h->stream);
     else
         launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, kTilesPure, fin, fo, h->type, h->Cw, u,
                     h->stream);
@@ -419,8 +422,9 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     // multiple of 16 bytes); LBM3_DISABLE_TMA=1 in the environment keeps the plain kernel
     if (e == cudaSuccess && g->precision == LBM3_FP32 && nx % 4 == 0 && h->n_pure > 0) {
         const char* off = std::getenv("LBM3_DISABLE_TMA");
-        if (!(off && off[0] == '1') && make_tensor_maps(P, h->pop[0].f, &h->tm_in[0], &h->tm_out[0]) &&
-            make_tensor_maps(P, h->pop[1].f, &h->tm_in[1], &h->tm_out[1])) {
+        if (!(off && off[0] == '1') &&
+            make_tensor_maps(P, h->pop[0].f, &h->tm_in_a[0], &h->tm_in_b[0], &h->tm_out[0]) &&
+            make_tensor_maps(P, h->pop[1].f, &h->tm_in_a[1], &h->tm_in_b[1], &h->tm_out[1])) {
             int dev = 0, sms = 0;
             e = cudaGetDevice(&dev);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -296,12 +296,14 @@ constexpr int kTX = 32, kTY = 8;
 // nodes within 3 nodes of it and away from the domain edges
 // pure FP32 tiles through bulk tensor copies (persistent, nblocks blocks): the dynamic shared
 // memory they need, the one-time attribute set-up, and the launch with tensor maps of fin
-// (box (kTX + 8, kTY + 6, 27)) and fout (box (kTX, kTY, 27)) over the [27][ny][nx] buffers
+// (boxes (kTX + 8, kTY + 6, kTmaPlanesA) and (kTX + 8, kTY + 6, 27 - kTmaPlanesA)) and fout
+// (box (kTX, kTY, 27)) over the [27][ny][nx] buffers
 constexpr int kTmaBlocksPerSm = 2;  // resident blocks of the persistent pure-tile kernel per SM
+constexpr int kTmaPlanesA = 14;     // planes of a pull box in its first copy (the rest in the second)
 size_t step_tma_smem_bytes();
 cudaError_t step_tma_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
-                     const CUtensorMap& tin, const CUtensorMap& tout, cudaStream_t s);
+                     const CUtensorMap& tin_a, const CUtensorMap& tin_b, const CUtensorMap& tout, cudaStream_t s);
 // tile lists of the fused step: pure tiles (no solid within 3 nodes, away from the domain
 // edge), wall tiles (solids near, halo inside the domain) and edge tiles (halo crossing the
 // domain edge: wrap, ghost columns, seam)

@@ -726,7 +726,8 @@ template <int TX, int TY, bool STAGE>
 __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Params P, const int* __restrict__ tiles,
                                                         const int ntiles, float* __restrict__ fout,
                                                         float* __restrict__ uout,
-                                                        const __grid_constant__ CUtensorMap tm_in,
+                                                        const __grid_constant__ CUtensorMap tm_in_a,
+                                                        const __grid_constant__ CUtensorMap tm_in_b,
                                                         const __grid_constant__ CUtensorMap tm_out)
 {
     constexpr int NT = TX * TY;
@@ -735,10 +736,13 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
     constexpr int BX = TX + 8, BY = TY + 6;  // pull-source box
     constexpr int NBOX = kQ * kNF * BY * BX;
     constexpr int NBOXP = (NBOX + 31) / 32 * 32;  // keeps the staging buffer 128-byte aligned
+    constexpr int NRING = CX * CY - TX * TY;      // halo-2 ring: one node per thread at most
+    static_assert(NRING <= NT, "the ring of the halo-2 region must not exceed one node per thread");
+    static_assert((kTmaPlanesA * BY * BX * 4) % 128 == 0, "second copy must start 128-byte aligned");
     __shared__ float s_ch[kNF][CY][CX];
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
-    __shared__ __align__(8) uint64_t s_bar;
+    __shared__ __align__(8) uint64_t s_bar[2];  // completion of copy A (planes 0..13) and B (14..26)
     extern __shared__ unsigned char dsm[];
     float* box = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [27][BY][BX]
     float* outb = box + NBOXP;                                                              // [27][TY][TX]
@@ -746,44 +750,83 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
     const int tid = threadIdx.x + TX * threadIdx.y;
     const int lx = threadIdx.x, ly = threadIdx.y;
     const int ntx = (P.nx + TX - 1) / TX;
-    const uint32_t bar = smem_u32(&s_bar);
+    const uint32_t bar_a = smem_u32(&s_bar[0]), bar_b = smem_u32(&s_bar[1]);
     if ((int)blockIdx.x >= ntiles) return;
-    auto issue = [&](int tile) {
+    auto issue_a = [&](int tile) {
         const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-        mbar_arrive_expect_tx(bar, (uint32_t)NBOX * 4u);
-        tma_load_3d(smem_u32(box), &tm_in, x0 - 4, y0 - 3, 0, bar);
+        mbar_arrive_expect_tx(bar_a, (uint32_t)(kTmaPlanesA * BY * BX) * 4u);
+        tma_load_3d(smem_u32(box), &tm_in_a, x0 - 4, y0 - 3, 0, bar_a);
+    };
+    auto issue_b = [&](int tile) {
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        mbar_arrive_expect_tx(bar_b, (uint32_t)((kQ * kNF - kTmaPlanesA) * BY * BX) * 4u);
+        tma_load_3d(smem_u32(box + kTmaPlanesA * BY * BX), &tm_in_b, x0 - 4, y0 - 3, kTmaPlanesA, bar_b);
     };
     int tile = tiles[blockIdx.x];
+    int last_a = 0, last_b = 0;  // tile iteration of the latest copy into each part (thread 0)
     if (tid == 0) {
-        mbar_init(bar, 1);
+        mbar_init(bar_a, 1);
+        mbar_init(bar_b, 1);
         fence_mbar_init();
-        issue(tile);
+        issue_a(tile);
+        issue_b(tile);
     }
     __syncthreads();
 
-    // pull of the node at (cx, cy) of the phase-field region from the box
-    auto pull = [&](int cx, int cy, float q[27]) {
+    // bounded wait for one part of iteration j's box, with the same outcome in every thread; on
+    // a timeout the error bit is set and thread 0 gives the copies it issued a second bounded
+    // wait, so that none lands in a later block's shared memory
+    auto wait_part = [&](uint32_t bar, int j) -> bool {
+        bool ok = false;
+        for (int it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(bar, j & 1);
+        if (!__syncthreads_or(!ok)) return true;
+        if (tid == 0) {
+            atomicOr(P.err, 1);
+            for (int it = 0; it < kWaitLimit && !mbar_try_wait(bar_a, last_a & 1); it++) {
+            }
+            for (int it = 0; it < kWaitLimit && !mbar_try_wait(bar_b, last_b & 1); it++) {
+            }
+            bulk_wait_read0();
+        }
+        return false;
+    };
+    // pulls of the node at (cx, cy) of the phase-field region from the planes p of the box with
+    // P0 <= p < P1 (q[p], p = 9 k + a)
+    auto pull = [&](int cx, int cy, float q[27], int p0, int p1) {
 #pragma unroll
-        for (int a = 0; a < kQ; a++)
-#pragma unroll
-            for (int k = 0; k < kNF; k++)
-                q[9 * k + a] = box[((k * kQ + a) * BY + cy + 1 - ey(a)) * BX + cx + 2 - ex(a)];
+        for (int p = 0; p < kQ * kNF; p++) {
+            const int a = p % kQ;
+            if (p >= p0 && p < p1) q[p] = box[(p * BY + cy + 1 - ey(a)) * BX + cx + 2 - ex(a)];
+        }
     };
     // densities and phase fields of one node; returns which fluids it holds (bit k: rho_k != 0)
-    auto store_phase = [&](int cx, int cy, const float q[27]) {
-        float r[kNF];
-#pragma unroll
-        for (int k = 0; k < kNF; k++) {
-            const float* qk = q + 9 * k;
-            r[k] = ((qk[0] + (qk[1] + qk[3])) + (qk[2] + qk[4])) + ((qk[5] + qk[7]) + (qk[6] + qk[8]));
-        }
-        const float rho = (r[0] + r[1]) + r[2];
+    auto store_phase = [&](int cx, int cy, float r0, float r1, float r2) {
+        const float rho = (r0 + r1) + r2;
         const float ir = __fdividef(1.0f, rho);
-#pragma unroll
-        for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = r[k] * ir;
+        s_ch[0][cy][cx] = r0 * ir;
+        s_ch[1][cy][cx] = r1 * ir;
+        s_ch[2][cy][cx] = r2 * ir;
         s_rho[cy][cx] = rho;
-        return (r[0] != 0.0f ? 1 : 0) | (r[1] != 0.0f ? 2 : 0) | (r[2] != 0.0f ? 4 : 0);
+        return (r0 != 0.0f ? 1 : 0) | (r1 != 0.0f ? 2 : 0) | (r2 != 0.0f ? 4 : 0);
     };
+
+    // the ring node of this thread (a fixed position in every tile)
+    const bool ring = tid < NRING;
+    int rcx = 0, rcy = 0;
+    if (ring) {
+        if (tid < 2 * CX) {
+            rcx = tid % CX;
+            rcy = tid / CX;
+        } else if (tid < 4 * CX) {
+            rcx = (tid - 2 * CX) % CX;
+            rcy = CY - 2 + (tid - 2 * CX) / CX;
+        } else {
+            const int rr0 = tid - 4 * CX;  // 4 * TY side nodes
+            const int side = rr0 / (2 * TY), rr = rr0 % (2 * TY);
+            rcy = 2 + rr / 2;
+            rcx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
+        }
+    }
 
     int j = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, j++) {
@@ -791,57 +834,48 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
         const bool more = t + (int)gridDim.x < ntiles;
         const int next = more ? tiles[t + gridDim.x] : 0;
         const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-        bool ok = false;
-        for (int it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(bar, j & 1);
-        if (__syncthreads_or(!ok)) {
-            // the copy did not complete in time: record it, give it a second bounded wait so
-            // that it does not land in a later block's shared memory, and stop
-            if (tid == 0) {
-                atomicOr(P.err, 1);
-                for (int it = 0; it < kWaitLimit && !mbar_try_wait(bar, j & 1); it++) {
-                }
-                bulk_wait_read0();
-            }
-            return;
-        }
 
-        // ---- phase 1: pulls, densities and phase fields of the halo-2 region ----
-        int present = 0;
-        {
-            constexpr int NRING = CX * CY - TX * TY;
-            for (int r = tid; r < NRING; r += NT) {
-                int cx, cy;
-                if (r < 2 * CX) {
-                    cx = r % CX;
-                    cy = r / CX;
-                } else if (r < 4 * CX) {
-                    cx = (r - 2 * CX) % CX;
-                    cy = CY - 2 + (r - 2 * CX) / CX;
-                } else {
-                    const int rr0 = r - 4 * CX;  // 4 * TY side nodes
-                    const int side = rr0 / (2 * TY), rr = rr0 % (2 * TY);
-                    cy = 2 + rr / 2;
-                    cx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
-                }
-                float q[27];
-                pull(cx, cy, q);
-                present |= store_phase(cx, cy, q);
-            }
+        // ---- phase 1: pulls, densities and phase fields of the halo-2 region, in two passes
+        // over the two parts of the box (the sums keep the order of the one-pass kernel) ----
+        if (!wait_part(bar_a, j)) return;
+        float q[27];
+        float ra0 = 0.0f, ra1 = 0.0f;  // ring node: rho_0 and the planes 9..13 part of rho_1
+        if (ring) {
+            pull(rcx, rcy, q, 0, kTmaPlanesA);
+            ra0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+            ra1 = (q[9] + (q[10] + q[12])) + (q[11] + q[13]);
         }
         float f[kQ], r0, r1, r2;
-        {
-            float q[27];
-            pull(lx + 2, ly + 2, q);
-            present |= store_phase(lx + 2, ly + 2, q);
+        pull(lx + 2, ly + 2, q, 0, kTmaPlanesA);
 #pragma unroll
-            for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
-            r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
-            r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
-            r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+        for (int a = 0; a < kQ; a++) f[a] = a < 5 ? q[a] + q[9 + a] : q[a];
+        r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+        r1 = (q[9] + (q[10] + q[12])) + (q[11] + q[13]);
+        __syncthreads();
+        // part A is free: fetch the next tile's while part B is pulled and this tile computes
+        if (tid == 0 && more) {
+            issue_a(next);
+            last_a = j + 1;
         }
+        if (!wait_part(bar_b, j)) return;
+        int present = 0;
+        if (ring) {
+            pull(rcx, rcy, q, kTmaPlanesA, kQ * kNF);
+            const float rb1 = ra1 + ((q[14] + q[16]) + (q[15] + q[17]));
+            const float rb2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+            present |= store_phase(rcx, rcy, ra0, rb1, rb2);
+        }
+        pull(lx + 2, ly + 2, q, kTmaPlanesA, kQ * kNF);
+#pragma unroll
+        for (int a = 0; a < kQ; a++) f[a] = (a < 5 ? f[a] : f[a] + q[9 + a]) + q[18 + a];
+        r1 = r1 + ((q[14] + q[16]) + (q[15] + q[17]));
+        r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+        present |= store_phase(lx + 2, ly + 2, r0, r1, r2);
         const bool mixed = single_fluid_or(present) != 1;
-        // the box is free: fetch the next tile's while this one computes
-        if (tid == 0 && more) issue(next);
+        if (tid == 0 && more) {
+            issue_b(next);
+            last_b = j + 1;
+        }
 
         // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
         for (int r = mixed ? tid : RX * RY; r < RX * RY; r += NT) {
@@ -1151,12 +1185,12 @@ cudaError_t step_tma_prepare()
 }
 
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
-                     const CUtensorMap& tin, const CUtensorMap& tout, cudaStream_t s)
+                     const CUtensorMap& tin_a, const CUtensorMap& tin_b, const CUtensorMap& tout, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     const int nb = nblocks < ntiles ? nblocks : ntiles;
     k_step_tma<kTX, kTY, kTmaStage>
-        <<<nb, dim3(kTX, kTY), step_tma_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin, tout);
+        <<<nb, dim3(kTX, kTY), step_tma_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin_a, tin_b, tout);
 }
 
 void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,
