@@ -152,7 +152,7 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, dou
  * + 1 class byte per node), out[3] = fused-step launches per timestep, out[4] = wetting launches
  * per timestep, out[5] = device bytes held by the handle, out[6] = algorithmic bytes of the
  * pure-tile launch, out[7] = nodes in pure tiles, out[8] = 1 if the pure tiles move their
- * populations with bulk tensor copies (FP32 storage, nx a multiple of 4, not disabled by
+ * populations with bulk tensor copies (nx a multiple of 4 and not disabled by
  * LBM3_DISABLE_TMA=1 in the environment at lbm3_create), else 0. */
 int lbm3_info(const lbm3* h, int64_t out[9]);
 

@@ -29,8 +29,9 @@ struct lbm3 {
     double* partials = nullptr;    // diagnostics block partials
     double* dout = nullptr;        // 8 doubles
     int* err_flag = nullptr;       // error bits set by kernels (Params::err)
-    // bulk-tensor-copy path of the pure tiles (FP32 storage, nx a multiple of 4): tensor maps
-    // of each population buffer as the source box and as the destination tile
+    // bulk-tensor-copy path of the pure tiles (nx a multiple of 4): tensor maps of each
+    // population buffer, FP32 storage: the two parts of the source box and the destination tile;
+    // 16-bit storage: the density box (tm_in_a) and the offset-record box (tm_in_b)
     bool tma = false;
     int tma_blocks = 0;  // persistent blocks of that kernel: kTmaBlocksPerSm per SM
     CUtensorMap tm_in_a[2], tm_in_b[2], tm_out[2];
@@ -132,7 +133,7 @@ void release(lbm3* h)
 // of a pure tile, (kTX + 8) x (kTY + 6) x kTmaPlanesA and x (27 - kTmaPlanesA) planes, and as its
 // destination tile kTX x kTY x 27.  false if the driver has no encoder or refuses the layout (the
 // plain kernel is used then).
-bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in_a, CUtensorMap* in_b, CUtensorMap* out)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
@@ -142,10 +143,17 @@ bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in_a, CUtensorMap*
                 cudaSuccess ||
             q != cudaDriverEntryPointSuccess || !fn) {
             cudaGetLastError();
-            return false;
+            return nullptr;
         }
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
+    return encode;
+}
+
+bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in_a, CUtensorMap* in_b, CUtensorMap* out)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 27};
     const cuuint64_t strides[2] = {(cuuint64_t)P.nx * sizeof(float), (cuuint64_t)P.N * sizeof(float)};
     const cuuint32_t box_a[3] = {kTX + 8, kTY + 6, kTmaPlanesA};
@@ -160,6 +168,27 @@ bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in_a, CUtensorMap*
     return enc(in_a, box_a) && enc(in_b, box_b) && enc(out, box_out);
 }
 
+// Tensor maps of one 16-bit-storage population buffer: the densities rho[3][ny][nx] (FP32, box
+// (kTX + 8) x (kTY + 6) x 3) and the offset records off[3][ny][nx] as 16-bit words
+// [3][ny][nx][8] (box 8 x (kTX + 8) x (kTY + 6) x 3).
+bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtensorMap* toff)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint64_t rdims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 3};
+    const cuuint64_t rstrides[2] = {(cuuint64_t)P.nx * sizeof(float), (cuuint64_t)P.N * sizeof(float)};
+    const cuuint32_t rbox[3] = {kTX + 8, kTY + 6, 3}, runit[3] = {1, 1, 1};
+    const cuuint64_t odims[4] = {8, (cuuint64_t)P.nx, (cuuint64_t)P.ny, 3};
+    const cuuint64_t ostrides[3] = {16, (cuuint64_t)P.nx * 16, (cuuint64_t)P.N * 16};
+    const cuuint32_t obox[4] = {8, kTX + 8, kTY + 6, 3}, ounit[4] = {1, 1, 1, 1};
+    return encode(trho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p.rho, rdims, rstrides, rbox, runit,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
+           encode(toff, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, p.off, odims, ostrides, obox, ounit,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
 // while the side stream runs the wetting pass and then the remaining tiles, join.  With ev != NULL
 // the launches are bracketed by the events ev[0..5] (main: 0-1 pure; side: 2-3 wet, 4-5 rest).
@@ -172,9 +201,12 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
-    if (h->tma)
+    if (h->tma && h->precision == LBM3_FP32)
         launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
                         h->tm_in_b[h->cur], h->tm_out[1 - h->cur], h->stream);
+    else if (h->tma)
+        launch_step_tma16(h->precision, h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
+                          h->tm_in_b[h->cur], h->stream);
     else
         launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, kTilesPure, fin, fo, h->type, h->Cw, u,
                     h->stream);
@@ -418,24 +450,27 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (e == cudaSuccess && !wang.empty()) e = cudaMemcpy(h->wang, wang.data(), wang.size() * sizeof(float), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->Cw, 0, 3 * N * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(h->u, 0, 2 * N * sizeof(float));
-    // pure FP32 tiles through bulk tensor copies where the layout allows them (row pitch a
-    // multiple of 16 bytes); LBM3_DISABLE_TMA=1 in the environment keeps the plain kernel
-    if (e == cudaSuccess && g->precision == LBM3_FP32 && nx % 4 == 0 && h->n_pure > 0) {
+    // pure tiles through bulk tensor copies where the layout allows them (row pitch a multiple of
+    // 16 bytes); LBM3_DISABLE_TMA=1 in the environment keeps the plain kernel
+    if (e == cudaSuccess && nx % 4 == 0 && h->n_pure > 0) {
         const char* off = std::getenv("LBM3_DISABLE_TMA");
-        if (!(off && off[0] == '1') &&
-            make_tensor_maps(P, h->pop[0].f, &h->tm_in_a[0], &h->tm_in_b[0], &h->tm_out[0]) &&
-            make_tensor_maps(P, h->pop[1].f, &h->tm_in_a[1], &h->tm_in_b[1], &h->tm_out[1])) {
+        const bool f32 = g->precision == LBM3_FP32;
+        bool maps = !(off && off[0] == '1');
+        for (int b = 0; b < 2 && maps; b++)
+            maps = f32 ? make_tensor_maps(P, h->pop[b].f, &h->tm_in_a[b], &h->tm_in_b[b], &h->tm_out[b])
+                       : make_tensor_maps16(P, h->pop[b], &h->tm_in_a[b], &h->tm_in_b[b]);
+        if (maps) {
             int dev = 0, sms = 0;
             e = cudaGetDevice(&dev);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = step_tma_prepare();
+            if (e == cudaSuccess && f32) e = step_tma_prepare();
             // SMs left free for the wetting pass and the wall / edge tiles, which run on the side
             // stream while the persistent pure-tile kernel holds its SMs: their share of the step's
             // work, a wall or edge tile counted as two pure tiles (measured on 4096 x 2048 pillars:
             // 39 of 152 SMs, 20.3k instead of 18.6k MLUPS with every SM given to pure tiles)
             const double wg = 2.0 * h->n_gen;
             const int spare = std::min(sms / 2, (int)std::lround(sms * wg / (wg + h->n_pure)));
-            h->tma_blocks = kTmaBlocksPerSm * (sms - spare);
+            h->tma_blocks = (f32 ? kTmaBlocksPerSm : kTma16BlocksPerSm) * (sms - spare);
             h->tma = e == cudaSuccess && sms > 0;
         }
     }

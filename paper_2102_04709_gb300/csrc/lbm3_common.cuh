@@ -300,10 +300,17 @@ constexpr int kTX = 32, kTY = 8;
 // (box (kTX, kTY, 27)) over the [27][ny][nx] buffers
 constexpr int kTmaBlocksPerSm = 2;  // resident blocks of the persistent pure-tile kernel per SM
 constexpr int kTmaPlanesA = 14;     // planes of a pull box in its first copy (the rest in the second)
+constexpr int kTma16BlocksPerSm = 3;  // the same for the pure tiles of the 16-bit storage
 size_t step_tma_smem_bytes();
 cudaError_t step_tma_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
                      const CUtensorMap& tin_a, const CUtensorMap& tin_b, const CUtensorMap& tout, cudaStream_t s);
+// pure tiles of the 16-bit storage through bulk tensor copies (persistent, nblocks blocks): tensor
+// maps of the densities (box (kTX + 8, kTY + 6, 3) of [3][ny][nx] FP32) and of the offset records
+// (box (8, kTX + 8, kTY + 6, 3) of [3][ny][nx][8] 16-bit words)
+size_t step_tma16_smem_bytes();
+void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
+                       float* u, const CUtensorMap& trho, const CUtensorMap& toff, cudaStream_t s);
 // tile lists of the fused step: pure tiles (no solid within 3 nodes, away from the domain
 // edge), wall tiles (solids near, halo inside the domain) and edge tiles (halo crossing the
 // domain edge: wrap, ghost columns, seam)

@@ -241,6 +241,15 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+        : "memory");
+}
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src)
 {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
@@ -712,6 +721,35 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
 
 
 
+// Eq.(10) stress on the halo-1 region of a pure tile from the phase fields of its halo-2 region
+// (float path: no solid, no float-float words)
+template <int TX, int TY>
+__device__ __forceinline__ void stress_halo1(const Params& P, const float (*s_ch)[TY + 4][TX + 4],
+                                             const float (*s_rho)[TX + 4], float (*s_txx)[TX + 2],
+                                             float (*s_txy)[TX + 2], float (*s_tyy)[TX + 2], int tid)
+{
+    constexpr int CX = TX + 4, RX = TX + 2, RY = TY + 2;
+    for (int r = tid; r < RX * RY; r += TX * TY) {
+        const int rx = r % RX, ry = r / RX;
+        const int cx = rx + 1, cy = ry + 1;
+        const float rho = s_rho[cy][cx];
+        float c[kNF], gxk[kNF], gyk[kNF];
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            c[k] = s_ch[k][cy][cx];
+            grad9_f<CX>(s_ch[k], cx, cy, gxk[k], gyk[k]);
+        }
+        float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
+        const float rho2 = rho * rho;
+        pair_stress(P.sig01, c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
+        pair_stress(P.sig02, c[0], c[2], gxk[0], gyk[0], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+        pair_stress(P.sig12, c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
+        s_txx[ry][rx] = Txx;
+        s_txy[ry][rx] = Txy;
+        s_tyy[ry][rx] = Tyy;
+    }
+}
+
 // Pure FP32 tiles through the tensor memory accelerator, persistent: block b handles tiles
 // b, b + gridDim.x, ...  For each tile the 27 pull-source planes over the (TX + 8) x (TY + 6)
 // box starting at (x0 - 4, y0 - 3) -- x rounded down to a 16-byte boundary -- arrive by one bulk
@@ -878,25 +916,7 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
         }
 
         // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
-        for (int r = mixed ? tid : RX * RY; r < RX * RY; r += NT) {
-            const int rx = r % RX, ry = r / RX;
-            const int cx = rx + 1, cy = ry + 1;
-            const float rho = s_rho[cy][cx];
-            float c[kNF], gxk[kNF], gyk[kNF];
-#pragma unroll
-            for (int k = 0; k < kNF; k++) {
-                c[k] = s_ch[k][cy][cx];
-                grad9_f<CX>(s_ch[k], cx, cy, gxk[k], gyk[k]);
-            }
-            float Txx = 0.f, Txy = 0.f, Tyy = 0.f;
-            const float rho2 = rho * rho;
-            pair_stress(P.sig01, c[0], c[1], gxk[0], gyk[0], gxk[1], gyk[1], rho2, Txx, Txy, Tyy);
-            pair_stress(P.sig02, c[0], c[2], gxk[0], gyk[0], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
-            pair_stress(P.sig12, c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
-            s_txx[ry][rx] = Txx;
-            s_txy[ry][rx] = Txy;
-            s_tyy[ry][rx] = Tyy;
-        }
+        if (mixed) stress_halo1<TX, TY>(P, s_ch, s_rho, s_txx, s_txy, s_tyy, tid);
         // the previous tile's bulk store must have read the staging buffer before it is refilled
         if (STAGE && tid == 0) bulk_wait_read0();
         __syncthreads();
@@ -1167,6 +1187,180 @@ void launch_step(int store, const Params& P, const int* tiles, int ntiles, int k
         launch_step_t<kStoreBF16>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, s);
 }
 
+// Pure tiles of the 16-bit storage through the tensor memory accelerator, persistent, with the
+// tile loop of k_step_tma: per tile one bulk copy of the FP32 densities (box (TX + 8) x (TY + 6)
+// x 3) and one of the 16-byte offset records (box 8 x (TX + 8) x (TY + 6) x 3 of 16-bit words)
+// complete on an mbarrier; a pull rebuilds w_a rho_k + offset at its source, the rest population
+// from the node's own record, exactly as the plain kernel does from global memory.  The next
+// tile's boxes are fetched as soon as the pulls are done.
+template <int TX, int TY, int STORE>
+__global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const Params P, const int* __restrict__ tiles,
+                                                            const int ntiles, const Pop fout,
+                                                            float* __restrict__ uout,
+                                                            const __grid_constant__ CUtensorMap tm_rho,
+                                                            const __grid_constant__ CUtensorMap tm_off)
+{
+    constexpr int NT = TX * TY;
+    constexpr int CX = TX + 4, CY = TY + 4;
+    constexpr int RX = TX + 2, RY = TY + 2;
+    constexpr int BX = TX + 8, BY = TY + 6;
+    constexpr int NR = kNF * BY * BX;                 // floats of the density box
+    constexpr int NRP = (NR + 31) / 32 * 32;         // keeps the record box 128-byte aligned
+    constexpr uint32_t kBytes = NR * 4u + NR * 16u;  // both copies
+    __shared__ float s_ch[kNF][CY][CX];
+    __shared__ float s_rho[CY][CX];
+    __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
+    __shared__ __align__(8) uint64_t s_bar;
+    extern __shared__ unsigned char dsm[];
+    float* rbox = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [3][BY][BX]
+    const unsigned short* obox = reinterpret_cast<const unsigned short*>(rbox + NRP);          // [3][BY][BX][8]
+
+    const int tid = threadIdx.x + TX * threadIdx.y;
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const int ntx = (P.nx + TX - 1) / TX;
+    const uint32_t bar = smem_u32(&s_bar);
+    if ((int)blockIdx.x >= ntiles) return;
+    auto issue = [&](int tile) {
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        mbar_arrive_expect_tx(bar, kBytes);
+        tma_load_3d(smem_u32(rbox), &tm_rho, x0 - 4, y0 - 3, 0, bar);
+        tma_load_4d(smem_u32(obox), &tm_off, 0, x0 - 4, y0 - 3, 0, bar);
+    };
+    int tile = tiles[blockIdx.x];
+    int last = 0;
+    if (tid == 0) {
+        mbar_init(bar, 1);
+        fence_mbar_init();
+        issue(tile);
+    }
+    __syncthreads();
+
+    // pull of the node at (cx, cy) of the phase-field region from the boxes
+    auto pull = [&](int cx, int cy, float q[27]) {
+        const int own = (cy + 1) * BX + cx + 2;
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            const float rk = rbox[k * BY * BX + own];
+            const uint4 w = *reinterpret_cast<const uint4*>(obox + 8 * (k * BY * BX + own));
+            const unsigned u[4] = {w.x, w.y, w.z, w.w};
+            float d[kQ];
+#pragma unroll
+            for (int jj = 0; jj < 4; jj++) {
+                d[2 * jj + 1] = dec16<STORE>((unsigned short)(u[jj] & 0xffffu));
+                d[2 * jj + 2] = dec16<STORE>((unsigned short)(u[jj] >> 16));
+            }
+            const float ds = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
+            q[9 * k] = wq(0) * rk - ds;
+#pragma unroll
+            for (int a = 1; a < kQ; a++) {
+                const int src = k * BY * BX + (cy + 1 - ey(a)) * BX + cx + 2 - ex(a);
+                q[9 * k + a] = wq(a) * rbox[src] + dec16<STORE>(obox[8 * src + a - 1]);
+            }
+        }
+    };
+    auto store_phase = [&](int cx, int cy, const float q[27]) {
+        float r[kNF];
+#pragma unroll
+        for (int k = 0; k < kNF; k++) {
+            const float* qk = q + 9 * k;
+            r[k] = ((qk[0] + (qk[1] + qk[3])) + (qk[2] + qk[4])) + ((qk[5] + qk[7]) + (qk[6] + qk[8]));
+        }
+        const float rho = (r[0] + r[1]) + r[2];
+        const float ir = __fdividef(1.0f, rho);
+#pragma unroll
+        for (int k = 0; k < kNF; k++) s_ch[k][cy][cx] = r[k] * ir;
+        s_rho[cy][cx] = rho;
+        return (r[0] != 0.0f ? 1 : 0) | (r[1] != 0.0f ? 2 : 0) | (r[2] != 0.0f ? 4 : 0);
+    };
+
+    int j = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, j++) {
+        const bool more = t + (int)gridDim.x < ntiles;
+        const int next = more ? tiles[t + gridDim.x] : 0;
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        bool ok = false;
+        for (int it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(bar, j & 1);
+        if (__syncthreads_or(!ok)) {
+            // the copies did not complete in time: record it, give them a second bounded wait
+            // so that they do not land in a later block's shared memory, and stop
+            if (tid == 0) {
+                atomicOr(P.err, 1);
+                for (int it = 0; it < kWaitLimit && !mbar_try_wait(bar, last & 1); it++) {
+                }
+            }
+            return;
+        }
+
+        // ---- phase 1: pulls, densities and phase fields of the halo-2 region ----
+        int present = 0;
+        {
+            constexpr int NRING = CX * CY - TX * TY;
+            for (int r = tid; r < NRING; r += NT) {
+                int cx, cy;
+                if (r < 2 * CX) {
+                    cx = r % CX;
+                    cy = r / CX;
+                } else if (r < 4 * CX) {
+                    cx = (r - 2 * CX) % CX;
+                    cy = CY - 2 + (r - 2 * CX) / CX;
+                } else {
+                    const int rr0 = r - 4 * CX;  // 4 * TY side nodes
+                    const int side = rr0 / (2 * TY), rr = rr0 % (2 * TY);
+                    cy = 2 + rr / 2;
+                    cx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
+                }
+                float q[27];
+                pull(cx, cy, q);
+                present |= store_phase(cx, cy, q);
+            }
+        }
+        float f[kQ], r0, r1, r2;
+        {
+            float q[27];
+            pull(lx + 2, ly + 2, q);
+            present |= store_phase(lx + 2, ly + 2, q);
+#pragma unroll
+            for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
+            r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+            r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
+            r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+        }
+        const bool mixed = single_fluid_or(present) != 1;
+        // the boxes are free: fetch the next tile's while this one computes
+        if (tid == 0 && more) {
+            issue(next);
+            last = j + 1;
+        }
+
+        // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
+        if (mixed) stress_halo1<TX, TY>(P, s_ch, s_rho, s_txx, s_txy, s_tyy, tid);
+        __syncthreads();
+
+        // ---- phase 3: force, collision, recolouring, 16-bit stores ----
+        float Fx = 0.0f, Fy = 0.0f, g[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (mixed) {
+            div_stress<RX>(s_txx, s_txy, s_tyy, lx + 1, ly + 1, Fx, Fy);
+#pragma unroll
+            for (int k = 0; k < kNF; k++) grad9_f<CX>(s_ch[k], lx + 2, ly + 2, g[2 * k], g[2 * k + 1]);
+        }
+        float ux, uy;
+        const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, g, ux, uy);
+        const int i = (y0 + ly) * P.nx + x0 + lx;
+        if (uout) {
+            uout[i] = ux;
+            uout[P.N + i] = uy;
+        }
+        tile = next;
+        float v[27];
+#pragma unroll
+        for (int k = 0; k < kNF; k++)
+#pragma unroll
+            for (int a = 0; a < kQ; a++)
+                v[9 * k + a] = rc.C[k] * f[a] + wq(a) * (rc.Vx[k] * (float)ex(a) + rc.Vy[k] * (float)ey(a));
+        store_node<STORE>(fout, P.N, i, v);
+    }
+}
+
 // output path of the TMA kernel: staged in shared memory and written by one bulk tensor store per
 // tile, or written directly (a smaller shared-memory footprint leaves room on each SM for blocks
 // of the wall-tile kernel, which runs concurrently)
@@ -1191,6 +1385,25 @@ void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks,
     const int nb = nblocks < ntiles ? nblocks : ntiles;
     k_step_tma<kTX, kTY, kTmaStage>
         <<<nb, dim3(kTX, kTY), step_tma_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin_a, tin_b, tout);
+}
+
+size_t step_tma16_smem_bytes()
+{
+    const size_t nr = ((size_t)kNF * (kTY + 6) * (kTX + 8) + 31) / 32 * 32;
+    return nr * sizeof(float) + (size_t)kNF * (kTY + 6) * (kTX + 8) * 16u + 128u;
+}
+
+void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
+                       float* u, const CUtensorMap& trho, const CUtensorMap& toff, cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    const int nb = nblocks < ntiles ? nblocks : ntiles;
+    if (store == kStoreF16)
+        k_step_tma16<kTX, kTY, kStoreF16>
+            <<<nb, dim3(kTX, kTY), step_tma16_smem_bytes(), s>>>(P, tiles, ntiles, fout, u, trho, toff);
+    else
+        k_step_tma16<kTX, kTY, kStoreBF16>
+            <<<nb, dim3(kTX, kTY), step_tma16_smem_bytes(), s>>>(P, tiles, ntiles, fout, u, trho, toff);
 }
 
 void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,
