@@ -300,7 +300,7 @@ constexpr int kTX = 32, kTY = 8;
 // (box (kTX, kTY, 27)) over the [27][ny][nx] buffers
 constexpr int kTmaBlocksPerSm = 2;  // resident blocks of the persistent pure-tile kernel per SM
 constexpr int kTmaPlanesA = 14;     // planes of a pull box in its first copy (the rest in the second)
-constexpr int kTma16BlocksPerSm = 3;  // the same for the pure tiles of the 16-bit storage
+constexpr int kTma16BlocksPerSm = 4;  // the same for the pure tiles of the 16-bit storage (3: 16.2k, 2: 15.7k MLUPS)
 size_t step_tma_smem_bytes();
 cudaError_t step_tma_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
