@@ -56,6 +56,23 @@ def parse():
     return ap.parse_args()
 
 
+def max_over_ranks(x, ws, device):
+    """Largest x over the ranks of the default process group (x itself with one rank): the
+    whole job takes as long as its slowest replica."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mlups(nodes, steps, ws, ms):
+    """Whole-job throughput: the grid nodes that all ws replicas advanced, per second of the
+    slowest replica, in millions."""
+    return nodes * steps * ws / (ms * 1e-3) / 1e6
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -265,11 +282,7 @@ def run_ours(args):
     barrier()
     t1 = time.time()
     sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1), ws, "cuda")
     d = sim.diag(check=False)
 
     # end to end through the C ABI with host buffers: H2D of the initial densities, the steps,
@@ -284,7 +297,8 @@ def run_ours(args):
         rho_out, u_out = sim.fields()
         barrier()
         tb = time.perf_counter()
-        e2e = {"value": w.n * args.steps * ws / (tb - ta) / 1e6, "unit": "MLUPS",
+        e2e_ms = max_over_ranks((tb - ta) * 1e3, ws, "cuda")
+        e2e = {"value": job_mlups(w.n, args.steps, ws, e2e_ms), "unit": "MLUPS",
                "h2d_bytes_per_step": int(math.ceil(rho_host.nbytes / args.steps)),
                "d2h_bytes_per_step": int(math.ceil((rho_out.nbytes + u_out.nbytes) / args.steps))}
 
@@ -305,9 +319,9 @@ def run_ours(args):
             _, msp, _ = sim.step_timed(n_alt)
             a1.record(stream)
             barrier()
-            ams = a0.elapsed_time(a1)
+            ams = max_over_ranks(a0.elapsed_time(a1), ws, "cuda")
             ainfo = sim.info()
-            alt[name] = {"value": w.n * n_alt * ws / (ams * 1e-3) / 1e6, "unit": "MLUPS",
+            alt[name] = {"value": job_mlups(w.n, n_alt, ws, ams), "unit": "MLUPS",
                          "ms_per_step": ams / n_alt, "steps": n_alt,
                          "bytes_per_fluid_node": 216 if p == 0 else 120,
                          "pure_kernel_gbs": ainfo["pure_bytes"] / (msp / n_alt * 1e-3) / 1e9}
@@ -341,7 +355,7 @@ def run_ours(args):
 
     if rank != 0:
         return
-    value = w.n * args.steps * ws / (ms * 1e-3) / 1e6
+    value = job_mlups(w.n, args.steps, ws, ms)
     # dominant kernel: the fused step on the pure tiles (216 B per node, no class bytes)
     bytes_launch = info["pure_bytes"]
     achieved = bytes_launch / (ms_pure / args.steps * 1e-3) / 1e9
