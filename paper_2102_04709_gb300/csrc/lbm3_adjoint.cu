@@ -708,10 +708,12 @@ __global__ void b_frac(const Params P, const Adj A, const uint8_t* __restrict__ 
 __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__ type)
 {
     const int y = blockIdx.x * blockDim.x + threadIdx.x;
-    if (y >= P.ny || P.bc_x != kZouHe) return;
+    if (P.bc_x != kZouHe) return;
     auto L = [&](int k, int a, int i) -> float& { return A.l_fpost[(long long)(9 * k + a) * P.N + i]; };
     auto Fv = [&](int k, int a, int i) { return A.fpost[(long long)(9 * k + a) * P.N + i]; };
-    {
+    // dJ/dU of this row, summed over the warp before one atomic (rows beyond ny add 0)
+    double lU = 0.0;
+    if (y < P.ny) {
         // inlet x = 0: unknown a = 1, 5, 8 (fluid 2)
         const int i = y * P.nx;
         float f[kQ];
@@ -733,13 +735,16 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
         lf[3] += 2.f * lrho * ir;
         lf[6] += 2.f * lrho * ir;
         lf[7] += 2.f * lrho * ir;
-        const double lU = (double)L1 * (2.0 / 3.0) * rho + (double)(L5 + L8) * rho / 6.0 + (double)lrho * rho / (1.0 - U);
-        atomicAdd(A.d_u, lU);
+        lU = (double)L1 * (2.0 / 3.0) * rho + (double)(L5 + L8) * rho / 6.0 + (double)lrho * rho / (1.0 - U);
         for (int k = 0; k < kNF; k++)
             for (int a : {0, 2, 3, 4, 6, 7}) L(k, a, i) += lf[a];
         for (int k = 0; k < kNF; k++)
             for (int a : {1, 5, 8}) L(k, a, i) = 0.f;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lU += __shfl_xor_sync(0xffffffffu, lU, o);
+    if ((threadIdx.x & 31) == 0 && lU != 0.0) atomicAdd(A.d_u, lU);
+    if (y >= P.ny) return;
     {
         // outlet x = nx-1: unknown a = 3, 6, 7, split by the known fractions
         const int i = y * P.nx + P.nx - 1;
