@@ -308,11 +308,12 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     }
     for (int a = 0; a < kQ; a++) f[a] = q[a] + q[9 + a] + q[18 + a];
     const float rho = r[0] + r[1] + r[2];
+    const float irho = 1.f / rho;  // one division; every other quotient by rho is a product
     const float Fx = A.F[i], Fy = A.F[P.N + i];
     float g[6];
     for (int j = 0; j < 6; j++) g[j] = A.g[j * NP + p];
     float C[kNF];
-    for (int k = 0; k < kNF; k++) C[k] = r[k] / rho;
+    for (int k = 0; k < kNF; k++) C[k] = r[k] * irho;
     // moments
     const float e = -4.f * f[0] - (f[1] + f[2] + f[3] + f[4]) + 2.f * (f[5] + f[6] + f[7] + f[8]);
     const float eps = 4.f * f[0] - 2.f * (f[1] + f[2] + f[3] + f[4]) + (f[5] + f[6] + f[7] + f[8]);
@@ -322,7 +323,7 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     const float qy = -2.f * (f[2] - f[4]) + f[5] + f[6] - f[7] - f[8];
     const float pxx = f[1] - f[2] + f[3] - f[4];
     const float pxy = f[5] - f[6] + f[7] - f[8];
-    const float ux = (jx + 0.5f * Fx) / rho, uy = (jy + 0.5f * Fy) / rho;
+    const float ux = (jx + 0.5f * Fx) * irho, uy = (jy + 0.5f * Fy) * irho;
     const float u2 = ux * ux + uy * uy, uF = ux * Fx + uy * Fy;
     const float D = r[0] * P.inv_nu0 + r[1] * P.inv_nu1 + r[2] * P.inv_nu2;
     const float s1 = D / (0.5f * D + 3.0f);
@@ -338,10 +339,10 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     // f_dag = f + M^-1 dm
     float fd[kQ];
     {
-        const float c0 = (dEps - dE) / 9.f;
-        const float ca = -dE / 36.f - dEps / 18.f, cd = dE / 18.f + dEps / 36.f;
-        const float X1 = (Fx - dqx) / 6.f, Y1 = (Fy - dqy) / 6.f;
-        const float X2 = Fx / 6.f + dqx / 12.f, Y2 = Fy / 6.f + dqy / 12.f;
+        const float c0 = (dEps - dE) * (1.f / 9.f);
+        const float ca = -dE * (1.f / 36.f) - dEps * (1.f / 18.f), cd = dE * (1.f / 18.f) + dEps * (1.f / 36.f);
+        const float X1 = (Fx - dqx) * (1.f / 6.f), Y1 = (Fy - dqy) * (1.f / 6.f);
+        const float X2 = Fx * (1.f / 6.f) + dqx * (1.f / 12.f), Y2 = Fy * (1.f / 6.f) + dqy * (1.f / 12.f);
         const float P4 = 0.25f * dpxx, Q4 = 0.25f * dpxy;
         fd[0] = f[0] + c0;
         fd[1] = f[1] + ca + X1 + P4;
@@ -356,7 +357,7 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     // normals
     const float gg[3][2] = {{g[0], g[1]}, {g[2], g[3]}, {g[4], g[5]}};
     const int pk[3] = {0, 0, 1}, pl[3] = {1, 2, 2};
-    float nxp_[3], nyp_[3], Gx[3], Gy[3], Gn[3];
+    float nxp_[3], nyp_[3], Gx[3], Gy[3], rGn[3];
     bool act[3];
     for (int m = 0; m < 3; m++) {
         const int k = pk[m], l = pl[m];
@@ -364,15 +365,16 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
         Gy[m] = C[l] * gg[k][1] - C[k] * gg[l][1];
         const float G2 = Gx[m] * Gx[m] + Gy[m] * Gy[m];
         act[m] = G2 > 1e-24f;
-        Gn[m] = act[m] ? sqrtf(G2) : 1.f;
-        nxp_[m] = act[m] ? Gx[m] / Gn[m] : 0.f;
-        nyp_[m] = act[m] ? Gy[m] / Gn[m] : 0.f;
+        rGn[m] = act[m] ? rsqrtf(G2) : 1.f;  // 1 / |G|
+        nxp_[m] = act[m] ? Gx[m] * rGn[m] : 0.f;
+        nyp_[m] = act[m] ? Gy[m] * rGn[m] : 0.f;
     }
     const float gX[3] = {P.g01, P.g02, P.g12};
-    const float T3 = 35.f * r[0] * r[1] * r[2] / (rho * rho * rho);
+    const float irho3 = irho * irho * irho;
+    const float T3 = 35.f * r[0] * r[1] * r[2] * irho3;
     const float trip = fminf(T3, 1.0f);
     float b[3];
-    for (int m = 0; m < 3; m++) b[m] = P.beta0 * (1.f + trip * gX[m]) * r[pk[m]] * r[pl[m]] / rho;
+    for (int m = 0; m < 3; m++) b[m] = P.beta0 * (1.f + trip * gX[m]) * r[pk[m]] * r[pl[m]] * irho;
 
     // ---- reverse ----
     float lo[27];
@@ -396,7 +398,7 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
         if (!act[m]) continue;
         const float lnx = b[m] * dV[m][0], lny = b[m] * dV[m][1];
         const float dot = nxp_[m] * lnx + nyp_[m] * lny;
-        const float lGx = (lnx - nxp_[m] * dot) / Gn[m], lGy = (lny - nyp_[m] * dot) / Gn[m];
+        const float lGx = (lnx - nxp_[m] * dot) * rGn[m], lGy = (lny - nyp_[m] * dot) * rGn[m];
         const int k = pk[m], l = pl[m];
         lg[k][0] += C[l] * lGx;
         lg[k][1] += C[l] * lGy;
@@ -410,28 +412,30 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     for (int m = 0; m < 3; m++) {
         const int k = pk[m], l = pl[m];
         const float base = P.beta0 * (1.f + trip * gX[m]);
-        ltrip += lb[m] * P.beta0 * gX[m] * r[k] * r[l] / rho;
-        lr[k] += lb[m] * base * r[l] / rho;
-        lr[l] += lb[m] * base * r[k] / rho;
-        lrho -= lb[m] * b[m] / rho;
+        ltrip += lb[m] * P.beta0 * gX[m] * r[k] * r[l] * irho;
+        lr[k] += lb[m] * base * r[l] * irho;
+        lr[l] += lb[m] * base * r[k] * irho;
+        lrho -= lb[m] * b[m] * irho;
     }
     if (T3 < 1.0f) {
-        lr[0] += ltrip * 35.f * r[1] * r[2] / (rho * rho * rho);
-        lr[1] += ltrip * 35.f * r[0] * r[2] / (rho * rho * rho);
-        lr[2] += ltrip * 35.f * r[0] * r[1] / (rho * rho * rho);
-        lrho -= ltrip * 3.f * T3 / rho;
+        lr[0] += ltrip * 35.f * r[1] * r[2] * irho3;
+        lr[1] += ltrip * 35.f * r[0] * r[2] * irho3;
+        lr[2] += ltrip * 35.f * r[0] * r[1] * irho3;
+        lrho -= ltrip * 3.f * T3 * irho;
     }
     // collision: f_dag = f + M^-1 dm
     float lf[kQ];
     for (int a = 0; a < kQ; a++) lf[a] = lfd[a];
     // lambda of the moment changes = (M^-1)^T lfd
-    const float ldE = (-lfd[0] / 9.f) + (-(lfd[1] + lfd[2] + lfd[3] + lfd[4]) / 36.f) + ((lfd[5] + lfd[6] + lfd[7] + lfd[8]) / 18.f);
-    const float ldEps = (lfd[0] / 9.f) + (-(lfd[1] + lfd[2] + lfd[3] + lfd[4]) / 18.f) + ((lfd[5] + lfd[6] + lfd[7] + lfd[8]) / 36.f);
-    const float lX1 = (lfd[1] - lfd[3]) / 6.f, lY1 = (lfd[2] - lfd[4]) / 6.f;
+    const float ldE = (-lfd[0] * (1.f / 9.f)) + (-(lfd[1] + lfd[2] + lfd[3] + lfd[4]) * (1.f / 36.f)) +
+                      ((lfd[5] + lfd[6] + lfd[7] + lfd[8]) * (1.f / 18.f));
+    const float ldEps = (lfd[0] * (1.f / 9.f)) + (-(lfd[1] + lfd[2] + lfd[3] + lfd[4]) * (1.f / 18.f)) +
+                        ((lfd[5] + lfd[6] + lfd[7] + lfd[8]) * (1.f / 36.f));
+    const float lX1 = (lfd[1] - lfd[3]) * (1.f / 6.f), lY1 = (lfd[2] - lfd[4]) * (1.f / 6.f);
     const float lX2 = (lfd[5] - lfd[6] - lfd[7] + lfd[8]), lY2 = (lfd[5] + lfd[6] - lfd[7] - lfd[8]);
     // X1 = (Fx - dqx)/6, X2 = Fx/6 + dqx/12
-    const float ldqx = -lX1 + lX2 / 12.f, ldqy = -lY1 + lY2 / 12.f;
-    float lFx = lX1 + lX2 / 6.f, lFy = lY1 + lY2 / 6.f;
+    const float ldqx = -lX1 + lX2 * (1.f / 12.f), ldqy = -lY1 + lY2 * (1.f / 12.f);
+    float lFx = lX1 + lX2 * (1.f / 6.f), lFy = lY1 + lY2 * (1.f / 6.f);
     const float ldpxx = 0.25f * (lfd[1] - lfd[2] + lfd[3] - lfd[4]);
     const float ldpxy = 0.25f * (lfd[5] - lfd[6] + lfd[7] - lfd[8]);
     // moment changes -> moments, rho, u, F, s1, s4
@@ -454,10 +458,10 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     lr[1] += lD * P.inv_nu1;
     lr[2] += lD * P.inv_nu2;
     // u = (j + F/2)/rho
-    const float ljx = lux / rho, ljy = luy / rho;
-    lFx += 0.5f * lux / rho;
-    lFy += 0.5f * luy / rho;
-    lrho -= (lux * ux + luy * uy) / rho;
+    const float ljx = lux * irho, ljy = luy * irho;
+    lFx += 0.5f * lux * irho;
+    lFy += 0.5f * luy * irho;
+    lrho -= (lux * ux + luy * uy) * irho;
     // moments -> populations (rows of M)
     for (int a = 0; a < kQ; a++) {
         const int e2 = ex(a) * ex(a) + ey(a) * ey(a);
@@ -471,7 +475,7 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     // C_k = r_k / rho
     float sc = 0.f;
     for (int k = 0; k < kNF; k++) sc += lC[k] * C[k];
-    for (int k = 0; k < kNF; k++) lr[k] += (lC[k] - sc) / rho;
+    for (int k = 0; k < kNF; k++) lr[k] += (lC[k] - sc) * irho;
     for (int k = 0; k < kNF; k++)
         for (int a = 0; a < kQ; a++) A.l_fpost[(long long)(9 * k + a) * P.N + i] = lf[a] + lr[k];
     A.l_F[i] = lFx;
@@ -707,22 +711,34 @@ __global__ void b_frac(const Params P, const Adj A, const uint8_t* __restrict__ 
 // and of the inflow velocity)
 __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__ type)
 {
-    const int y = blockIdx.x * blockDim.x + threadIdx.x;
     if (P.bc_x != kZouHe) return;
-    auto L = [&](int k, int a, int i) -> float& { return A.l_fpost[(long long)(9 * k + a) * P.N + i]; };
-    auto Fv = [&](int k, int a, int i) { return A.fpost[(long long)(9 * k + a) * P.N + i]; };
-    // dJ/dU of this row, summed over the warp before one atomic (rows beyond ny add 0)
+    // threads [0, ny): inlet rows; [ny, 2 ny): outlet rows.  Every value is loaded before any is
+    // written, so that the loads go out together instead of one round trip at a time.
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool inlet = t < P.ny;
+    const int y = inlet ? t : t - P.ny;
+    const bool valid = y < P.ny;
+    const int i = y * P.nx + (inlet ? 0 : P.nx - 1);
+    float fk[27], lk[27];
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < 27; j++) {
+            fk[j] = A.fpost[(long long)j * P.N + i];
+            lk[j] = A.l_fpost[(long long)j * P.N + i];
+        }
+    }
+    float f[kQ];
+#pragma unroll
+    for (int a = 0; a < kQ; a++) f[a] = valid ? fk[a] + fk[9 + a] + fk[18 + a] : 0.f;
+    float lf[kQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, lpart[kNF] = {0, 0, 0};
+    // dJ/dU of this row, summed over the warp before one atomic
     double lU = 0.0;
-    if (y < P.ny) {
+    if (valid && inlet) {
         // inlet x = 0: unknown a = 1, 5, 8 (fluid 2)
-        const int i = y * P.nx;
-        float f[kQ];
-        for (int a = 0; a < kQ; a++) f[a] = Fv(0, a, i) + Fv(1, a, i) + Fv(2, a, i);
         const float U = P.u_in;
         const float rho = (f[0] + f[2] + f[4] + 2.f * (f[3] + f[6] + f[7])) / (1.f - U);
-        const float L1 = L(2, 1, i), L5 = L(2, 5, i), L8 = L(2, 8, i);
+        const float L1 = lk[18 + 1], L5 = lk[18 + 5], L8 = lk[18 + 8];
         const float lrho = (2.f / 3.f) * U * L1 + (U / 6.f) * (L5 + L8);
-        float lf[kQ] = {0};
         lf[3] += L1;
         lf[7] += L5;
         lf[6] += L8;
@@ -736,22 +752,13 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
         lf[6] += 2.f * lrho * ir;
         lf[7] += 2.f * lrho * ir;
         lU = (double)L1 * (2.0 / 3.0) * rho + (double)(L5 + L8) * rho / 6.0 + (double)lrho * rho / (1.0 - U);
-        for (int k = 0; k < kNF; k++)
-            for (int a : {0, 2, 3, 4, 6, 7}) L(k, a, i) += lf[a];
-        for (int k = 0; k < kNF; k++)
-            for (int a : {1, 5, 8}) L(k, a, i) = 0.f;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lU += __shfl_xor_sync(0xffffffffu, lU, o);
-    if ((threadIdx.x & 31) == 0 && lU != 0.0) atomicAdd(A.d_u, lU);
-    if (y >= P.ny) return;
-    {
+    } else if (valid) {
         // outlet x = nx-1: unknown a = 3, 6, 7, split by the known fractions
-        const int i = y * P.nx + P.nx - 1;
-        float f[kQ], part[kNF], tot = 0.f;
-        for (int a = 0; a < kQ; a++) f[a] = Fv(0, a, i) + Fv(1, a, i) + Fv(2, a, i);
+        float part[kNF], tot = 0.f;
+#pragma unroll
         for (int k = 0; k < kNF; k++) {
-            part[k] = Fv(k, 0, i) + Fv(k, 1, i) + Fv(k, 2, i) + Fv(k, 4, i) + Fv(k, 5, i) + Fv(k, 8, i);
+            const float* q = fk + 9 * k;
+            part[k] = q[0] + q[1] + q[2] + q[4] + q[5] + q[8];
             tot += part[k];
         }
         const float ro = P.rho_out;
@@ -759,17 +766,18 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
         const float h3 = f[1] - (2.f / 3.f) * (S - ro);
         const float h7 = f[5] + 0.5f * (f[2] - f[4]) - (S - ro) / 6.f;
         const float h6 = f[8] - 0.5f * (f[2] - f[4]) - (S - ro) / 6.f;
-        float lh3 = 0.f, lh6 = 0.f, lh7 = 0.f, lpart[kNF], acc = 0.f;
+        float lh3 = 0.f, lh6 = 0.f, lh7 = 0.f, acc = 0.f;
+#pragma unroll
         for (int k = 0; k < kNF; k++) {
-            const float a3 = L(k, 3, i), a6 = L(k, 6, i), a7 = L(k, 7, i);
+            const float a3 = lk[9 * k + 3], a6 = lk[9 * k + 6], a7 = lk[9 * k + 7];
             lh3 += a3 * part[k] / tot;
             lh6 += a6 * part[k] / tot;
             lh7 += a7 * part[k] / tot;
             lpart[k] = (a3 * h3 + a6 * h6 + a7 * h7) / tot;
             acc += lpart[k] * part[k] / tot;
         }
+#pragma unroll
         for (int k = 0; k < kNF; k++) lpart[k] -= acc;
-        float lf[kQ] = {0};
         // h3 = f1 - (2/3)(S - ro), h7 = f5 + (f2 - f4)/2 - (S - ro)/6, h6 = f8 - (f2 - f4)/2 - (S - ro)/6
         lf[1] += lh3 * (1.f - 4.f / 3.f);
         lf[0] += lh3 * (-2.f / 3.f);
@@ -789,11 +797,20 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
         lf[0] += lh6 * (-1.f / 6.f);
         lf[1] += lh6 * (-1.f / 3.f);
         lf[5] += lh6 * (-1.f / 3.f);
-        for (int k = 0; k < kNF; k++)
-            for (int a : {0, 1, 2, 4, 5, 8}) L(k, a, i) += lf[a] + lpart[k];
-        for (int k = 0; k < kNF; k++)
-            for (int a : {3, 6, 7}) L(k, a, i) = 0.f;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) lU += __shfl_xor_sync(0xffffffffu, lU, o);
+    if ((threadIdx.x & 31) == 0 && lU != 0.0) atomicAdd(A.d_u, lU);
+    if (!valid) return;
+    // the unknown populations were set by the boundary, so their adjoint ends here; the known
+    // ones collect the boundary's contribution
+#pragma unroll
+    for (int k = 0; k < kNF; k++)
+#pragma unroll
+        for (int a = 0; a < kQ; a++) {
+            const bool unknown = inlet ? (a == 1 || a == 5 || a == 8) : (a == 3 || a == 6 || a == 7);
+            A.l_fpost[(long long)(9 * k + a) * P.N + i] = unknown ? 0.f : lk[9 * k + a] + (lf[a] + lpart[k]);
+        }
 }
 
 // B7b: adjoint of the pull: the stored population (s, a) was read by exactly one puller
@@ -915,7 +932,7 @@ void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_
     const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
     a_dens<<<gp, 128, 0, s>>>(P, A, fs, type);
     b_seed<<<gn, 128, 0, s>>>(P, A, type, J, M0);
-    b_zouhe<<<(P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
+    b_zouhe<<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
     cudaMemsetAsync(A.l_cw, 0, sizeof(float) * 3 * (size_t)P.N, s);
 }
@@ -946,7 +963,7 @@ void adjoint_step(const Params& P, AdjointWork* W, int nw, const int* widx, cons
     cudaMemsetAsync(A.l_cw2, 0, sizeof(float) * 3 * (size_t)P.N, s);
     if (nw > 0) b_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, A, nw, widx, wang, cw_lag, type);
     b_frac<<<gn, 128, 0, s>>>(P, A, type);
-    b_zouhe<<<(P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
+    b_zouhe<<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
     std::swap(A.l_cw, A.l_cw2);
 }
