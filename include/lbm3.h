@@ -87,9 +87,11 @@ int lbm3_set_fields(lbm3* h, const double* rho);
  * the wetting pass over the C_SB list (Eq.21-22) and the fused step kernel (Eq.1-16: densities,
  * gradients, interfacial force, MRT collision, recolouring, streaming with halfway bounce-back
  * and the x boundary).  Tiles with no solid node within 3 nodes run concurrently with the wetting
- * pass on the handle's stream; the other tiles follow the wetting pass on an internal
- * higher-priority stream that is joined back before the call's work completes.  The velocity of
- * the last collision of the call is recorded for lbm3_fields / lbm3_diag. */
+ * pass on the handle's stream (through bulk tensor copies when nx is a multiple of 4, on the SMs
+ * that the other tiles' share of the work leaves); the other tiles follow the wetting pass on an
+ * internal higher-priority stream that is joined back before the call's work completes.  The
+ * velocity of the last collision of the call is recorded for lbm3_fields / lbm3_diag.  A bulk
+ * copy that does not complete within its wait limit is reported by the next lbm3_diag. */
 int lbm3_step(lbm3* h, int32_t nsteps);
 
 /* lbm3_step with per-launch timing: CUDA events are recorded around every launch on the stream
