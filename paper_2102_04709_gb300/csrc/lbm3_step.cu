@@ -521,8 +521,8 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
         if (inl) zou_he(P, q, true);
         if (outl) zou_he(P, q, false);
     };
-    // densities / phase fields of the position (cx, cy) of the phase-field region from q; in
-    // pure tiles also which fluids occur in the region (bit k: some rho_k != 0)
+    // densities / phase fields of the position (cx, cy) of the phase-field region from q, and which
+    // fluids occur in the region (bit k: some rho_k != 0, or a wall value C_k != 0 at a C_SB node)
     int present = 0;
     auto store_phase = [&](int cx, int cy, const float q[27]) {
         if (df) {
@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
 #pragma unroll
             for (int k = 0; k < kNF; k++) div_df(rh[k], rl[k], dh, sl, s_ch[k][cy][cx], s_cl[k][cy][cx]);
             s_rho[cy][cx] = dh;
+            present = 7;  // float-float tiles (mixed wall values) are never skipped
         } else {
             float r[kNF];
 #pragma unroll
@@ -545,8 +546,7 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
                 const float* qk = q + 9 * k;
                 r[k] = ((qk[0] + (qk[1] + qk[3])) + (qk[2] + qk[4])) + ((qk[5] + qk[7]) + (qk[6] + qk[8]));
             }
-            if constexpr (PURE)
-                present |= (r[0] != 0.0f ? 1 : 0) | (r[1] != 0.0f ? 2 : 0) | (r[2] != 0.0f ? 4 : 0);
+            present |= (r[0] != 0.0f ? 1 : 0) | (r[1] != 0.0f ? 2 : 0) | (r[2] != 0.0f ? 4 : 0);
             const float rho = (r[0] + r[1]) + r[2];
             const float ir = __fdividef(1.0f, rho);
 #pragma unroll
@@ -572,6 +572,7 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
                 const float h = (float)c;
                 s_ch[k][cy][cx] = h;
                 s_cl[k][cy][cx] = (float)(c - (double)h);
+                if (c != 0.0) present |= 1 << k;
             }
             s_rho[cy][cx] = 1.0f;
         } else {
@@ -617,11 +618,7 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
         r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
         r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
     }
-    bool mixed = true;
-    if constexpr (PURE)
-        mixed = single_fluid_or(present) != 1;
-    else
-        __syncthreads();
+    const bool mixed = single_fluid_or(present) != 1;
 
     // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
     for (int j = mixed ? tid : RX * RY; j < RX * RY; j += NT) {
