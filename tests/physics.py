@@ -66,3 +66,59 @@ def cap_workload(theta, Rc=12.0, nx=80, ny=40, nu=1.0 / 6.0):
     ang[..., 2] = 90.0
     return Workload(f"cap{theta}", nx, ny, 0, BC_PERIODIC, solid, rho, ang, (0.01,) * 3,
                     (nu,) * 3, steps=0)
+
+
+
+def _cap_angle_inside(p, wall_y):
+    """Angle (deg) at the wall, measured inside the phase enclosed by a circle fitted to the
+    arc p[:, 2] of a cap on a horizontal wall at wall_y: cos(theta) = -(yc - wall_y) / R."""
+    xc, yc, R = fit_circle(p)
+    return float(np.degrees(np.arccos(np.clip(-(yc - wall_y) / R, -1.0, 1.0))))
+
+
+def janus_angles(rho, solid, wall_y=0.5, y_min=0.5, frac=0.7):
+    """The three contact angles (deg) of a Janus droplet (fluid 0 on the left, fluid 2 on the
+    right, both in fluid 1) resting on the bottom wall, as (theta_01, theta_20, theta_12),
+    theta_kl measured inside fluid k:
+
+    * theta_01 at the left contact line: circle fitted to the left arc of the C_1 = 1/2
+      contour (a cap enclosing fluid 0);
+    * theta_12 at the right contact line: 180 deg minus the angle inside fluid 2 of the
+      circle fitted to the right arc;
+    * theta_20 where the internal interface, the C_0 / (C_0 + C_2) = 1/2 contour inside the
+      droplet, meets the wall: fitted by x = a + b y + c y^2, its tangent (b, 1) at the wall
+      makes the angle with the +x direction, the wall on the fluid-2 side.
+
+    Each arc is fitted between wall_y + y_min and wall_y + frac * H, H the height of the triple
+    junction (the top of the internal interface), so that the rounded junction region, where
+    the three interfaces meet at the Neumann angles, stays out of the fits."""
+    rho = np.asarray(rho, dtype=np.float64)
+    C = rho / np.maximum(rho.sum(0), 1e-30)
+    s = np.asarray(solid).astype(bool)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        phi = np.where(C[1] < 0.5, C[0] / (C[0] + C[2]), np.nan)
+    inner = contour_points(phi, s)
+    H = inner[:, 1].max() - wall_y
+    band = lambda p: p[(p[:, 1] > wall_y + y_min) & (p[:, 1] < wall_y + frac * H)]
+    inner = band(inner)
+    outer = band(contour_points(C[1], s))
+    xm = inner[:, 0].mean()
+    t01 = _cap_angle_inside(outer[outer[:, 0] < xm], wall_y)
+    t12 = 180.0 - _cap_angle_inside(outer[outer[:, 0] > xm], wall_y)
+    yy = inner[:, 1] - wall_y
+    b = np.linalg.lstsq(np.c_[np.ones_like(yy), yy, yy * yy], inner[:, 0], rcond=None)[0][1]
+    t20 = float(np.degrees(np.arctan2(1.0, b)))
+    return t01, t20, t12
+
+
+def table1():
+    """The six angle sets of Table I: [(label, analytical (rg, br, gb), simulated (rg, br, gb))]."""
+    import os
+    rows = []
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                        "table1_janus_flat.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            t = line.split()
+            rows.append((t[0], tuple(map(float, t[1:4])), tuple(map(float, t[4:7]))))
+    return rows
