@@ -27,8 +27,10 @@
  *   - weights of directions 5-8 are 1/36 (the text prints "5-6"; the weights must sum to 1)
  *   - Eq.(10) sums ordered pairs with a factor 1/2, i.e. each unordered pair once
  *   - n_kl = 0 and no stress contribution when |G_kl|^2 <= 1e-24
- *   - the stress tensor is also evaluated at C_SB nodes; a C_SI (or out-of-domain
- *     solid) neighbour in that stencil takes the C_SB node's own value
+  *   - the stress tensor is also evaluated at C_SB nodes; a neighbour in that stencil with no
+ *     C of its own (C_SI, or solid beyond a wall side) takes the linear extrapolation
+ *     2 C(P) - C(P - e_a) through the C_SB node P, or C(P) when P - e_a has no C either
+ *     (this reading reproduces the angles of Table I; C(P) alone biased them towards 90 deg)
  *   - at C_SB nodes rho := 1, so rho_k = C_k for A_kl
  *   - "in contact with" means any of the 8 D2Q9 neighbours
  *   - n_s of Eq.(19) points into the solid; the characteristic lines use -n_s
@@ -273,7 +275,16 @@ static void state_at(const ora_t* o, int X, int Y, double c[NF], double rk[NF])
     }
 }
 
-/* grad C_k at (X, Y) by Eq.(12); C_SI / out-of-domain solid neighbours take the centre value */
+/* a position whose C is never defined: solid beyond a wall side, a C_SI node, or the ghost
+ * copy of a C_SI node beyond an open side */
+static int no_value(const ora_t* o, int loc, int idx)
+{
+    return loc == LOC_SOLID || o->cls[idx] == CL_SI;
+}
+
+/* grad C_k at (X, Y) by Eq.(12).  Only a C_SB centre has neighbours without a value; such a
+ * neighbour P + e_a takes the value on the straight line through the opposite neighbour and
+ * the centre, 2 C(P) - C(P - e_a) (the centre's own value when P - e_a has none either) */
 static void grad_at(const ora_t* o, int X, int Y, double g[NF][2])
 {
     double c0[NF], r0[NF];
@@ -283,8 +294,14 @@ static void grad_at(const ora_t* o, int X, int Y, double g[NF][2])
         int idx, sw;
         int loc = locate(o, X + EX[a], Y + EY[a], &idx, &sw);
         double cv[NF];
-        if (loc == LOC_SOLID || (loc == LOC_IN && o->cls[idx] == CL_SI)) {
-            for (int k = 0; k < NF; k++) cv[k] = c0[k];
+        if (no_value(o, loc, idx)) {
+            int idx2, sw2;
+            int loc2 = locate(o, X - EX[a], Y - EY[a], &idx2, &sw2);
+            if (no_value(o, loc2, idx2)) {
+                for (int k = 0; k < NF; k++) cv[k] = c0[k];
+            } else {
+                for (int k = 0; k < NF; k++) cv[k] = 2.0 * c0[k] - c_at(o, idx2, sw2, k);
+            }
         } else {
             for (int k = 0; k < NF; k++) cv[k] = c_at(o, idx, sw, k);
         }

@@ -210,28 +210,39 @@ __device__ __forceinline__ bool is_active(const Params& P, const Adj& A, const u
     return cls != kSI;
 }
 
-// gather of the 9-point stencil of C_k around the position (gx, gy) (in-domain or ghost);
-// v[a] and the padded position src[a] the value came from (C_SI / wall-side neighbours of a
-// C_SB centre take the centre's own value)
+// gather of the 9-point stencil of C_k around the position (gx, gy) (in-domain or ghost):
+// v[a] = m[a] C[src[a]] - C[src2[a]], the second term only where src2[a] >= 0.  At a C_SB centre
+// a neighbour without a value of its own (C_SI, or solid beyond a wall side) is the
+// extrapolation 2 C(centre) - C(opposite neighbour), or C(centre) when the opposite neighbour
+// has no value either.
 __device__ __forceinline__ void stencil_C(const Params& P, const Adj& A, const uint8_t* type, int gx,
-                                          int gy, int cls, int k, float v[kQ], int src[kQ])
+                                          int gy, int cls, int k, float v[kQ], int src[kQ], int src2[kQ],
+                                          float m[kQ])
 {
     const int NP = P.ny * A.nxp;
     int kind;
     const int pc = cpos(P, A, gx, gy, kind);
+    // kd == 1: solid beyond a wall side; otherwise the class of the node (or of the boundary
+    // column node a ghost copies)
+    auto no_value = [&](int kd, int q) { return kd == 1 || (type[(q / A.nxp) * P.nx + q % A.nxp - 1] & 3) == kSI; };
     for (int a = 0; a < kQ; a++) {
         int kd;
         int q = cpos(P, A, gx + ex(a), gy + ey(a), kd);
-        if (cls == kSB && a > 0) {
-            bool si = kd == 1;
-            if (!si) {
-                const int qx = q % A.nxp - 1, qy = q / A.nxp;
-                si = (type[qy * P.nx + qx] & 3) == kSI;
+        int q2 = -1;
+        float mm = 1.0f;
+        if (cls == kSB && a > 0 && no_value(kd, q)) {
+            int kd2;
+            const int qo = cpos(P, A, gx - ex(a), gy - ey(a), kd2);
+            q = pc;
+            if (!no_value(kd2, qo)) {
+                q2 = qo;
+                mm = 2.0f;
             }
-            if (si) q = pc;
         }
         src[a] = q;
-        v[a] = A.C[k * NP + q];
+        src2[a] = q2;
+        m[a] = mm;
+        v[a] = q2 < 0 ? A.C[k * NP + q] : mm * A.C[k * NP + q] - A.C[k * NP + q2];
     }
 }
 
@@ -247,9 +258,9 @@ __global__ void a_grad_stress(const Params P, const Adj A, const uint8_t* __rest
     const int p = pad(A, gx, y);
     float c[kNF], gxk[kNF], gyk[kNF];
     for (int k = 0; k < kNF; k++) {
-        float v[kQ];
-        int src[kQ];
-        stencil_C(P, A, type, gx, y, cls, k, v, src);
+        float v[kQ], m[kQ];
+        int src[kQ], src2[kQ];
+        stencil_C(P, A, type, gx, y, cls, k, v, src, src2, m);
         c[k] = v[0];
         gxk[k] = (1.0f / 3.0f) * (v[1] - v[3]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[8] - v[6]));
         gyk[k] = (1.0f / 3.0f) * (v[2] - v[4]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[6] - v[8]));
@@ -575,12 +586,15 @@ __global__ void b_stress_grad(const Params P, const Adj A, const uint8_t* __rest
     for (int k = 0; k < kNF; k++) {
         if (lc[k] != 0.f) atomicAdd(&A.l_C[k * NP + pc], lc[k]);
         // gradient stencil transpose
-        float v[kQ];
-        int src[kQ];
-        stencil_C(P, A, type, gx, y, cls, k, v, src);
+        float v[kQ], m[kQ];
+        int src[kQ], src2[kQ];
+        stencil_C(P, A, type, gx, y, cls, k, v, src, src2, m);
         for (int a = 1; a < kQ; a++) {
             const float w = 3.0f * wq(a) * (ex(a) * lg[k][0] + ey(a) * lg[k][1]);
-            if (w != 0.f) atomicAdd(&A.l_C[k * NP + src[a]], w);
+            if (w != 0.f) {
+                atomicAdd(&A.l_C[k * NP + src[a]], m[a] * w);
+                if (src2[a] >= 0) atomicAdd(&A.l_C[k * NP + src2[a]], -w);
+            }
         }
     }
     // rho is 1 at C_SB nodes (no dependence); at fluid and ghost positions it is the pulled total

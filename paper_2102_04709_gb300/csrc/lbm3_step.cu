@@ -632,17 +632,30 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
 #pragma unroll
             for (int k = 0; k < kNF; k++) c[k] = s_ch[k][cy][cx];
             if (!PURE && (t & 3) == kSB) {
-                // solid node: a solid-interior neighbour takes the node's own value
+                // solid node: a neighbour P + e_a without a value of its own (C_SI, or solid
+                // beyond a wall side) takes the extrapolation 2 C(P) - C(P - e_a) through the
+                // node, with its rounding error carried in the lo word; C(P) itself when P - e_a
+                // has no value either (the lo words of the phase fields exist only in
+                // float-float tiles)
 #pragma unroll
-                // (the lo words exist only in float-float tiles)
                 for (int k = 0; k < kNF; k++) {
                     float v[kQ], vl[kQ];
                     const float ch = s_ch[k][cy][cx], cl = df ? s_cl[k][cy][cx] : 0.0f;
 #pragma unroll
                     for (int a = 1; a < kQ; a++) {
-                        const bool si = (s_t[hy + ey(a)][hx + ex(a)] & 3) == kSI;
-                        v[a] = si ? ch : s_ch[k][cy + ey(a)][cx + ex(a)];
-                        vl[a] = si || !df ? cl : s_cl[k][cy + ey(a)][cx + ex(a)];
+                        if ((s_t[hy + ey(a)][hx + ex(a)] & 3) != kSI) {
+                            v[a] = s_ch[k][cy + ey(a)][cx + ex(a)];
+                            vl[a] = df ? s_cl[k][cy + ey(a)][cx + ex(a)] : 0.0f;
+                        } else if ((s_t[hy - ey(a)][hx - ex(a)] & 3) == kSI) {
+                            v[a] = ch;
+                            vl[a] = cl;
+                        } else {
+                            const float oh = s_ch[k][cy - ey(a)][cx - ex(a)];
+                            const float ol = df ? s_cl[k][cy - ey(a)][cx - ex(a)] : 0.0f;
+                            float e;
+                            two_sum(2.0f * ch, -oh, v[a], e);
+                            vl[a] = (2.0f * cl - ol) + e;
+                        }
                     }
                     gxk[k] = (1.0f / 3.0f) * (v[1] - v[3]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[8] - v[6])) +
                              ((1.0f / 3.0f) * (vl[1] - vl[3]) + (1.0f / 12.0f) * ((vl[5] - vl[7]) + (vl[8] - vl[6])));
