@@ -169,22 +169,22 @@ bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in_a, CUtensorMap*
 }
 
 // Tensor maps of one 16-bit-storage population buffer: the densities rho[3][ny][nx] (FP32, box
-// (kTX + 8) x (kTY + 6) x 3) and the offset records off[3][ny][nx] as 16-bit words
-// [3][ny][nx][8] (box 8 x (kTX + 8) x (kTY + 6) x 3).
+// (kTX + 8) x (kTY + 6) x 3) and the offset planes off[24][ny][nx] (16-bit words, box
+// (kTX + 16) x (kTY + 6) x 24; its row pitch 2 nx bytes must be a multiple of 16).
 bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtensorMap* toff)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
     if (!encode) return false;
     const cuuint64_t rdims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 3};
     const cuuint64_t rstrides[2] = {(cuuint64_t)P.nx * sizeof(float), (cuuint64_t)P.N * sizeof(float)};
-    const cuuint32_t rbox[3] = {kTX + 8, kTY + 6, 3}, runit[3] = {1, 1, 1};
-    const cuuint64_t odims[4] = {8, (cuuint64_t)P.nx, (cuuint64_t)P.ny, 3};
-    const cuuint64_t ostrides[3] = {16, (cuuint64_t)P.nx * 16, (cuuint64_t)P.N * 16};
-    const cuuint32_t obox[4] = {8, kTX + 8, kTY + 6, 3}, ounit[4] = {1, 1, 1, 1};
-    return encode(trho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p.rho, rdims, rstrides, rbox, runit,
+    const cuuint32_t rbox[3] = {kTX + 8, kTY + 6, 3}, unit[3] = {1, 1, 1};
+    const cuuint64_t odims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 24};
+    const cuuint64_t ostrides[2] = {(cuuint64_t)P.nx * 2, (cuuint64_t)P.N * 2};
+    const cuuint32_t obox[3] = {kTX + 16, kTY + 6, 24};
+    return encode(trho, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, p.rho, rdims, rstrides, rbox, unit,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS &&
-           encode(toff, CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, p.off, odims, ostrides, obox, ounit,
+           encode(toff, CU_TENSOR_MAP_DATA_TYPE_UINT16, 3, p.off, odims, ostrides, obox, unit,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -397,6 +397,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
             P.off_plane[k * kQ + a] = (k * kQ + a) * (int)N;
             P.off_pull[k * kQ + a] = (k * kQ + a) * (int)N - ex(a) - ey(a) * nx;
             P.off_pull16[k * kQ + a] = k * (int)N - ex(a) - ey(a) * nx;
+            P.off_pull16o[k * kQ + a] = a > 0 ? (8 * k + a - 1) * (int)N - ex(a) - ey(a) * nx : 0;
         }
     h->nw = (int)widx.size();
     h->n_fluid = n_fluid;
@@ -418,7 +419,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
             if (e == cudaSuccess) e = dmalloc((void**)&h->pop[b].f, (size_t)27 * N * sizeof(float));
         } else {
             if (e == cudaSuccess) e = dmalloc((void**)&h->pop[b].rho, (size_t)3 * N * sizeof(float));
-            if (e == cudaSuccess) e = dmalloc((void**)&h->pop[b].off, (size_t)3 * N * sizeof(uint4));
+            if (e == cudaSuccess) e = dmalloc((void**)&h->pop[b].off, (size_t)24 * N * sizeof(unsigned short));
         }
     }
     if (e == cudaSuccess) e = dmalloc((void**)&h->type, N);
@@ -451,8 +452,9 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (e == cudaSuccess) e = cudaMemset(h->Cw, 0, 3 * N * sizeof(double));
     if (e == cudaSuccess) e = cudaMemset(h->u, 0, 2 * N * sizeof(float));
     // pure tiles through bulk tensor copies where the layout allows them (row pitch a multiple of
-    // 16 bytes); LBM3_DISABLE_TMA=1 in the environment keeps the plain kernel
-    if (e == cudaSuccess && nx % 4 == 0 && h->n_pure > 0) {
+    // 16 bytes: nx % 4 == 0 for FP32 populations, nx % 8 == 0 for 16-bit offset planes);
+    // LBM3_DISABLE_TMA=1 in the environment keeps the plain kernel
+    if (e == cudaSuccess && nx % (g->precision == LBM3_FP32 ? 4 : 8) == 0 && h->n_pure > 0) {
         const char* off = std::getenv("LBM3_DISABLE_TMA");
         const bool f32 = g->precision == LBM3_FP32;
         bool maps = !(off && off[0] == '1');

@@ -60,19 +60,24 @@ struct Params {
     // reduced storage: element offsets k * N - e_ax - e_ay * nx of the pull sources in the rho and
     // offset-record planes
     int off_pull16[27];
+    // reduced storage: element offsets (8 k + a - 1) * N - e_ax - e_ay * nx of the pull sources in
+    // the 16-bit offset planes (a >= 1; entry a = 0 unused)
+    int off_pull16o[27];
     // device word of error bits set by kernels (bit 0: a bulk tensor copy did not complete)
     int* err;
 };
 
 // One population buffer.  FP32 storage: f[27][N], plane k*9+a, the post-collision populations
 // f''_ak.  Reduced storage (FP16 / BF16 offsets): rho[3][N] = sum_a f''_ak in FP32 and
-// off[3][N] = one 16-byte record per node and fluid holding the 8 offsets f''_ak - w_a rho_k
-// (a = 1..8, element a-1); the rest population is w_0 rho_k - sum of the offsets, so the
-// stored mass of every fluid is exact whatever the 16-bit rounding.
+// off[3][8][N] = 24 planes of 16-bit words, plane 8k + a - 1 holding the offsets
+// f''_ak - w_a rho_k (a = 1..8); the rest population is w_0 rho_k - sum of the offsets, so the
+// stored mass of every fluid is exact whatever the 16-bit rounding.  Planes (rather than one
+// 16-byte record per node) keep the 16-bit reads of a warp contiguous, in global and in shared
+// memory.
 struct Pop {
     float* f;
     float* rho;
-    uint4* off;
+    unsigned short* off;
 };
 
 template <int STORE>
@@ -91,6 +96,13 @@ __device__ __forceinline__ unsigned short enc16(float v)
         return __half_as_ushort(__float2half_rn(v));
     else
         return __bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
+// sum of the 8 decoded offsets d[1..8] of one node and fluid, in the one order every kernel uses
+// for the rest population w_0 rho_k - sum
+__device__ __forceinline__ float sum_offsets(const float d[kQ])
+{
+    return ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
 }
 
 __host__ __device__ inline int floordiv_i(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
@@ -203,24 +215,22 @@ struct Store<kStoreF32> {
 template <int STORE>
 struct Store16 {
     const float* rho;
-    const uint4* off;
+    const unsigned short* off;
     long long N;
     __host__ __device__ Store16(const Pop& p, long long n) : rho(p.rho), off(p.off), N(n) {}
+    // offset of population a >= 1 of fluid k at node idx
     __device__ __forceinline__ float offset(int k, int a, int idx) const
     {
-        return dec16<STORE>(__ldg(reinterpret_cast<const unsigned short*>(off + (long long)k * N + idx) + (a - 1)));
+        return dec16<STORE>(__ldg(off + (long long)(8 * k + a - 1) * N + idx));
     }
     __device__ __forceinline__ float get(int k, int a, int idx) const
     {
         const float r = __ldg(rho + (long long)k * N + idx);
         if (a > 0) return wq(a) * r + offset(k, a, idx);
-        const uint4 w = __ldg(off + (long long)k * N + idx);
-        const unsigned u[4] = {w.x, w.y, w.z, w.w};
-        float s = 0.0f;
+        float d[kQ];
 #pragma unroll
-        for (int j = 0; j < 4; j++)
-            s += dec16<STORE>((unsigned short)(u[j] & 0xffffu)) + dec16<STORE>((unsigned short)(u[j] >> 16));
-        return wq(0) * r - s;
+        for (int b = 1; b < kQ; b++) d[b] = offset(k, b, idx);
+        return wq(0) * r - sum_offsets(d);
     }
 };
 template <>
@@ -244,12 +254,9 @@ __device__ __forceinline__ void store_node(const Pop& out, long long N, int i, c
         for (int k = 0; k < kNF; k++) {
             const float* q = v + 9 * k;
             const float r = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
-            unsigned short h[8];
-#pragma unroll
-            for (int a = 1; a < kQ; a++) h[a - 1] = enc16<STORE>(q[a] - wq(a) * r);
             out.rho[(long long)k * N + i] = r;
-            out.off[(long long)k * N + i] = make_uint4(h[0] | ((unsigned)h[1] << 16), h[2] | ((unsigned)h[3] << 16),
-                                                       h[4] | ((unsigned)h[5] << 16), h[6] | ((unsigned)h[7] << 16));
+#pragma unroll
+            for (int a = 1; a < kQ; a++) out.off[(long long)(8 * k + a - 1) * N + i] = enc16<STORE>(q[a] - wq(a) * r);
         }
     }
 }

@@ -459,22 +459,16 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
                     }
                 }
             } else {
-                // own record: rho_k and the 8 offsets (the rest population and any bounce-back)
+                // own node: rho_k and the 8 offsets (the rest population and any bounce-back)
                 const float* rb = fin.rho + i;
-                const uint4* ob = fin.off + i;
+                const unsigned short* ob = fin.off + i;
 #pragma unroll
                 for (int k = 0; k < kNF; k++) {
                     const float rk = __ldg(rb + k * N);
-                    const uint4 w = __ldg(ob + k * N);
-                    const unsigned u[4] = {w.x, w.y, w.z, w.w};
                     float d[kQ];
 #pragma unroll
-                    for (int j = 0; j < 4; j++) {
-                        d[2 * j + 1] = dec16<STORE>((unsigned short)(u[j] & 0xffffu));
-                        d[2 * j + 2] = dec16<STORE>((unsigned short)(u[j] >> 16));
-                    }
-                    const float ds = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-                    q[9 * k] = wq(0) * rk - ds;
+                    for (int a = 1; a < kQ; a++) d[a] = dec16<STORE>(__ldg(ob + (8 * k + a - 1) * N));
+                    q[9 * k] = wq(0) * rk - sum_offsets(d);
 #pragma unroll
                     for (int a = 1; a < kQ; a++) {
                         const bool bb = !fi && (s_t[hy - ey(a)][hx - ex(a)] & 2);
@@ -483,7 +477,7 @@ __global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __re
                         } else {
                             const int o = P.off_pull16[k * kQ + a];
                             q[9 * k + a] = wq(a) * __ldg(fin.rho + i + o) +
-                                           dec16<STORE>(__ldg(reinterpret_cast<const unsigned short*>(fin.off + i + o) + (a - 1)));
+                                           dec16<STORE>(__ldg(ob + P.off_pull16o[k * kQ + a]));
                         }
                     }
                 }
@@ -1199,10 +1193,12 @@ void launch_step(int store, const Params& P, const int* tiles, int ntiles, int k
 
 // Pure tiles of the 16-bit storage through the tensor memory accelerator, persistent, with the
 // tile loop of k_step_tma: per tile one bulk copy of the FP32 densities (box (TX + 8) x (TY + 6)
-// x 3) and one of the 16-byte offset records (box 8 x (TX + 8) x (TY + 6) x 3 of 16-bit words)
-// complete on an mbarrier; a pull rebuilds w_a rho_k + offset at its source, the rest population
-// from the node's own record, exactly as the plain kernel does from global memory.  The next
-// tile's boxes are fetched as soon as the pulls are done.
+// x 3 from (x0 - 4, y0 - 3)) and one of the 24 planes of 16-bit offsets (box (TX + 16) x (TY + 6)
+// x 24 from (x0 - 8, y0 - 3): a 16-bit box must start on a 16-byte boundary) complete on an
+// mbarrier; a pull rebuilds w_a rho_k + offset at its source, the rest population from the
+// node's own offsets, exactly as the plain kernel does from global memory.  A warp's reads of
+// one plane are consecutive 16-bit words (no bank conflicts).  The next tile's boxes are fetched
+// as soon as the pulls are done.
 template <int TX, int TY, int STORE>
 __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const Params P, const int* __restrict__ tiles,
                                                             const int ntiles, const Pop fout,
@@ -1213,17 +1209,19 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
     constexpr int NT = TX * TY;
     constexpr int CX = TX + 4, CY = TY + 4;
     constexpr int RX = TX + 2, RY = TY + 2;
-    constexpr int BX = TX + 8, BY = TY + 6;
-    constexpr int NR = kNF * BY * BX;                 // floats of the density box
-    constexpr int NRP = (NR + 31) / 32 * 32;         // keeps the record box 128-byte aligned
-    constexpr uint32_t kBytes = NR * 4u + NR * 16u;  // both copies
+    constexpr int BX = TX + 8, BY = TY + 6;          // density box
+    constexpr int OX = TX + 16;                      // width of the offset box
+    constexpr int NR = kNF * BY * BX;                // floats of the density box
+    constexpr int NRP = (NR + 31) / 32 * 32;         // keeps the offset box 128-byte aligned
+    constexpr int PO = BY * OX;                      // 16-bit words of one offset plane
+    constexpr uint32_t kBytes = NR * 4u + 24u * PO * 2u;  // both copies
     __shared__ float s_ch[kNF][CY][CX];
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
     __shared__ __align__(8) uint64_t s_bar;
     extern __shared__ unsigned char dsm[];
     float* rbox = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [3][BY][BX]
-    const unsigned short* obox = reinterpret_cast<const unsigned short*>(rbox + NRP);          // [3][BY][BX][8]
+    const unsigned short* obox = reinterpret_cast<const unsigned short*>(rbox + NRP);          // [24][BY][OX]
 
     const int tid = threadIdx.x + TX * threadIdx.y;
     const int lx = threadIdx.x, ly = threadIdx.y;
@@ -1234,7 +1232,7 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
         const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
         mbar_arrive_expect_tx(bar, kBytes);
         tma_load_3d(smem_u32(rbox), &tm_rho, x0 - 4, y0 - 3, 0, bar);
-        tma_load_4d(smem_u32(obox), &tm_off, 0, x0 - 4, y0 - 3, 0, bar);
+        tma_load_3d(smem_u32(obox), &tm_off, x0 - 8, y0 - 3, 0, bar);
     };
     int tile = tiles[blockIdx.x];
     int last = 0;
@@ -1247,24 +1245,19 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
 
     // pull of the node at (cx, cy) of the phase-field region from the boxes
     auto pull = [&](int cx, int cy, float q[27]) {
-        const int own = (cy + 1) * BX + cx + 2;
+        const int own = (cy + 1) * BX + cx + 2, owno = (cy + 1) * OX + cx + 6;
 #pragma unroll
         for (int k = 0; k < kNF; k++) {
             const float rk = rbox[k * BY * BX + own];
-            const uint4 w = *reinterpret_cast<const uint4*>(obox + 8 * (k * BY * BX + own));
-            const unsigned u[4] = {w.x, w.y, w.z, w.w};
             float d[kQ];
 #pragma unroll
-            for (int jj = 0; jj < 4; jj++) {
-                d[2 * jj + 1] = dec16<STORE>((unsigned short)(u[jj] & 0xffffu));
-                d[2 * jj + 2] = dec16<STORE>((unsigned short)(u[jj] >> 16));
-            }
-            const float ds = ((d[1] + d[3]) + (d[2] + d[4])) + ((d[5] + d[7]) + (d[6] + d[8]));
-            q[9 * k] = wq(0) * rk - ds;
+            for (int a = 1; a < kQ; a++) d[a] = dec16<STORE>(obox[(8 * k + a - 1) * PO + owno]);
+            q[9 * k] = wq(0) * rk - sum_offsets(d);
 #pragma unroll
             for (int a = 1; a < kQ; a++) {
                 const int src = k * BY * BX + (cy + 1 - ey(a)) * BX + cx + 2 - ex(a);
-                q[9 * k + a] = wq(a) * rbox[src] + dec16<STORE>(obox[8 * src + a - 1]);
+                const int srco = (8 * k + a - 1) * PO + (cy + 1 - ey(a)) * OX + cx + 6 - ex(a);
+                q[9 * k + a] = wq(a) * rbox[src] + dec16<STORE>(obox[srco]);
             }
         }
     };
@@ -1400,7 +1393,7 @@ void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks,
 size_t step_tma16_smem_bytes()
 {
     const size_t nr = ((size_t)kNF * (kTY + 6) * (kTX + 8) + 31) / 32 * 32;
-    return nr * sizeof(float) + (size_t)kNF * (kTY + 6) * (kTX + 8) * 16u + 128u;
+    return nr * sizeof(float) + (size_t)24 * (kTY + 6) * (kTX + 16) * sizeof(unsigned short) + 128u;
 }
 
 void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
