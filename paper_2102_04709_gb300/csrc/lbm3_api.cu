@@ -465,7 +465,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
             int dev = 0, sms = 0;
             e = cudaGetDevice(&dev);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess && f32) e = step_tma_prepare();
+            if (e == cudaSuccess) e = f32 ? step_tma_prepare() : step_tma16_prepare();
             // SMs left free for the wetting pass and the wall / edge tiles, which run on the side
             // stream while the persistent pure-tile kernel holds its SMs: their share of the step's
             // work, a wall or edge tile counted as two pure tiles (measured on 4096 x 2048 pillars:

@@ -310,6 +310,7 @@ constexpr int kTmaPlanesA = 14;     // planes of a pull box in its first copy (t
 constexpr int kTma16BlocksPerSm = 4;  // the same for the pure tiles of the 16-bit storage (3: 16.2k, 2: 15.7k MLUPS)
 size_t step_tma_smem_bytes();
 cudaError_t step_tma_prepare();
+cudaError_t step_tma16_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
                      const CUtensorMap& tin_a, const CUtensorMap& tin_b, const CUtensorMap& tout, cudaStream_t s);
 // pure tiles of the 16-bit storage through bulk tensor copies (persistent, nblocks blocks): tensor

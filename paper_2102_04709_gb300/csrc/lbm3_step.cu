@@ -1396,6 +1396,18 @@ size_t step_tma16_smem_bytes()
     return nr * sizeof(float) + (size_t)24 * (kTY + 6) * (kTX + 16) * sizeof(unsigned short) + 128u;
 }
 
+// the 16-bit offset box takes the block past the 48 KB of shared memory a kernel gets without
+// opting in
+cudaError_t step_tma16_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_step_tma16<kTX, kTY, kStoreF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)step_tma16_smem_bytes());
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_step_tma16<kTX, kTY, kStoreBF16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)step_tma16_smem_bytes());
+    return e;
+}
+
 void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
                        float* u, const CUtensorMap& trho, const CUtensorMap& toff, cudaStream_t s)
 {
