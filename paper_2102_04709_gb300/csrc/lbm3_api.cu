@@ -46,13 +46,10 @@ struct lbm3 {
     int* tiles_pure = nullptr;
     int* tiles_gen = nullptr;
     int n_pure = 0, n_gen = 0;
-    // tiles_gen lists the inner wall tiles, then the edge tiles with a solid node within 3 nodes
-    // (wrapped), then the edge tiles without one: those read no wall value, so they run on a
-    // third stream alongside the wetting pass
-    int n_walltiles = 0, n_edgewet = 0;
+    int n_walltiles = 0;  // tiles_gen lists the inner wall tiles first, then the edge tiles
     long long pure_fluid = 0;
-    cudaStream_t side = nullptr, side2 = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t bytes = 0;
     int cur = 0;
     bool ready = false;
@@ -129,9 +126,7 @@ void release(lbm3* h)
     h->pop[0] = h->pop[1] = Pop{nullptr, nullptr, nullptr};
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
-    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
     if (h->side) cudaStreamDestroy(h->side);
-    if (h->side2) cudaStreamDestroy(h->side2);
 }
 
 // Tensor maps of one [27][ny][nx] FP32 population buffer: as the two parts of the pull-source box
@@ -194,9 +189,8 @@ bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtens
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// One timestep: fork the side streams off the main stream, run the pure tiles on the main stream
-// while the side stream runs the wetting pass and then the wall tiles and the edge tiles near a
-// solid, and the second side stream the edge tiles away from every solid; join.  With ev != NULL
+// One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
+// while the side stream runs the wetting pass and then the remaining tiles, join.  With ev != NULL
 // the launches are bracketed by the events ev[0..5] (main: 0-1 pure; side: 2-3 wet, 4-5 rest).
 cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 {
@@ -206,13 +200,6 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     float* u = last ? h->u : nullptr;
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    const int n_dry = h->n_gen - h->n_walltiles - h->n_edgewet;
-    if (n_dry > 0) {
-        if ((e = cudaStreamWaitEvent(h->side2, h->ev_fork, 0)) != cudaSuccess) return e;
-        launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles + h->n_edgewet, n_dry, kTilesEdge, fin, fo,
-                    h->type, h->Cw, u, h->side2);
-        if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
-    }
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->tma && h->precision == LBM3_FP32)
         launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
@@ -229,12 +216,11 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if (ev) cudaEventRecord(ev[3], h->side);
     launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
                 h->side);
-    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_edgewet, kTilesEdge, fin, fo, h->type,
-                h->Cw, u, h->side);
+    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge, fin,
+                fo, h->type, h->Cw, u, h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
-    if (n_dry > 0 && (e = cudaStreamWaitEvent(h->stream, h->ev_join2, 0)) != cudaSuccess) return e;
     h->cur = 1 - h->cur;
     return cudaGetLastError();
 }
@@ -350,7 +336,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     }
 
     // ---- tiles of the fused step kernel (2-D prefix sums of the solid mask)
-    std::vector<int> tp, tg, te, td;
+    std::vector<int> tp, tg, te;
     long long pure_fluid = 0;
     {
         std::vector<long long> ps((size_t)(nx + 1) * (ny + 1), 0);
@@ -375,16 +361,12 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                 } else if (inner) {
                     tg.push_back(ty * ntx + tx);
                 } else {
-                    bool dry = true;  // no solid (wrapped, or beyond a wall side) within 3 nodes
-                    for (int y = y0 - 3; y < y0 + kTY + 3 && dry; y++)
-                        for (int x = x0 - 3; x < x0 + kTX + 3 && dry; x++) dry = !S(x, y);
-                    (dry ? td : te).push_back(ty * ntx + tx);
+                    te.push_back(ty * ntx + tx);
                 }
             }
     }
-    const int n_wall_tiles = (int)tg.size(), n_edge_wet = (int)te.size();
+    const int n_wall_tiles = (int)tg.size();
     tg.insert(tg.end(), te.begin(), te.end());
-    tg.insert(tg.end(), td.begin(), td.end());
 
     // ---- parameters
     lbm3* h = new lbm3();
@@ -422,7 +404,6 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     h->n_pure = (int)tp.size();
     h->n_gen = (int)tg.size();
     h->n_walltiles = n_wall_tiles;
-    h->n_edgewet = n_edge_wet;
     h->pure_fluid = pure_fluid;
     h->wall_host = widx;
 
@@ -461,11 +442,9 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
-        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpy(h->type, cls.data(), N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !widx.empty()) e = cudaMemcpy(h->widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !wnrm.empty()) e = cudaMemcpy(h->wnrm, wnrm.data(), wnrm.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -794,8 +773,7 @@ int lbm3_info(const lbm3* h, int64_t out[9])
     // and 8 16-bit offsets (120 B); plus one class byte per node
     const long long per = h->precision == LBM3_FP32 ? 216 : 120;
     out[2] = h->n_fluid * per + h->P.N;
-    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_edgewet > 0) +
-             (h->n_gen > h->n_walltiles + h->n_edgewet);
+    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_gen > h->n_walltiles);
     out[4] = h->nw > 0 ? 1 : 0;
     out[5] = (int64_t)h->bytes;
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes
