@@ -122,3 +122,90 @@ def table1():
             t = line.split()
             rows.append((t[0], tuple(map(float, t[1:4])), tuple(map(float, t[4:7]))))
     return rows
+
+
+# ---- Section III.B: a perfect Janus droplet on a cylinder, Eq.(23) ----
+E5_NX, E5_NY, E5_XC, E5_YC, E5_RS, E5_RJ = 200, 200, 100.0, 60.0, 40.0, 45.0
+E5_SURFACE = E5_RS + 0.5   # halfway bounce-back: the wall lies half a link outside the solid nodes
+
+
+def eq23_distance(rs, rj, theta):
+    """Eq.(23) with its square restored: the distance between the centres of the cylinder
+    (radius rs) and of the droplet's circular arc (radius rj) at contact angle theta (deg)."""
+    return float(np.sqrt(rs * rs + rj * rj - 2.0 * rs * rj * np.cos(np.radians(theta))))
+
+
+def janus_cylinder_e5(theta):
+    """Section III.B: 200 x 200, periodic in x, solid rows at the bottom and top, a cylinder of
+    radius 40 (solid nodes within 40 of (100, 60)); the droplet starts as its analytical
+    equilibrium: a disc of radius 45 whose centre lies eq23_distance(40.5, 45, theta) above the
+    cylinder's, fluid 0 left of x = 100 and fluid 2 right of it, in fluid 1.  Wall triple
+    (theta_rg, theta_br, theta_gb) = (theta, 90, 180 - theta): fluids 0 and 2 wet alike;
+    sigma_01 = sigma_12 = 0.01 and sigma_02 = 1e-4 (the paper's negligible red-blue tension);
+    every viscosity 0.1."""
+    from paper_2102_04709_gb300.workloads import Workload, BC_PERIODIC
+    nx, ny = E5_NX, E5_NY
+    x, y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    solid = ((x - E5_XC) ** 2 + (y - E5_YC) ** 2 <= E5_RS ** 2).astype(np.uint8)
+    solid[0] = 1
+    solid[-1] = 1
+    yd = E5_YC + eq23_distance(E5_SURFACE, E5_RJ, theta)
+    drop = ((x - E5_XC) ** 2 + (y - yd) ** 2 < E5_RJ ** 2) & (solid == 0)
+    lab = np.full((ny, nx), 1)
+    lab[drop & (x < E5_XC)] = 0
+    lab[drop & (x >= E5_XC)] = 2
+    rho = np.zeros((3, ny, nx))
+    for k in range(3):
+        rho[k][(lab == k) & (solid == 0)] = 1.0
+    ang = np.tile(np.array([theta, 90.0, 180.0 - theta]), (ny, nx, 1))
+    return Workload(f"janus_cylinder_e5_{theta:g}", nx, ny, 0, BC_PERIODIC, solid, rho, ang,
+                    (0.01, 1e-4, 0.01), (0.1, 0.1, 0.1), steps=0)
+
+
+def e5_arc(rho, solid, gap=3.0):
+    """Circle fitted to the droplet's outer interface (C_1 = 1/2), points more than gap from
+    the cylinder's wall; returns (radius, distance of its centre from the cylinder's centre,
+    contact angle from the law of cosines of Eq.(23))."""
+    C1 = rho[1] / np.maximum(rho.sum(0), 1e-30)
+    p = contour_points(C1, solid)
+    p = p[np.hypot(p[:, 0] - E5_XC, p[:, 1] - E5_YC) > E5_SURFACE + gap]
+    xc, yc, R = fit_circle(p)
+    D = float(np.hypot(xc - E5_XC, yc - E5_YC))
+    c = (E5_SURFACE ** 2 + R * R - D * D) / (2.0 * E5_SURFACE * R)
+    return R, D, float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
+
+
+# ---- Section III.C: capillary intrusion, Eq.(24)-(26) ----
+def meniscus_angle(rho, solid, k, l, y_wall_lo, y_wall_hi):
+    """Contact angle (deg) inside fluid l of the meniscus between fluid k (left) and fluid l
+    (right) in a channel whose walls lie at y_wall_lo and y_wall_hi: a circle is fitted to the
+    C_k / (C_k + C_l) = 1/2 contour where the third fluid is absent, and the angle between the
+    wall (pointing into fluid l) and the circle's tangent at the wall is averaged over both
+    walls."""
+    rho = np.asarray(rho, dtype=np.float64)
+    C = rho / np.maximum(rho.sum(0), 1e-30)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        phi = np.where(C[k] + C[l] > 0.9, C[k] / (C[k] + C[l]), np.nan)
+    p = contour_points(phi, solid)
+    p = p[(p[:, 1] > y_wall_lo + 1.0) & (p[:, 1] < y_wall_hi - 1.0)]
+    xc, yc, R = fit_circle(p)
+    xm = p[:, 0].mean()
+    out = []
+    for yw, sgn in ((y_wall_lo, 1.0), (y_wall_hi, -1.0)):
+        h = np.sqrt(max(R * R - (yw - yc) ** 2, 0.0))
+        xw = xc + h if abs(xc + h - xm) < abs(xc - h - xm) else xc - h
+        dxdy = -(yw - yc) / (xw - xc)
+        out.append(float(np.degrees(np.arctan2(1.0, sgn * dxdy))))
+    return 0.5 * (out[0] + out[1])
+
+
+def washburn_ternary(t, s0, H, L, Lg, sig_gb, th_gb, sig_gr, th_gr, mu_r, mu_g, mu_b):
+    """Eq.(25)-(26): intrusion length s(t) of the red fluid (angles in degrees)."""
+    A = H * (sig_gb * np.cos(np.radians(th_gb)) - sig_gr * np.cos(np.radians(th_gr))) / 6.0
+    B = mu_g * Lg + mu_b * (L - Lg)
+    C = mu_r - mu_b
+    t = np.asarray(t, dtype=np.float64)
+    if C == 0.0:
+        return A / B * t + s0
+    f = -0.5 * C * s0 * s0 - B * s0 - A * t
+    return (-B + np.sqrt(B * B - 2.0 * C * f)) / C
