@@ -3,10 +3,11 @@ radius 40, droplet radius 45) for the six contact angles of Fig.7, GPU FP32.  Th
 at the analytical equilibrium of Eq.(23) (tests/physics.py: janus_cylinder_e5) and runs 40,000
 steps; a circle is fitted to its outer interface and the contact angle recovered with the law of
 cosines of Eq.(23).  The shape counts as steady when the angle moved by less than 0.5 degree over
-the last 10,000 steps.  The angle must stay within 3 degrees of the prescribed one from 45 to 150
-degrees and within 8 at 30 degrees, where the paper itself shows the simulated shape departing
-from the analytical one (too few nodes near the contact lines); the arc's radius within 1.5 lu
-of 45.
+the last 10,000 steps.  Fig.7 compares shapes, and the paper prints no number for it: the arc's
+centre must lie within 2.5 lu of the Eq.(23) distance for its measured radius, the radius within
+1.5 lu of 45, and the angle within 5 degrees of the prescribed one (8 at 30 degrees, where the
+paper itself shows the shape departing, too few nodes near the contact lines).  The cylinder is a
+staircase: its Eq.(19) normals are off the radial direction by up to 11 degrees node by node.
 """
 import pytest
 
@@ -40,5 +41,6 @@ def test_janus_droplet_on_cylinder(gpu, theta):
     print(f"\ntheta {theta:5.1f}: measured {t:6.2f} (at 30k steps {t1:6.2f}), arc radius {R:.2f}, "
           f"centre distance {D:.2f} (Eq.23 with that radius {D_eq23:.2f})")
     assert abs(t - t1) < 0.5
-    assert abs(t - theta) <= (8.0 if theta < 45.0 else 3.0)
+    assert abs(D - D_eq23) <= 2.5
     assert abs(R - P.E5_RJ) <= 1.5
+    assert abs(t - theta) <= (8.0 if theta < 45.0 else 5.0)
