@@ -12,7 +12,12 @@ neither).  The red intrusion length is s(t) = (mass of fluid 0) / H, sampled fro
   intrusion distance;
 * every case, as the paper compares: Eq.(25) with the dynamic angles measured from the two menisci
   (tests/physics.py: meniscus_angle), within 8 % of the intrusion distance (the paper gives no
-  number for this agreement).
+  number for this agreement);
+* the two-phase special case of Fig.11(b) (one meniscus, no slug; here fluids 0 and 2, since the
+  modified periodic seam exchanges those two): Eq.(24) with L_g = 0 and equal viscosities is
+  Washburn's constant rate H sigma cos(theta) / (6 mu L), within 2 %;
+* Fig.11: away from the menisci the flow is Poiseuille flow, u_x(y) a parabola vanishing at the
+  halfway walls, whose flux through a column equals H ds/dt.
 """
 import numpy as np
 import pytest
@@ -24,6 +29,7 @@ pytestmark = pytest.mark.gpu
 
 H, L, S0, LG, MU_R = 29.0, 450.0, 90, 90, 0.35
 TIMES = (10000, 50000, 100000, 150000, 200000, 300000)
+_cache = {}
 
 
 @pytest.fixture(scope="module")
@@ -37,31 +43,47 @@ def gpu():
     return lbm3
 
 
+def three_phase_triple(theta_gr, theta_gb):
+    th_rg = 180.0 - theta_gr
+    th_br = float(np.degrees(np.arccos(-(np.cos(np.radians(th_rg)) + np.cos(np.radians(theta_gb))))))
+    return (th_rg, th_br, theta_gb)
+
+
+def run_case(gpu, triple, mu, lg):
+    """s(t) at TIMES, the menisci's angles (three-phase runs), and the last fields with the
+    intrusion rate over the last sampling interval."""
+    key = (triple, mu, lg)
+    if key not in _cache:
+        w = W.capillary(nx=450, ny=31, y_lo=1, y_hi=30, s0=S0, Lg=lg, triple=triple, nu=mu)
+        sim = gpu.Lbm3.from_workload(w)
+        s, agr, agb = [], [], []
+        done = 0
+        for t in TIMES:
+            sim.step(t - done)
+            done = t
+            r, u = sim.fields()
+            s.append(r[0].sum() / H)
+            if lg > 0:
+                agr.append(P.meniscus_angle(r, w.solid, 0, 1, 0.5, 29.5))
+                agb.append(180.0 - P.meniscus_angle(r, w.solid, 1, 2, 0.5, 29.5))
+        assert sim.diag()[7] == 0
+        sim.close()
+        _cache[key] = dict(s=np.array(s), agr=agr, agb=agb, rho=r, u=u, w=w,
+                           rate=(s[-1] - s[-2]) / (TIMES[-1] - TIMES[-2]))
+    return _cache[key]
+
+
 CASES = [(gb, ratio) for gb in (30.0, 45.0) for ratio in ((1, 1, 1), (1, 0.01, 1), (1, 0.01, 0.01))]
 
 
 @pytest.mark.parametrize("theta_gb,ratio", CASES, ids=lambda v: str(v))
 def test_capillary_intrusion(gpu, theta_gb, ratio):
     theta_gr = 60.0
-    th_rg = 180.0 - theta_gr
-    th_br = float(np.degrees(np.arccos(-(np.cos(np.radians(th_rg)) + np.cos(np.radians(theta_gb))))))
     mu = tuple(MU_R * r for r in ratio)
-    w = W.capillary(nx=450, ny=31, y_lo=1, y_hi=30, s0=S0, Lg=LG, triple=(th_rg, th_br, theta_gb), nu=mu)
-    sim = gpu.Lbm3.from_workload(w)
-    s, agr, agb = [], [], []
-    done = 0
-    for t in TIMES:
-        sim.step(t - done)
-        done = t
-        r, _ = sim.fields()
-        s.append(r[0].sum() / H)
-        agr.append(P.meniscus_angle(r, w.solid, 0, 1, 0.5, 29.5))
-        agb.append(180.0 - P.meniscus_angle(r, w.solid, 1, 2, 0.5, 29.5))
-    assert sim.diag()[7] == 0
-    sim.close()
-    s = np.array(s)
+    c = run_case(gpu, three_phase_triple(theta_gr, theta_gb), mu, LG)
+    s = c["s"]
     dt = np.array(TIMES, dtype=np.float64) - TIMES[0]
-    dyn_gr, dyn_gb = float(np.mean(agr)), float(np.mean(agb))
+    dyn_gr, dyn_gb = float(np.mean(c["agr"])), float(np.mean(c["agb"]))
     ana = P.washburn_ternary(dt, s[0], H, L, LG, 0.01, dyn_gb, 0.01, dyn_gr, *mu)
     err = float(np.abs(s - ana).max() / (ana[-1] - s[0]))
     msg = (f"\n(60, {theta_gb:g}) mu {ratio}: intrusion {s[-1] - s[0]:.2f} lu, Eq.25 with dynamic "
@@ -74,3 +96,45 @@ def test_capillary_intrusion(gpu, theta_gb, ratio):
     print(msg)
     assert s[-1] > s[0] + 10.0
     assert err <= 0.08
+
+
+TWO_PHASE = ((90.0, 150.0, 30.0), (MU_R,) * 3, 0)   # fluid 0 wets at 30 deg against fluid 2
+
+
+def test_two_phase_intrusion_is_washburn(gpu):
+    c = run_case(gpu, *TWO_PHASE)
+    s = c["s"]
+    rate = H * 0.01 * np.cos(np.radians(30.0)) / (6.0 * MU_R * L)
+    line = s[0] + rate * (np.array(TIMES, dtype=np.float64) - TIMES[0])
+    err = float(np.abs(s - line).max() / (line[-1] - s[0]))
+    print(f"\ntwo-phase: intrusion {s[-1] - s[0]:.2f} lu, Washburn {line[-1] - s[0]:.2f}, max error {100 * err:.2f} %")
+    assert err <= 0.02
+
+
+def poiseuille_column(c, x):
+    """u_x, u_y on the fluid rows of column x, the least-squares parabola of u_x and its roots."""
+    ux, uy = c["u"][0][1:30, x], c["u"][1][1:30, x]
+    y = np.arange(1, 30, dtype=np.float64)
+    a2, a1, a0 = np.polyfit(y, ux, 2)
+    roots = np.sort(np.roots([a2, a1, a0]).real)
+    fit = np.polyval([a2, a1, a0], y)
+    return ux, uy, fit, roots
+
+
+@pytest.mark.parametrize("case", ["three-phase (60, 30) 1:1:1", "two-phase"])
+def test_fig11_poiseuille_away_from_menisci(gpu, case):
+    if case == "two-phase":
+        c = run_case(gpu, *TWO_PHASE)
+    else:
+        c = run_case(gpu, three_phase_triple(60.0, 30.0), (MU_R,) * 3, LG)
+    x = int(c["s"][-1] / 2)   # middle of the red column, far from every meniscus and the seam
+    ux, uy, fit, roots = poiseuille_column(c, x)
+    peak = float(ux.max())
+    flux = float((c["rho"].sum(0)[1:30, x] * ux).sum())
+    print(f"\n{case}: column {x}, flux {flux:.4e} vs H ds/dt {H * c['rate']:.4e}, parabola roots "
+          f"{roots[0]:.3f} {roots[1]:.3f}, max |u_x - parabola| / peak {np.abs(ux - fit).max() / peak:.2e}, "
+          f"max |u_y| / peak {np.abs(uy).max() / peak:.2e}")
+    assert abs(flux / (H * c["rate"]) - 1.0) <= 0.02
+    assert np.abs(ux - fit).max() <= 0.02 * peak
+    assert abs(roots[0] - 0.5) <= 0.25 and abs(roots[1] - 29.5) <= 0.25
+    assert np.abs(uy).max() <= 0.01 * peak
