@@ -223,6 +223,34 @@ def pillars(nx=4096, ny=2048, count=60, r_lo=40.0, r_hi=80.0, x_lo=900.0, x_hi=3
                     rho_out=1.0, steps=steps)
 
 
+def five_pillars(triple=(90.0, 90.0, 90.0), r_outer=50.0, sigma=0.01, name=None):
+    """Section III.D as printed, in units of the outer droplet radius R_o: a 16 R_o x 7.5 R_o box
+    (800 x 375 for R_o = 50), five pillars of radius 0.8 R_o centred at (6.9, 3.75), (7.3, 6.2),
+    (7.5, 1.6), (9.5, 5.14) and (9.8, 2.54) R_o, a compound droplet at (2, 3.75) R_o: core of
+    radius 0.6 R_o in fluid 0 (red), shell of radius R_o in fluid 1 (green), carrier fluid 2
+    (blue).  Zou-He velocity inlet / pressure outlet, periodic in y.  Every tension is sigma and
+    the viscosities are equal; Re = U R_o / nu = 0.75 and Ca = U nu / sigma = 0.04 then give
+    nu = sqrt(0.04 sigma R_o / 0.75) and U = 0.75 nu / R_o.  ``triple`` = (theta_rg, theta_br,
+    theta_gb) at every wall node; ``steps`` covers t* = U t / R_o = 40."""
+    R = float(r_outer)
+    nx, ny = int(round(16 * R)), int(round(7.5 * R))
+    nu = math.sqrt(0.04 * sigma * R / 0.75)
+    u_in = 0.75 * nu / R
+    x, y = _grid(nx, ny)
+    solid = np.zeros((ny, nx), np.uint8)
+    for cx, cy in ((6.9, 3.75), (7.3, 6.2), (7.5, 1.6), (9.5, 5.14), (9.8, 2.54)):
+        dy = np.abs(y - cy * R)
+        dy = np.minimum(dy, ny - dy)
+        solid[(x - cx * R) ** 2 + dy ** 2 <= (0.8 * R) ** 2] = 1
+    d2 = (x - 2.0 * R) ** 2 + (y - 3.75 * R) ** 2
+    labels = np.full((ny, nx), 2, np.int64)
+    labels[d2 < R * R] = 1
+    labels[d2 < (0.6 * R) ** 2] = 0
+    return Workload(name or f"five_pillars_{nx}x{ny}", nx, ny, 1, BC_ZOUHE, solid,
+                    _fill(labels, solid), _uniform_angles(nx, ny, tuple(triple)), (sigma,) * 3,
+                    (nu,) * 3, u_in=u_in, rho_out=1.0, steps=int(round(40.0 * R / u_in)))
+
+
 # ---- the five standard configurations ---------------------------------------------------
 def config1():
     """Janus droplet on a flat wall, 128x64, R = 20, angles 90/60/120, 1000 steps."""
