@@ -42,9 +42,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--theta", type=float, default=90.0)
-    ap.add_argument("--workload", choices=["pillars_4096x2048", "pillars_2048x1024"],
+    ap.add_argument("--workload", choices=["pillars_4096x2048", "pillars_2048x1024", "five_pillars_800x375"],
                     default="pillars_4096x2048",
-                    help="the half-size case exists for detailed kernel profiles")
+                    help="the half-size case exists for detailed kernel profiles; five_pillars_800x375 "
+                         "is the paper's own Section III.D set-up (wall triple (90, 180 - theta, theta))")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--precision", choices=["fp32", "fp16", "bf16"], default="fp32",
@@ -256,7 +257,12 @@ def run_ours(args):
     build.build()
     lbm3.load()
 
-    w = W.config4(args.theta) if args.workload == "pillars_4096x2048" else W.pillars_half(args.theta)
+    if args.workload == "pillars_4096x2048":
+        w = W.config4(args.theta)
+    elif args.workload == "pillars_2048x1024":
+        w = W.pillars_half(args.theta)
+    else:
+        w = W.five_pillars((90.0, 180.0 - args.theta, args.theta))
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     prec = PRECISIONS[args.precision]
