@@ -91,7 +91,11 @@ int lbm3_set_fields(lbm3* h, const double* rho);
  * that the other tiles' share of the work leaves); the other tiles follow the wetting pass on an
  * internal higher-priority stream that is joined back before the call's work completes.  The
  * velocity of the last collision of the call is recorded for lbm3_fields / lbm3_diag.  A bulk
- * copy that does not complete within its wait limit is reported by the next lbm3_diag. */
+ * copy that does not complete within its wait limit is reported by the next lbm3_diag.  While more
+ * than 8 steps remain, blocks of 8 steps are launched as one CUDA graph, captured on an internal
+ * stream the first time it is needed (one graph per starting population buffer) and replayed on
+ * the handle's stream: the same kernels in the same order, so the results do not depend on how
+ * steps are split between calls.  If a capture fails the steps are launched one by one. */
 int lbm3_step(lbm3* h, int32_t nsteps);
 
 /* lbm3_step with per-launch timing: CUDA events are recorded around every launch on the stream

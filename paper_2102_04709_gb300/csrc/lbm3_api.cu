@@ -50,6 +50,14 @@ struct lbm3 {
     long long pure_fluid = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // CUDA graphs of kGraphSteps consecutive steps (an even count: a graph starts and ends on the
+    // same population buffer), one per starting buffer, captured on the internal stream gcap
+    // when lbm3_step first needs them and replayed on the caller's stream; dropped when a
+    // captured launch argument changes (lbm3_set_inflow).  graph_off: a capture failed, so steps
+    // are launched one by one (the same kernels, the same results).
+    cudaStream_t gcap = nullptr;
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    bool graph_off = false;
     size_t bytes = 0;
     int cur = 0;
     bool ready = false;
@@ -124,6 +132,9 @@ void release(lbm3* h)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->pop[0] = h->pop[1] = Pop{nullptr, nullptr, nullptr};
+    for (int c = 0; c < 2; c++)
+        if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
+    if (h->gcap) cudaStreamDestroy(h->gcap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
     if (h->side) cudaStreamDestroy(h->side);
@@ -223,6 +234,54 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
     h->cur = 1 - h->cur;
     return cudaGetLastError();
+}
+
+constexpr int kGraphSteps = 8;
+
+void drop_graphs(lbm3* h)
+{
+    for (int c = 0; c < 2; c++) {
+        if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
+        h->gexec[c] = nullptr;
+    }
+}
+
+// kGraphSteps steps from the current buffer, none of them the last of an lbm3_step call (no
+// velocity output): replay of the captured graph, captured first if needed.  Capturing only
+// records the launches (nothing runs), on the internal stream, so the caller's stream may be any
+// stream, the legacy default one included.
+cudaError_t graph_block(lbm3* h)
+{
+    const int c = h->cur;
+    if (!h->gexec[c] && !h->graph_off) {
+        cudaStream_t user = h->stream;
+        h->stream = h->gcap;
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(h->gcap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaError_t el = cudaSuccess;
+            for (int s = 0; s < kGraphSteps && el == cudaSuccess; s++) el = enqueue_step(h, false, nullptr);
+            e = cudaStreamEndCapture(h->gcap, &g);
+            if (el != cudaSuccess) e = el;
+        }
+        h->stream = user;
+        h->cur = c;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[c], g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            h->gexec[c] = nullptr;
+            h->graph_off = true;
+            cudaGetLastError();  // a failed capture leaves no sticky error; clear the last one
+        }
+    }
+    if (!h->gexec[c]) {
+        for (int s = 0; s < kGraphSteps; s++) {
+            const cudaError_t e = enqueue_step(h, false, nullptr);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    return cudaGraphLaunch(h->gexec[c], h->stream);  // ends on buffer c again
 }
 
 }  // namespace
@@ -442,6 +501,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gcap, cudaStreamNonBlocking);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
@@ -515,7 +575,11 @@ int lbm3_step(lbm3* h, int32_t nsteps)
     if (!h) return fail(h, LBM3_ERR_INVALID, "NULL handle");
     if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
-    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, nullptr));
+    // blocks of kGraphSteps steps through the graphs while at least one step remains after them;
+    // the rest, and the last step (it writes the velocity), one by one
+    int s = 0;
+    for (; s + kGraphSteps < nsteps; s += kGraphSteps) CUDA_TRY(h, graph_block(h));
+    for (; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, nullptr));
     return LBM3_OK;
 }
 
@@ -667,6 +731,7 @@ int lbm3_set_inflow(lbm3* h, double u_in)
     if (h->P.bc_x != kZouHe) return fail(h, LBM3_ERR_INVALID, "no Zou-He inlet");
     if (!(std::fabs(u_in) < 0.3)) return fail(h, LBM3_ERR_INVALID, "|u_in| must be < 0.3");
     h->P.u_in = (float)u_in;
+    drop_graphs(h);  // the graphs hold the old Params
     return LBM3_OK;
 }
 
