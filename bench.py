@@ -308,6 +308,20 @@ def run_ours(args):
                "h2d_bytes_per_step": int(math.ceil(rho_host.nbytes / args.steps)),
                "d2h_bytes_per_step": int(math.ceil((rho_out.nbytes + u_out.nbytes) / args.steps))}
 
+    # the same steps through lbm3_step itself, which replays captured CUDA graphs of 8 steps and
+    # records no per-launch events (the timed region above records five events per step so that
+    # the roofline can use each kernel's own duration)
+    g0 = torch.cuda.Event(enable_timing=True)
+    g1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    g0.record(stream)
+    sim.step(args.steps)
+    g1.record(stream)
+    barrier()
+    gms = max_over_ranks(g0.elapsed_time(g1), ws, "cuda")
+    graphs = {"value": job_mlups(w.n, args.steps, ws, gms), "unit": "MLUPS",
+              "ms_per_step": gms / args.steps, "steps": args.steps}
+
     # the same workload with the other population storages (shorter timed region each)
     alt = {}
     if not args.no_alt_storage:
@@ -374,7 +388,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "fluid_nodes": info["n_fluid"],
                    "wall_nodes": info["n_wall"], "storage": args.precision,
-                   "alt_storage": alt, "adjoint": adj,
+                   "alt_storage": alt, "adjoint": adj, "lbm3_step_graphs": graphs,
                    "mflups": info["n_fluid"] * args.steps * ws / (ms * 1e-3) / 1e6,
                    "l2": "populations 2 x 0.91 GB > 129 MB L2: no flush between steps",
                    "replicas": ws, "ms_wet_per_step": ms_wet / args.steps,
