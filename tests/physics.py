@@ -135,43 +135,45 @@ def eq23_distance(rs, rj, theta):
     return float(np.sqrt(rs * rs + rj * rj - 2.0 * rs * rj * np.cos(np.radians(theta))))
 
 
-def janus_cylinder_e5(theta):
+def janus_cylinder_e5(theta, scale=1.0):
     """Section III.B: 200 x 200, periodic in x, solid rows at the bottom and top, a cylinder of
     radius 40 (solid nodes within 40 of (100, 60)); the droplet starts as its analytical
     equilibrium: a disc of radius 45 whose centre lies eq23_distance(40.5, 45, theta) above the
     cylinder's, fluid 0 left of x = 100 and fluid 2 right of it, in fluid 1.  Wall triple
     (theta_rg, theta_br, theta_gb) = (theta, 90, 180 - theta): fluids 0 and 2 wet alike;
     sigma_01 = sigma_12 = 0.01 and sigma_02 = 1e-4 (the paper's negligible red-blue tension);
-    every viscosity 0.1."""
+    every viscosity 0.1.  ``scale`` multiplies every length (the box, centres and radii)."""
     from paper_2102_04709_gb300.workloads import Workload, BC_PERIODIC
-    nx, ny = E5_NX, E5_NY
+    nx = ny = int(round(E5_NX * scale))
+    xc, yc, rs, rj = E5_XC * scale, E5_YC * scale, E5_RS * scale, E5_RJ * scale
     x, y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
-    solid = ((x - E5_XC) ** 2 + (y - E5_YC) ** 2 <= E5_RS ** 2).astype(np.uint8)
+    solid = ((x - xc) ** 2 + (y - yc) ** 2 <= rs ** 2).astype(np.uint8)
     solid[0] = 1
     solid[-1] = 1
-    yd = E5_YC + eq23_distance(E5_SURFACE, E5_RJ, theta)
-    drop = ((x - E5_XC) ** 2 + (y - yd) ** 2 < E5_RJ ** 2) & (solid == 0)
+    yd = yc + eq23_distance(rs + 0.5, rj, theta)
+    drop = ((x - xc) ** 2 + (y - yd) ** 2 < rj ** 2) & (solid == 0)
     lab = np.full((ny, nx), 1)
-    lab[drop & (x < E5_XC)] = 0
-    lab[drop & (x >= E5_XC)] = 2
+    lab[drop & (x < xc)] = 0
+    lab[drop & (x >= xc)] = 2
     rho = np.zeros((3, ny, nx))
     for k in range(3):
         rho[k][(lab == k) & (solid == 0)] = 1.0
     ang = np.tile(np.array([theta, 90.0, 180.0 - theta]), (ny, nx, 1))
-    return Workload(f"janus_cylinder_e5_{theta:g}", nx, ny, 0, BC_PERIODIC, solid, rho, ang,
+    return Workload(f"janus_cylinder_e5_{theta:g}_{nx}", nx, ny, 0, BC_PERIODIC, solid, rho, ang,
                     (0.01, 1e-4, 0.01), (0.1, 0.1, 0.1), steps=0)
 
 
-def e5_arc(rho, solid, gap=3.0):
+def e5_arc(rho, solid, gap=3.0, scale=1.0):
     """Circle fitted to the droplet's outer interface (C_1 = 1/2), points more than gap from
-    the cylinder's wall; returns (radius, distance of its centre from the cylinder's centre,
-    contact angle from the law of cosines of Eq.(23))."""
+    the cylinder's wall (radius 40 scale + 1/2); returns (radius, distance of its centre from
+    the cylinder's centre, contact angle from the law of cosines of Eq.(23))."""
+    xc0, yc0, surf = E5_XC * scale, E5_YC * scale, E5_RS * scale + 0.5
     C1 = rho[1] / np.maximum(rho.sum(0), 1e-30)
     p = contour_points(C1, solid)
-    p = p[np.hypot(p[:, 0] - E5_XC, p[:, 1] - E5_YC) > E5_SURFACE + gap]
+    p = p[np.hypot(p[:, 0] - xc0, p[:, 1] - yc0) > surf + gap]
     xc, yc, R = fit_circle(p)
-    D = float(np.hypot(xc - E5_XC, yc - E5_YC))
-    c = (E5_SURFACE ** 2 + R * R - D * D) / (2.0 * E5_SURFACE * R)
+    D = float(np.hypot(xc - xc0, yc - yc0))
+    c = (surf ** 2 + R * R - D * D) / (2.0 * surf * R)
     return R, D, float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0))))
 
 
