@@ -5,19 +5,21 @@ import numpy as np
 
 def contour_points(C, solid, level=0.5):
     """Points where the field C crosses `level` along grid rows and columns (linear
-    interpolation between two fluid nodes)."""
+    interpolation between two fluid nodes).  A crossing is a sign change of C - level counted
+    half-open (a >= 0 > b or a < 0 <= b), so a node exactly at the level gives one point;
+    non-finite values (masked regions) never cross."""
     C = np.asarray(C)
     s = np.asarray(solid).astype(bool)
     pts = []
     a = C[:, :-1] - level
     b = C[:, 1:] - level
-    ok = (a * b < 0) & ~s[:, :-1] & ~s[:, 1:]
+    ok = ((a >= 0) != (b >= 0)) & np.isfinite(a) & np.isfinite(b) & ~s[:, :-1] & ~s[:, 1:]
     ys, xs = np.nonzero(ok)
     for y, x in zip(ys, xs):
         pts.append((x + a[y, x] / (a[y, x] - b[y, x]), y))
     a = C[:-1, :] - level
     b = C[1:, :] - level
-    ok = (a * b < 0) & ~s[:-1, :] & ~s[1:, :]
+    ok = ((a >= 0) != (b >= 0)) & np.isfinite(a) & np.isfinite(b) & ~s[:-1, :] & ~s[1:, :]
     ys, xs = np.nonzero(ok)
     for y, x in zip(ys, xs):
         pts.append((x, y + a[y, x] / (a[y, x] - b[y, x])))
@@ -25,7 +27,9 @@ def contour_points(C, solid, level=0.5):
 
 
 def fit_circle(p):
-    """Least-squares circle (xc, yc, R) through points p[:, 2]."""
+    """Least-squares circle (xc, yc, R) through points p[:, 2] (at least three)."""
+    if len(p) < 3:
+        raise ValueError(f"a circle needs at least 3 points, got {len(p)}")
     A = np.c_[2 * p[:, 0], 2 * p[:, 1], np.ones(len(p))]
     b = (p ** 2).sum(1)
     c = np.linalg.lstsq(A, b, rcond=None)[0]
@@ -190,6 +194,12 @@ def meniscus_angle(rho, solid, k, l, y_wall_lo, y_wall_hi):
         phi = np.where(C[k] + C[l] > 0.9, C[k] / (C[k] + C[l]), np.nan)
     p = contour_points(phi, solid)
     p = p[(p[:, 1] > y_wall_lo + 1.0) & (p[:, 1] < y_wall_hi - 1.0)]
+    sv = np.linalg.svd(p - p.mean(0), compute_uv=False)
+    if sv[-1] <= 1e-9 * sv[0]:
+        # a straight meniscus (collinear points): x = a + b y, slope b at both walls, the
+        # tangent into the fluid mirrored at the upper wall as below
+        b = np.polyfit(p[:, 1], p[:, 0], 1)[0]
+        return 0.5 * (float(np.degrees(np.arctan2(1.0, b))) + float(np.degrees(np.arctan2(1.0, -b))))
     xc, yc, R = fit_circle(p)
     xm = p[:, 0].mean()
     out = []
