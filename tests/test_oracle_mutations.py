@@ -1,0 +1,80 @@
+"""Planted mistakes: each case copies the oracle to a temporary directory, changes one line the
+way a plausible slip would (a dropped term, a wrong sign, a wrong index or weight), builds the
+copy and runs one of the pins of test_oracle_pins.py on it, which must fail.  The oracle itself is
+never modified; this shows that the pins, not only the parity with the CUDA path, would catch
+such a mistake in the oracle."""
+import importlib.util
+import os
+import shutil
+
+import pytest
+
+from tests import test_oracle_pins as PINS
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ORACLE = os.path.join(os.path.dirname(HERE), "oracle")
+
+# (what the slip is, text in lbm3_oracle.c, replacement, pin, pin arguments after the module)
+MUTATIONS = [
+    ("a diagonal weight 1/18 instead of 1/36",
+     "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};",
+     "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 18.0};",
+     "test_lattice_isotropy", ()),
+    ("the forcing term of Eq.9 with the wrong sign",
+     "Ft[a] = WQ[a] * (cx * Fs[0] + cy * Fs[1]);",
+     "Ft[a] = -WQ[a] * (cx * Fs[0] + cy * Fs[1]);",
+     "test_collision_conserves_mass_and_adds_force", ()),
+    ("the 1/2 of the relaxation time dropped",
+     "return mu / (rho * CS2) + 0.5;",
+     "return mu / (rho * CS2) + 1.0;",
+     "test_shear_wave_decay", ()),
+    ("the Eq.12 stencil without its 1/c_s^2",
+     "g[k][0] += WQ[a] * cv[k] * EX[a] / CS2;\n            g[k][1] += WQ[a] * cv[k] * EY[a] / CS2;",
+     "g[k][0] += WQ[a] * cv[k] * EX[a];\n            g[k][1] += WQ[a] * cv[k] * EY[a];",
+     "test_laplace_law", ()),
+    ("I + nn instead of I - nn in the Eq.10 stress",
+     "T[0] += s * (1.0 - nx * nx);",
+     "T[0] += s * (1.0 + nx * nx);",
+     "test_laplace_law", ()),
+    ("the recolouring term of Eq.13 with the wrong sign",
+     "v += beta * WQ[a] * rk[k] * rk[l] / rho * ne;",
+     "v -= beta * WQ[a] * rk[k] * rk[l] / rho * ne;",
+     "test_flat_interface_segregation_balance", ()),
+    ("the Zou-He inlet population with the wrong sign of U",
+     "double g1 = f[3] + 2.0 / 3.0 * rho * U;",
+     "double g1 = f[3] - 2.0 / 3.0 * rho * U;",
+     "test_zou_he_uniform_inflow", ()),
+    ("no fluid swap across the modified periodic seam",
+     "int kk = sw ? swapk(k) : k;",
+     "int kk = k;",
+     "test_mass_modified_periodic", ()),
+    ("Eq.22's max and min exchanged",
+     "return theta_k <= 90.0 ? fmax(c1, c2) : fmin(c1, c2);",
+     "return theta_k <= 90.0 ? fmin(c1, c2) : fmax(c1, c2);",
+     "test_contact_angle_flat_wall", (45.0,)),
+    ("Eq.21 weighted by the wrong fluid",
+     "th[0] = t_rg + Cb / (Cb + Cg) * (t_rb - t_rg);",
+     "th[0] = t_rg + Cg / (Cb + Cg) * (t_rb - t_rg);",
+     "test_weighted_contact_angle", ()),
+]
+
+
+def mutant(tmp_path, old, new):
+    d = tmp_path / "oracle"
+    d.mkdir()
+    src = open(os.path.join(ORACLE, "lbm3_oracle.c")).read()
+    assert src.count(old) == 1, "the planted text must occur exactly once"
+    (d / "lbm3_oracle.c").write_text(src.replace(old, new))
+    shutil.copy(os.path.join(ORACLE, "oracle.py"), d / "oracle.py")
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{tmp_path.name}", d / "oracle.py")
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    mod.build()
+    return mod
+
+
+@pytest.mark.parametrize("what,old,new,pin,args", MUTATIONS, ids=[m[0] for m in MUTATIONS])
+def test_pin_catches_planted_mistake(tmp_path, what, old, new, pin, args):
+    mod = mutant(tmp_path, old, new)
+    with pytest.raises(AssertionError):
+        getattr(PINS, pin)(mod, *args)
