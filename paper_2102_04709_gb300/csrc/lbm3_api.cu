@@ -20,7 +20,7 @@ struct lbm3 {
     int precision = 0;
     cudaStream_t stream = nullptr;
     // device buffers: two population buffers (FP32 planes, or FP32 densities + 16-bit offset
-    // records), the node classes, wall values, velocity, scratch
+    // planes), the node classes, wall values, velocity, scratch
     Pop pop[2] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
     uint8_t* type = nullptr;
     double* Cw = nullptr;          // [3][N] wall values (written at C_SB nodes only)
@@ -31,7 +31,7 @@ struct lbm3 {
     int* err_flag = nullptr;       // error bits set by kernels (Params::err)
     // bulk-tensor-copy path of the pure tiles (nx a multiple of 4): tensor maps of each
     // population buffer, FP32 storage: the two parts of the source box and the destination tile;
-    // 16-bit storage: the density box (tm_in_a) and the offset-record box (tm_in_b)
+    // 16-bit storage: the density box (tm_in_a) and the offset-plane box (tm_in_b)
     bool tma = false;
     int tma_blocks = 0;  // persistent blocks of that kernel: kTmaBlocksPerSm per SM
     CUtensorMap tm_in_a[2], tm_in_b[2], tm_out[2];

@@ -57,8 +57,8 @@ struct Params {
     // (k * 9 + a) * N - e_ax - e_ay * nx, for the step kernel's interior tiles
     int off_plane[27];
     int off_pull[27];
-    // reduced storage: element offsets k * N - e_ax - e_ay * nx of the pull sources in the rho and
-    // offset-record planes
+    // reduced storage: element offsets k * N - e_ax - e_ay * nx of the pull sources in the rho
+    // planes
     int off_pull16[27];
     // reduced storage: element offsets (8 k + a - 1) * N - e_ax - e_ay * nx of the pull sources in
     // the 16-bit offset planes (a >= 1; entry a = 0 unused)
@@ -314,8 +314,8 @@ cudaError_t step_tma16_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
                      const CUtensorMap& tin_a, const CUtensorMap& tin_b, const CUtensorMap& tout, cudaStream_t s);
 // pure tiles of the 16-bit storage through bulk tensor copies (persistent, nblocks blocks): tensor
-// maps of the densities (box (kTX + 8, kTY + 6, 3) of [3][ny][nx] FP32) and of the offset records
-// (box (8, kTX + 8, kTY + 6, 3) of [3][ny][nx][8] 16-bit words)
+// maps of the densities (box (kTX + 8, kTY + 6, 3) of [3][ny][nx] FP32) and of the offset planes
+// (box (kTX + 16, kTY + 6, 24) of [24][ny][nx] 16-bit words)
 size_t step_tma16_smem_bytes();
 void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
                        float* u, const CUtensorMap& trho, const CUtensorMap& toff, cudaStream_t s);
