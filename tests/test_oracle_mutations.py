@@ -28,6 +28,10 @@ MUTATIONS = [
      "return mu / (rho * CS2) + 0.5;",
      "return mu / (rho * CS2) + 1.0;",
      "test_shear_wave_decay", ()),
+    ("an arithmetic instead of a harmonic mixture viscosity in Eq.7",
+     "for (int k = 0; k < NF; k++) inv += rk[k] / (o->rho0[k] * o->nu[k]);\n    double mu = rho / inv;",
+     "for (int k = 0; k < NF; k++) inv += rk[k] * (o->rho0[k] * o->nu[k]);\n    double mu = inv / rho;",
+     "test_mixture_viscosity_is_harmonic", ()),
     ("the Eq.12 stencil without its 1/c_s^2",
      "g[k][0] += WQ[a] * cv[k] * EX[a] / CS2;\n            g[k][1] += WQ[a] * cv[k] * EY[a] / CS2;",
      "g[k][0] += WQ[a] * cv[k] * EX[a];\n            g[k][1] += WQ[a] * cv[k] * EY[a];",

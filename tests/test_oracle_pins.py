@@ -112,6 +112,38 @@ def test_shear_wave_decay(oracle_mod):
         assert np.abs(u[1]).max() < 1e-12
 
 
+def test_mixture_viscosity_is_harmonic(oracle_mod):
+    """A shear wave in a uniform mixture (rho_0 = rho_1 = 1/2 everywhere: no colour gradient, so
+    no interfacial force and no recolouring change) decays at the mixture viscosity of Eq.(7),
+    1 / sum(C_k / nu_k): 0.15 for nu = (0.1, 0.3), where an arithmetic mean would give 0.2."""
+    ex, ey, w, M, Mi = oracle_mod.lattice()
+    L, U = 32, 1e-3
+    y = np.arange(L)[:, None] * np.ones((1, L))
+    k = 2 * np.pi / L
+    kw = _single_fluid(L, L, 0.2)
+    kw["nu"] = (0.1, 0.3, 0.2)
+    o = oracle_mod.Oracle(**kw)
+    half = np.full((L, L), 0.5)
+    o.set_fields(np.stack([half, half, np.zeros((L, L))]))
+    ux = U * np.sin(k * y)
+    f = np.zeros((3, 9, L, L))
+    for a in range(9):
+        eu = ex[a] * ux
+        feq = w[a] * (1 + 3 * eu + 4.5 * eu * eu - 1.5 * ux * ux)
+        f[0, a] = 0.5 * feq
+        f[1, a] = 0.5 * feq
+    o.set_f(f)
+    amps = []
+    for _ in range(2):
+        o.step(150)
+        r, u = o.fields()
+        amps.append((u[0] * np.sin(k * y)).sum() / (np.sin(k * y) ** 2).sum())
+    rate = -math.log(amps[1] / amps[0]) / 150.0
+    nu_mix = 1.0 / (0.5 / 0.1 + 0.5 / 0.3)
+    assert abs(rate / (nu_mix * k * k) - 1.0) < 0.02, rate / (nu_mix * k * k)
+    assert np.abs(r[0] / r.sum(0) - 0.5).max() < 1e-12     # the mixture stays uniform
+
+
 def test_uniform_fluid_at_rest_stays_at_rest(oracle_mod):
     """No spurious force or flow from walls, a curved solid and the wetting step when a
     single fluid fills the domain."""
