@@ -40,6 +40,14 @@ MUTATIONS = [
      "T[0] += s * (1.0 - nx * nx);",
      "T[0] += s * (1.0 + nx * nx);",
      "test_laplace_law", ()),
+    ("A_kl of Eq.10 without its factor 1e6",
+     "double A = fmin(1e6 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);",
+     "double A = fmin(1.0 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);",
+     "test_laplace_law", ()),
+    ("halfway bounce-back that does not reverse the population",
+     "o->fnew[((size_t)k * Q + o->opp[a]) * n + i] = v;",
+     "o->fnew[((size_t)k * Q + a) * n + i] = v;",
+     "test_uniform_fluid_at_rest_stays_at_rest", ()),
     ("the recolouring term of Eq.13 with the wrong sign",
      "v += beta * WQ[a] * rk[k] * rk[l] / rho * ne;",
      "v -= beta * WQ[a] * rk[k] * rk[l] / rho * ne;",
