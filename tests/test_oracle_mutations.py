@@ -60,6 +60,26 @@ MUTATIONS = [
      "int kk = sw ? swapk(k) : k;",
      "int kk = k;",
      "test_mass_modified_periodic", ()),
+    ("a row of the transformation matrix M of Eq.4 with one wrong sign",
+     "{0, 1, 0, -1, 0, 1, -1, -1, 1},",
+     "{0, 1, 0, -1, 0, 1, 1, -1, 1},",
+     "test_transform_matrix", ()),
+    ("the Eq.19 normal left pointing into the solid",
+     "            o->ns[2 * (size_t)i] = -sx / nrm;\n            o->ns[2 * (size_t)i + 1] = -sy / nrm;",
+     "            o->ns[2 * (size_t)i] = sx / nrm;\n            o->ns[2 * (size_t)i + 1] = sy / nrm;",
+     "test_normals_flat_and_curved", ()),
+    ("the Eq.20 weights of the first two shells exchanged",
+     "        case 1: return 4.0 / 21.0;\n        case 2: return 4.0 / 45.0;",
+     "        case 1: return 4.0 / 45.0;\n        case 2: return 4.0 / 21.0;",
+     "test_normals_flat_and_curved", ()),
+    ("interpolation along a horizontal grid line from the wrong end",
+     "*CD = Clef + fr * (Crig - Clef);",
+     "*CD = Crig + fr * (Clef - Crig);",
+     "test_rays_flat_wall_hand_worked", ()),
+    ("interpolation along a vertical grid line from the wrong end",
+     "*CD = Clow + fr * (Cup - Clow);",
+     "*CD = Cup + fr * (Clow - Cup);",
+     "test_rays_vertical_wall_hand_worked", ()),
     ("Eq.22's max and min exchanged",
      "return theta_k <= 90.0 ? fmax(c1, c2) : fmin(c1, c2);",
      "return theta_k <= 90.0 ? fmin(c1, c2) : fmax(c1, c2);",

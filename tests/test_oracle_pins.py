@@ -318,6 +318,38 @@ def test_rays_flat_wall_hand_worked(oracle_mod):
     assert cp == pytest.approx(C[1, ny - 2, x0], abs=1e-15)
 
 
+def test_rays_vertical_wall_hand_worked(oracle_mod):
+    """The flat-wall cases turned by 90 degrees: solid columns at x = 0 and x = nx - 1 (walls
+    in x, periodic in y) and C linear in y, so the characteristic lines cross vertical grid
+    lines and the value is interpolated between a lower and an upper node."""
+    nx, ny = 12, 24
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[:, 0] = 1
+    solid[:, -1] = 1
+    o = oracle_mod.Oracle(**_single_fluid(nx, ny, 0.1, solid=solid, per_y=1, bc_x=3))
+    y = np.meshgrid(np.arange(nx), np.arange(ny))[1]
+    a, b = 0.2, 0.025
+    C = np.zeros((3, ny, nx))
+    C[0] = a + b * y
+    C[1] = 0.5 - 0.01 * y
+    C[2] = 1 - C[0] - C[1]
+    y0 = 10
+    p = y0 * nx          # left C_SB node, outward normal (1, 0)
+    lin = lambda yy: a + b * yy
+    # theta = 60 (phi = 30): vertical grid line x = 1 at y0 +- tan(30)
+    t30 = math.tan(math.radians(30))
+    cd1, cd2, cp = o.wet_probe(p, 0, 60.0, C)
+    assert sorted([cd1, cd2]) == pytest.approx([lin(y0 - t30), lin(y0 + t30)], abs=1e-14)
+    assert cp == pytest.approx(lin(y0 + t30), abs=1e-14)        # max for theta <= 90 (b > 0)
+    cd1, cd2, cp = o.wet_probe(p, 0, 120.0, C)
+    assert cp == pytest.approx(lin(y0 - t30), abs=1e-14)        # min branch
+    # theta = 30 (phi = 60): the first crossing y = y0 +- 1 at x = tan(30) brackets the solid
+    # node (0, y0 +- 1), so the line is extended to x = 1 at y0 +- tan(60)
+    t60 = math.tan(math.radians(60))
+    cd1, cd2, cp = o.wet_probe(p, 0, 30.0, C)
+    assert sorted([cd1, cd2]) == pytest.approx([lin(y0 - t60), lin(y0 + t60)], abs=1e-14)
+
+
 def test_weighted_contact_angle(oracle_mod):
     o, C, a, b, nx = _flat_probe(oracle_mod)
     p = 5
