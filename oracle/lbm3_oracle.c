@@ -719,6 +719,16 @@ static void zou_he(ora_t* o, double* F)
     }
 }
 
+/* Eq.(14): segregation parameters beta_kl of a node with densities rho_k (beta_kk = 0); the
+ * recolouring of the step and the ora_beta accessor both take them from here */
+static void segregation(const ora_t* o, const double rk[NF], double beta[NF][NF])
+{
+    double rho = rk[0] + rk[1] + rk[2];
+    double trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);
+    for (int k = 0; k < NF; k++)
+        for (int l = 0; l < NF; l++) beta[k][l] = (k == l) ? 0.0 : o->beta0 + o->beta0 * trip * o->gX[k][l];
+}
+
 static void one_step(ora_t* o)
 {
     size_t n = o->n;
@@ -794,13 +804,14 @@ static void one_step(ora_t* o)
                     nkl[k][l][0] = Gx / Gn;
                     nkl[k][l][1] = Gy / Gn;
                 }
-            double trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);
+            double beta_kl[NF][NF];
+            segregation(o, rk, beta_kl);
             for (int k = 0; k < NF; k++)
                 for (int a = 0; a < Q; a++) {
                     double v = rk[k] / rho * fdag[a];
                     for (int l = 0; l < NF; l++) {
                         if (l == k) continue;
-                        double beta = o->beta0 + o->beta0 * trip * o->gX[k][l];
+                        double beta = beta_kl[k][l];
                         double ne = nkl[k][l][0] * EX[a] + nkl[k][l][1] * EY[a];
                         v += beta * WQ[a] * rk[k] * rk[l] / rho * ne;
                     }
@@ -953,11 +964,10 @@ void ora_gradient_periodic(int nx, int ny, const double* psi, double* out)
 /* beta_kl table of Eq.(14) for given rho_k; out[3][3] */
 void ora_beta(ora_t* o, const double* rk, double* out)
 {
-    double rho = rk[0] + rk[1] + rk[2];
-    double trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);
+    double b[NF][NF];
+    segregation(o, rk, b);
     for (int k = 0; k < NF; k++)
-        for (int l = 0; l < NF; l++)
-            out[k * NF + l] = (k == l) ? 0.0 : o->beta0 + o->beta0 * trip * o->gX[k][l];
+        for (int l = 0; l < NF; l++) out[k * NF + l] = b[k][l];
 }
 
 /* Characteristic lines at one C_SB node against a caller-supplied C field (3n, C_F values

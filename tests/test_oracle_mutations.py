@@ -48,6 +48,14 @@ MUTATIONS = [
      "o->fnew[((size_t)k * Q + o->opp[a]) * n + i] = v;",
      "o->fnew[((size_t)k * Q + a) * n + i] = v;",
      "test_uniform_fluid_at_rest_stays_at_rest", ()),
+    ("the triple-point term of Eq.14 with 3.5 for 35",
+     "double trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);",
+     "double trip = fmin(3.5 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);",
+     "test_beta_table", ()),
+    ("the X > 0 branch of g(X) in Eq.15 with the wrong sign",
+     "    if (X <= 1.0) return sin(acos(X)) - 1.0;",
+     "    if (X <= 1.0) return 1.0 - sin(acos(X));",
+     "test_gfun_values", ()),
     ("the recolouring term of Eq.13 with the wrong sign",
      "v += beta * WQ[a] * rk[k] * rk[l] / rho * ne;",
      "v -= beta * WQ[a] * rk[k] * rk[l] / rho * ne;",
