@@ -275,6 +275,17 @@ static void state_at(const ora_t* o, int X, int Y, double c[NF], double rk[NF])
     }
 }
 
+/* Eq.(12) on the 9 values v[a] = psi(x + e_a): g = sum_a w_a psi(x + e_a) e_a / c_s^2 (the
+ * step's gradients and the ora_gradient_periodic accessor both use it) */
+static void eq12(const double v[Q], double g[2])
+{
+    g[0] = g[1] = 0.0;
+    for (int a = 0; a < Q; a++) {
+        g[0] += WQ[a] * v[a] * EX[a] / CS2;
+        g[1] += WQ[a] * v[a] * EY[a] / CS2;
+    }
+}
+
 /* a position whose C is never defined: solid beyond a wall side, a C_SI node, or the ghost
  * copy of a C_SI node beyond an open side */
 static int no_value(const ora_t* o, int loc, int idx)
@@ -289,27 +300,24 @@ static void grad_at(const ora_t* o, int X, int Y, double g[NF][2])
 {
     double c0[NF], r0[NF];
     state_at(o, X, Y, c0, r0);
-    for (int k = 0; k < NF; k++) g[k][0] = g[k][1] = 0.0;
+    double v[NF][Q];
+    for (int k = 0; k < NF; k++) v[k][0] = c0[k];
     for (int a = 1; a < Q; a++) {
         int idx, sw;
         int loc = locate(o, X + EX[a], Y + EY[a], &idx, &sw);
-        double cv[NF];
         if (no_value(o, loc, idx)) {
             int idx2, sw2;
             int loc2 = locate(o, X - EX[a], Y - EY[a], &idx2, &sw2);
             if (no_value(o, loc2, idx2)) {
-                for (int k = 0; k < NF; k++) cv[k] = c0[k];
+                for (int k = 0; k < NF; k++) v[k][a] = c0[k];
             } else {
-                for (int k = 0; k < NF; k++) cv[k] = 2.0 * c0[k] - c_at(o, idx2, sw2, k);
+                for (int k = 0; k < NF; k++) v[k][a] = 2.0 * c0[k] - c_at(o, idx2, sw2, k);
             }
         } else {
-            for (int k = 0; k < NF; k++) cv[k] = c_at(o, idx, sw, k);
-        }
-        for (int k = 0; k < NF; k++) {
-            g[k][0] += WQ[a] * cv[k] * EX[a] / CS2;
-            g[k][1] += WQ[a] * cv[k] * EY[a] / CS2;
+            for (int k = 0; k < NF; k++) v[k][a] = c_at(o, idx, sw, k);
         }
     }
+    for (int k = 0; k < NF; k++) eq12(v[k], g[k]);
 }
 
 /* Eq.(10) tensor sum_k sum_{l!=k} (sigma_kl A_kl / 2) |G_kl| (I - n_kl n_kl) at (X, Y) */
@@ -950,14 +958,11 @@ void ora_gradient_periodic(int nx, int ny, const double* psi, double* out)
 {
     for (int y = 0; y < ny; y++)
         for (int x = 0; x < nx; x++) {
-            double gx = 0.0, gy = 0.0;
-            for (int a = 0; a < Q; a++) {
-                int X = (x + EX[a] + nx) % nx, Y = (y + EY[a] + ny) % ny;
-                gx += WQ[a] * psi[Y * nx + X] * EX[a] / CS2;
-                gy += WQ[a] * psi[Y * nx + X] * EY[a] / CS2;
-            }
-            out[y * nx + x] = gx;
-            out[nx * ny + y * nx + x] = gy;
+            double v[Q], g[2];
+            for (int a = 0; a < Q; a++) v[a] = psi[((y + EY[a] + ny) % ny) * nx + (x + EX[a] + nx) % nx];
+            eq12(v, g);
+            out[y * nx + x] = g[0];
+            out[nx * ny + y * nx + x] = g[1];
         }
 }
 

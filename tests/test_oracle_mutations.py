@@ -33,9 +33,9 @@ MUTATIONS = [
      "for (int k = 0; k < NF; k++) inv += rk[k] * (o->rho0[k] * o->nu[k]);\n    double mu = inv / rho;",
      "test_mixture_viscosity_is_harmonic", ()),
     ("the Eq.12 stencil without its 1/c_s^2",
-     "g[k][0] += WQ[a] * cv[k] * EX[a] / CS2;\n            g[k][1] += WQ[a] * cv[k] * EY[a] / CS2;",
-     "g[k][0] += WQ[a] * cv[k] * EX[a];\n            g[k][1] += WQ[a] * cv[k] * EY[a];",
-     "test_laplace_law", ()),
+     "g[0] += WQ[a] * v[a] * EX[a] / CS2;\n        g[1] += WQ[a] * v[a] * EY[a] / CS2;",
+     "g[0] += WQ[a] * v[a] * EX[a];\n        g[1] += WQ[a] * v[a] * EY[a];",
+     "test_gradient_symbol", ()),
     ("I + nn instead of I - nn in the Eq.10 stress",
      "T[0] += s * (1.0 - nx * nx);",
      "T[0] += s * (1.0 + nx * nx);",
