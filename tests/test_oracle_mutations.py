@@ -28,6 +28,10 @@ MUTATIONS = [
      "return mu / (rho * CS2) + 0.5;",
      "return mu / (rho * CS2) + 1.0;",
      "test_shear_wave_decay", ()),
+    ("s_4 = s_1 instead of Eq.6's 8(2 - s_1)/(8 - s_1)",
+     "double s4 = 8.0 * (2.0 - s1) / (8.0 - s1);",
+     "double s4 = s1;",
+     "test_halfway_walls_in_poiseuille_flow", ()),
     ("an arithmetic instead of a harmonic mixture viscosity in Eq.7",
      "for (int k = 0; k < NF; k++) inv += rk[k] / (o->rho0[k] * o->nu[k]);\n    double mu = rho / inv;",
      "for (int k = 0; k < NF; k++) inv += rk[k] * (o->rho0[k] * o->nu[k]);\n    double mu = inv / rho;",

@@ -632,3 +632,24 @@ def test_cylinder_janus_reduced(oracle_mod):
     for theta, (R, D, t) in zip(thetas, got):
         assert abs(t - theta) <= 2.0, (theta, t)
         assert abs(D - P.eq23_distance(P.E5_RS * sc + 0.5, R, theta)) <= 1.0, (theta, R, D)
+
+
+def test_halfway_walls_in_poiseuille_flow(oracle_mod):
+    """Eq.(6)'s s_4 = 8(2 - s_1)/(8 - s_1) puts a halfway bounce-back wall exactly half a link
+    outside the last fluid node for every viscosity.  Behind a meniscus intruding into a channel
+    (two-phase, 150 x 17, H = 15, nu = 0.35 so tau = 1.55, 6000 steps) the flow is Poiseuille flow:
+    u_x across the channel in the middle of the intruding column is a parabola (to 1e-4 of its
+    peak) whose roots lie within 0.02 of the walls at y = 0.5 and 15.5 (with s_4 = s_1 they move
+    by 0.08)."""
+    w = W.capillary(nx=150, ny=17, y_lo=1, y_hi=16, s0=40, Lg=0, triple=(90.0, 150.0, 30.0),
+                    nu=(0.35,) * 3)
+    o = oracle_mod.Oracle.from_workload(w)
+    o.step(6000)
+    r, u = o.fields()
+    x = int(r[0].sum() / 15.0 / 2)
+    ux = u[0][1:16, x]
+    yy = np.arange(1, 16, dtype=np.float64)
+    c = np.polyfit(yy, ux, 2)
+    roots = np.sort(np.roots(c).real)
+    assert np.abs(ux - np.polyval(c, yy)).max() < 1e-4 * ux.max()
+    assert abs(roots[0] - 0.5) < 0.02 and abs(roots[1] - 15.5) < 0.02, roots
