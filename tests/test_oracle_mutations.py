@@ -103,22 +103,34 @@ MUTATIONS = [
 ]
 
 
-def mutant(tmp_path, old, new):
-    d = tmp_path / "oracle"
+def mutant(d, old, new, tag):
+    """Build the oracle with `old` replaced by `new` in directory d; return its module."""
     d.mkdir()
     src = open(os.path.join(ORACLE, "lbm3_oracle.c")).read()
     assert src.count(old) == 1, "the planted text must occur exactly once"
     (d / "lbm3_oracle.c").write_text(src.replace(old, new))
     shutil.copy(os.path.join(ORACLE, "oracle.py"), d / "oracle.py")
-    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{tmp_path.name}", d / "oracle.py")
+    spec = importlib.util.spec_from_file_location(f"oracle_mutant_{tag}", d / "oracle.py")
     mod = importlib.util.module_from_spec(spec)
     spec.loader.exec_module(mod)
     mod.build()
     return mod
 
 
-@pytest.mark.parametrize("what,old,new,pin,args", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_pin_catches_planted_mistake(tmp_path, what, old, new, pin, args):
-    mod = mutant(tmp_path, old, new)
-    with pytest.raises(AssertionError):
-        getattr(PINS, pin)(mod, *args)
+def test_every_planted_mistake_is_caught(tmp_path):
+    """All cases at once on threads (each mutant is its own library; the oracle's C calls
+    release the GIL); the failure message names every slip that no pin caught."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    def run(j):
+        what, old, new, pin, args = MUTATIONS[j]
+        mod = mutant(tmp_path / f"m{j}", old, new, j)
+        try:
+            getattr(PINS, pin)(mod, *args)
+        except AssertionError:
+            return None
+        return f"{what} (pin {pin})"
+
+    with ThreadPoolExecutor(8) as ex:
+        missed = [m for m in ex.map(run, range(len(MUTATIONS))) if m]
+    assert not missed, "not caught: " + "; ".join(missed)
