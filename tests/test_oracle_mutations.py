@@ -92,6 +92,14 @@ MUTATIONS = [
      "*CD = Clow + fr * (Cup - Clow);",
      "*CD = Cup + fr * (Clow - Cup);",
      "test_rays_vertical_wall_hand_worked", ()),
+    ("an unweighted instead of a w-weighted neighbour mean",
+     "            s += WQ[a] * c_at(o, idx, sw, k);\n            ws += WQ[a];",
+     "            s += c_at(o, idx, sw, k);\n            ws += 1.0;",
+     "test_initial_wall_values_weighted_mean", ()),
+    ("the third wall value without C_1 in 1 - C_0 - C_1",
+     "        double cb = fmax(0.0, 1.0 - cr - cg);",
+     "        double cb = fmax(0.0, 1.0 - cr);",
+     "test_wall_values_close_to_one", ()),
     ("Eq.22's max and min exchanged",
      "return theta_k <= 90.0 ? fmax(c1, c2) : fmin(c1, c2);",
      "return theta_k <= 90.0 ? fmin(c1, c2) : fmax(c1, c2);",

@@ -350,6 +350,40 @@ def test_rays_vertical_wall_hand_worked(oracle_mod):
     assert sorted([cd1, cd2]) == pytest.approx([lin(y0 - t60), lin(y0 + t60)], abs=1e-14)
 
 
+def test_initial_wall_values_weighted_mean(oracle_mod):
+    """Before the first wetting pass a C_SB node holds the w-weighted mean of its fluid
+    neighbours' C (the same mean is the fallback of a line with no valid crossing).  On a flat
+    bottom wall under C_0 = q(x) quadratic in x the three fluid neighbours of node (x0, 0) give
+    (q(x0-1) + 4 q(x0) + q(x0+1)) / 6 = q(x0) + q''/6, where an unweighted mean gives q(x0) + q''/3."""
+    nx, ny = 24, 10
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[0] = 1
+    solid[-1] = 1
+    o = oracle_mod.Oracle(**_single_fluid(nx, ny, 0.1, solid=solid, per_y=0))
+    x = np.arange(nx, dtype=np.float64)
+    q = 0.1 + 0.002 * (x - 10.0) ** 2                    # q'' = 0.004
+    rho = np.zeros((3, ny, nx))
+    rho[0, 1:-1] = q
+    rho[2, 1:-1] = 1.0 - q
+    o.set_fields(rho)
+    Cw = o.wall_C()
+    for x0 in (5, 12, 18):
+        assert abs(Cw[0, 0, x0] - (q[x0] + 0.004 / 6.0)) < 1e-14, (x0, Cw[0, 0, x0])
+
+
+def test_wall_values_close_to_one(oracle_mod):
+    """After the wetting pass (Eq.22 for fluids 0 and 1) the third fluid's wall value is
+    C_2 = 1 - C_0 - C_1: at every C_SB node of a three-fluid run the three wall values sum to 1."""
+    w = W.janus_flat(nx=64, ny=32, R=10.0, triple=(80.0, 60.0, 110.0))
+    o = oracle_mod.Oracle.from_workload(w)
+    o.step(30)
+    Cw = o.wall_C()
+    sb = w.solid.astype(bool)
+    sb[1:-1] = False                                     # the two wall rows are C_SB nodes
+    assert np.abs(Cw[:, sb].sum(0) - 1.0).max() < 1e-12
+    assert Cw[1, sb].max() > 0.5 and Cw[0, sb].max() > 0.5   # wall values of several fluids
+
+
 def test_weighted_contact_angle(oracle_mod):
     o, C, a, b, nx = _flat_probe(oracle_mod)
     p = 5
