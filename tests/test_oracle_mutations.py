@@ -68,6 +68,14 @@ MUTATIONS = [
      "double g1 = f[3] + 2.0 / 3.0 * rho * U;",
      "double g1 = f[3] - 2.0 / 3.0 * rho * U;",
      "test_zou_he_uniform_inflow", ()),
+    ("the Zou-He outlet population with the wrong sign of u",
+     "double h3 = f[1] - 2.0 / 3.0 * ro * ux;",
+     "double h3 = f[1] + 2.0 / 3.0 * ro * ux;",
+     "test_zou_he_uniform_inflow", ()),
+    ("Eq.21 for fluid 1 weighted by the wrong fluid",
+     "        th[1] = t_gr + Cb / (Cb + Cr) * (t_gb - t_gr);",
+     "        th[1] = t_gr + Cr / (Cb + Cr) * (t_gb - t_gr);",
+     "test_weighted_contact_angle", ()),
     ("no fluid swap across the modified periodic seam",
      "int kk = sw ? swapk(k) : k;",
      "int kk = k;",
