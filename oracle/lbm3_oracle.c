@@ -50,6 +50,11 @@
  *     C beyond the open columns is a copy of the boundary column (zero gradient)
  *
  * Fluid indices 0, 1, 2 are the paper's red, green, blue.
+ *
+ * Threads: the per-node loops of a step may run on several OpenMP threads (ora_set_threads,
+ * default 1).  Every iteration writes only its own node's values (push streaming: each
+ * destination population has exactly one source), and no loop reduces across nodes, so the
+ * result is bit-identical for any thread count.
  */
 #include <math.h>
 #include <stdio.h>
@@ -105,6 +110,7 @@ typedef struct ora {
     double *Fs;           /* [2][node] */
     double *u;            /* [2][node]: velocity of the last collision, Eq.(11) */
     long steps;
+    int threads;          /* OpenMP threads of the per-node loops (1 unless set) */
 } ora_t;
 
 /* ------------------------------------------------------------------------- */
@@ -482,6 +488,8 @@ static void local_angles(const ora_t* o, int p, double th[2])
 static void wetting(ora_t* o)
 {
     size_t n = o->n;
+    /* each C_SB node writes only its own values and reads C at fluid nodes */
+#pragma omp parallel for num_threads(o->threads) schedule(dynamic, 64) if (o->threads > 1)
     for (int p = 0; p < o->n; p++) {
         if (o->cls[p] != CL_SB) continue;
         double th[2];
@@ -626,6 +634,7 @@ ora_t* ora_create(int nx, int ny, int per_y, int bc_x, double u_in, double rho_o
     o->T = (double*)calloc(3 * n, sizeof(double));
     o->Fs = (double*)calloc(2 * n, sizeof(double));
     o->u = (double*)calloc(2 * n, sizeof(double));
+    o->threads = 1;
     classify(o);
     normals(o);
     return o;
@@ -643,6 +652,7 @@ void ora_destroy(ora_t* o)
 static void densities(ora_t* o)
 {
     size_t n = o->n;
+#pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (size_t i = 0; i < n; i++) {
         if (o->solid[i]) continue;
         double r = 0.0;
@@ -745,6 +755,7 @@ static void one_step(ora_t* o)
     /* O2-O4 */
     wetting(o);
     /* O5-O6: stress tensor at C_F and C_SB nodes, then its divergence at C_F */
+#pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             int i = y * o->nx + x;
@@ -753,6 +764,7 @@ static void one_step(ora_t* o)
             tensor_at(o, x, y, T);
             for (int c = 0; c < 3; c++) o->T[c * n + i] = T[c];
         }
+#pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             int i = y * o->nx + x;
@@ -777,6 +789,7 @@ static void one_step(ora_t* o)
     /* O7-O9 per fluid node: collision, then recolouring; results into fnew in place of
      * the post-collision populations of the node (streamed below) */
     double* fdd = (double*)malloc(sizeof(double) * NF * Q * n);
+#pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             int i = y * o->nx + x;
@@ -828,6 +841,7 @@ static void one_step(ora_t* o)
         }
     /* O10: streaming, Eq.(16) */
     memset(o->fnew, 0, sizeof(double) * NF * Q * n);
+#pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             int i = y * o->nx + x;
@@ -854,6 +868,9 @@ static void one_step(ora_t* o)
     o->fnew = t;
     o->steps++;
 }
+
+/* OpenMP threads of the per-node loops (results do not depend on it); n < 1 means 1 */
+void ora_set_threads(ora_t* o, int n) { o->threads = n < 1 ? 1 : n; }
 
 void ora_step(ora_t* o, int nsteps)
 {
@@ -989,4 +1006,18 @@ void ora_local_angles(ora_t* o, int p, const double* Cp, double* th)
     size_t n = o->n;
     for (int k = 0; k < NF; k++) o->Cw[k * n + p] = Cp[k];
     local_angles(o, p, th);
+}
+
+/* Eq.(12) gradients of C_0..C_2 at node (x, y), the step's own grad_at, against a
+ * caller-supplied C field (3n values: fluid nodes and C_SB wall values); g = 6 values
+ * (dC_k/dx, dC_k/dy for k = 0, 1, 2) */
+void ora_gradient_at(ora_t* o, const double* Cfield, int x, int y, double* g)
+{
+    double gg[NF][2];
+    memcpy(o->C, Cfield, sizeof(double) * NF * o->n);
+    grad_at(o, x, y, gg);
+    for (int k = 0; k < NF; k++) {
+        g[2 * k] = gg[k][0];
+        g[2 * k + 1] = gg[k][1];
+    }
 }

@@ -21,13 +21,25 @@ _U8 = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (portable flags only: it must build on x86 and Arm)."""
+    """Compile the oracle with gcc (portable flags only: it must build on x86 and Arm), with
+    OpenMP where the compiler has it (the per-node loops then run on ``threads`` threads; the
+    results do not depend on the thread count) and without it otherwise."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared",
-                               "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
+        base = ["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-ffp-contract=off",
+                "-o", tmp, _SRC, "-lm"]
+        if subprocess.run(base[:1] + ["-fopenmp"] + base[1:], capture_output=True).returncode != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def host_threads() -> int:
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover
+        return os.cpu_count() or 1
 
 
 def lib():
@@ -45,6 +57,7 @@ def lib():
         L.ora_check.restype = ctypes.c_int
         L.ora_set_fields.argtypes = [ctypes.c_void_p, _D]
         L.ora_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        L.ora_set_threads.argtypes = [ctypes.c_void_p, ctypes.c_int]
         L.ora_fields.argtypes = [ctypes.c_void_p, _D, _D]
         L.ora_diag.argtypes = [ctypes.c_void_p, _D]
         for name in ("ora_get_f", "ora_set_f", "ora_get_normals", "ora_get_wallC",
@@ -61,6 +74,7 @@ def lib():
         L.ora_wet_probe.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                     ctypes.c_double, _D, _D]
         L.ora_local_angles.argtypes = [ctypes.c_void_p, ctypes.c_int, _D, _D]
+        L.ora_gradient_at.argtypes = [ctypes.c_void_p, _D, ctypes.c_int, ctypes.c_int, _D]
         _lib = L
     return _lib
 
@@ -77,7 +91,7 @@ class Oracle:
     """One oracle simulation: geometry, parameters and FP64 state."""
 
     def __init__(self, nx, ny, periodic_y, bc_x, solid, angles, sigma, nu, beta0=0.7,
-                 u_in=0.0, rho_out=1.0):
+                 u_in=0.0, rho_out=1.0, threads=1):
         L = lib()
         self.nx, self.ny = int(nx), int(ny)
         self.n = self.nx * self.ny
@@ -94,13 +108,20 @@ class Oracle:
             L.ora_destroy(self._h)
             self._h = None
             raise ValueError(f"oracle: invalid configuration (code {code})")
+        self.set_threads(threads)
 
     @classmethod
-    def from_workload(cls, w):
+    def from_workload(cls, w, threads=1):
         o = cls(w.nx, w.ny, w.periodic_y, w.bc_x, w.solid, w.angles, w.sigma, w.nu, w.beta0,
-                w.u_in, w.rho_out)
+                w.u_in, w.rho_out, threads=threads)
         o.set_fields(w.rho)
         return o
+
+    def set_threads(self, n):
+        """OpenMP threads of the per-node loops (0 or None: every host core)."""
+        n = host_threads() if not n else int(n)
+        lib().ora_set_threads(self._h, n)
+        self.threads = n
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -167,6 +188,15 @@ class Oracle:
         out = np.empty(3)
         lib().ora_wet_probe(self._h, int(node), int(k), float(theta_k), _dp(C), _dp(out))
         return out
+
+    def gradient_at(self, C, x, y):
+        """Eq.(12) gradients (3, 2) of the three phase fields at node (x, y) as the step takes
+        them, against the phase-field array C (3, ny, nx) holding fluid and C_SB values."""
+        C = _c(C).reshape(-1)
+        assert C.size == 3 * self.n
+        out = np.empty(6)
+        lib().ora_gradient_at(self._h, _dp(C), int(x), int(y), _dp(out))
+        return out.reshape(3, 2)
 
     def local_angles(self, node, Cp):
         out = np.empty(2)

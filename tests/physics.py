@@ -221,3 +221,69 @@ def washburn_ternary(t, s0, H, L, Lg, sig_gb, th_gb, sig_gr, th_gr, mu_r, mu_g, 
         return A / B * t + s0
     f = -0.5 * C * s0 * s0 - B * s0 - A * t
     return (-B + np.sqrt(B * B - 2.0 * C * f)) / C
+
+
+# ---- Section II.A: a free lens of fluid 1 on a flat interface between fluids 0 and 2 ----
+def neumann_angles(sigma):
+    """Angles (gamma_0, gamma_1, gamma_2) in degrees, gamma_k inside fluid k, at a triple
+    junction where three interfaces with tensions sigma = (sigma_01, sigma_02, sigma_12) meet in
+    equilibrium: the tensions balance as the sides of a triangle, sigma_12 / sin gamma_0 =
+    sigma_02 / sin gamma_1 = sigma_01 / sin gamma_2, so 180 - gamma_k is the triangle's angle
+    opposite the side sigma_lm of the two other fluids (law of cosines)."""
+    s01, s02, s12 = sigma
+    g0 = 180.0 - np.degrees(np.arccos((s01 ** 2 + s02 ** 2 - s12 ** 2) / (2 * s01 * s02)))
+    g1 = 180.0 - np.degrees(np.arccos((s01 ** 2 + s12 ** 2 - s02 ** 2) / (2 * s01 * s12)))
+    g2 = 180.0 - np.degrees(np.arccos((s02 ** 2 + s12 ** 2 - s01 ** 2) / (2 * s02 * s12)))
+    return g0, g1, g2
+
+
+def lens_workload(sigma, nx=96, ny=64, c=12.0, nu=1.0 / 6.0):
+    """Fully periodic box: fluid 0 in the band 12 <= y < 44, fluid 2 elsewhere, and a lens of
+    fluid 1 on the upper 0-2 interface (y0 = 43.5) centred at x = nx / 2: two circular caps
+    on the chord of half-length c, the upper one (in fluid 2) and the lower one (in fluid 0)
+    each meeting the interface at the angles of Neumann's triangle for sigma, so that the run
+    starts near equilibrium."""
+    from paper_2102_04709_gb300.workloads import Workload, BC_PERIODIC
+    g0, g1, g2 = neumann_angles(sigma)
+    au, al = np.radians(180.0 - g2), np.radians(180.0 - g0)   # cap angles inside fluid 1
+    y0, xc = 43.5, nx / 2.0
+    x, y = np.meshgrid(np.arange(nx, dtype=float), np.arange(ny, dtype=float))
+    lab = np.where((y >= 12) & (y < 44), 0, 2)
+    Ru, Rl = c / np.sin(au), c / np.sin(al)
+    yu, yl = y0 - Ru * np.cos(au), y0 + Rl * np.cos(al)     # centres of the two arcs
+    up = (y >= y0) & ((x - xc) ** 2 + (y - yu) ** 2 < Ru * Ru)
+    lo = (y < y0) & ((x - xc) ** 2 + (y - yl) ** 2 < Rl * Rl)
+    lab[up | lo] = 1
+    rho = np.zeros((3, ny, nx))
+    for k in range(3):
+        rho[k][lab == k] = 1.0
+    solid = np.zeros((ny, nx), np.uint8)
+    return Workload(f"lens_{nx}x{ny}", nx, ny, 1, BC_PERIODIC, solid, rho,
+                    np.full((ny, nx, 3), 90.0), tuple(sigma), (nu,) * 3, steps=0)
+
+
+def lens_angles(rho, gap=2.5):
+    """Angles (gamma_0, gamma_1, gamma_2) in degrees of a lens of fluid 1 on the 0-2 interface,
+    measured from the final fields: the 0-2 interface height y0 is the mean of the
+    C_0 / (C_0 + C_2) = 1/2 crossings along the columns more than 12 nodes beyond the lens;
+    circles are fitted to the C_1 = 1/2 contour above y0 + gap (the 1-2 interface) and below
+    y0 - gap (the 0-1 interface), away from the junctions; each arc meets the line y = y0 at
+    the angle alpha of a cap on that line, measured inside fluid 1; gamma_1 = alpha_up +
+    alpha_low, gamma_2 = 180 - alpha_up, gamma_0 = 180 - alpha_low."""
+    rho = np.asarray(rho, dtype=np.float64)
+    C = rho / np.maximum(rho.sum(0), 1e-30)
+    ny, nx = C[0].shape
+    none = np.zeros((ny, nx), bool)
+    p1 = contour_points(C[1], none)
+    lx0, lx1 = p1[:, 0].min(), p1[:, 0].max()
+    with np.errstate(invalid="ignore", divide="ignore"):
+        phi = np.where(C[1] < 0.5, C[0] / (C[0] + C[2]), np.nan)
+    p02 = contour_points(phi, none)
+    far = (p02[:, 0] < lx0 - 12) | (p02[:, 0] > lx1 + 12)
+    top = p02[:, 1] > ny / 2          # the interface that carries the lens (upper one)
+    y0 = float(p02[far & top, 1].mean())
+    xu, yu, Ru = fit_circle(p1[p1[:, 1] > y0 + gap])
+    xl, yl, Rl = fit_circle(p1[p1[:, 1] < y0 - gap])
+    au = float(np.degrees(np.arccos(np.clip(-(yu - y0) / Ru, -1.0, 1.0))))
+    al = float(np.degrees(np.arccos(np.clip((yl - y0) / Rl, -1.0, 1.0))))
+    return 180.0 - al, au + al, 180.0 - au

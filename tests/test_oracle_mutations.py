@@ -112,6 +112,22 @@ MUTATIONS = [
      "return theta_k <= 90.0 ? fmax(c1, c2) : fmin(c1, c2);",
      "return theta_k <= 90.0 ? fmin(c1, c2) : fmax(c1, c2);",
      "test_contact_angle_flat_wall", (45.0,)),
+    ("the tensions sigma_02 and sigma_12 assigned to each other's pair",
+     "    o->sigma[0][2] = o->sigma[2][0] = sigma[1];\n    o->sigma[1][2] = o->sigma[2][1] = sigma[2];",
+     "    o->sigma[0][2] = o->sigma[2][0] = sigma[2];\n    o->sigma[1][2] = o->sigma[2][1] = sigma[1];",
+     "test_neumann_lens", ((0.010, 0.012, 0.008),)),
+    ("the Eq.10 stress of a pair weighted by the tension of another pair",
+     "double s = 0.5 * o->sigma[k][l] * A * Gn;",
+     "double s = 0.5 * o->sigma[k][3 - k - l] * A * Gn;",
+     "test_neumann_lens", ((0.010, 0.012, 0.008),)),
+    ("X_kl of Eq.15 built around the wrong pair (sigma_kl and sigma_ml exchanged)",
+     "            double X = (o->sigma[m][k] * o->sigma[m][k] + o->sigma[m][l] * o->sigma[m][l] -\n                        o->sigma[k][l] * o->sigma[k][l]) /\n                       (2.0 * o->sigma[m][k] * o->sigma[m][l]);",
+     "            double X = (o->sigma[m][k] * o->sigma[m][k] + o->sigma[k][l] * o->sigma[k][l] -\n                        o->sigma[m][l] * o->sigma[m][l]) /\n                       (2.0 * o->sigma[m][k] * o->sigma[k][l]);",
+     "test_beta_table", ()),
+    ("a missing Eq.12 neighbour of a wall node taking the node's own value",
+     "                for (int k = 0; k < NF; k++) v[k][a] = 2.0 * c0[k] - c_at(o, idx2, sw2, k);",
+     "                for (int k = 0; k < NF; k++) v[k][a] = c0[k];",
+     "test_gradient_at_wall_node_linear_field", ()),
     ("Eq.21 weighted by the wrong fluid",
      "th[0] = t_rg + Cb / (Cb + Cg) * (t_rb - t_rg);",
      "th[0] = t_rg + Cg / (Cb + Cg) * (t_rb - t_rg);",

@@ -350,6 +350,48 @@ def test_rays_vertical_wall_hand_worked(oracle_mod):
     assert sorted([cd1, cd2]) == pytest.approx([lin(y0 - t60), lin(y0 + t60)], abs=1e-14)
 
 
+def test_gradient_at_wall_node_linear_field(oracle_mod):
+    """Eq.(12) at a C_SB node, whose stencil reaches nodes without a phase field (C_SI, and
+    solid beyond a wall side).  The reading used here (a missing neighbour P + e_a takes the
+    linear extrapolation 2 C(P) - C(P - e_a) through the wall node P) makes the stencil exact on
+    a phase field that is linear across the wall, which is what the characteristic lines of
+    Section II.B assume: hand-worked, Eq.(12) of C = a + b y + c x is (c, b) at every node.
+    The alternative readings give other values: the node's own value C(P) for each missing
+    neighbour gives d/dy = 3 (1/9 + 2/36) b = b/2 at a flat wall, and a zero stress at solid
+    nodes takes no gradient there at all.  Bottom wall two rows thick (its C_SB row has C_SI
+    below), top wall one row (solid beyond the domain above it); x periodic."""
+    nx, ny = 16, 12
+    solid = np.zeros((ny, nx), np.uint8)
+    solid[:2] = 1
+    solid[-1] = 1
+    o = oracle_mod.Oracle(nx, ny, 0, W.BC_PERIODIC, solid, np.full((ny, nx, 3), 90.0),
+                          (0.01, 0.01, 0.01), (0.1, 0.1, 0.1))
+    cls = o.classes()
+    assert (cls[1] == 2).all() and (cls[0] == 3).all() and (cls[-1] == 2).all()
+    yy = np.arange(ny, dtype=float)[:, None] * np.ones((1, nx))
+    xx = np.ones((ny, 1)) * np.arange(nx, dtype=float)[None, :]
+    a, b = np.array([0.2, 0.5, 0.3]), np.array([0.03, -0.05, 0.02])
+    C = a[:, None, None] + b[:, None, None] * yy
+    C[:, 0] = np.nan                      # C_SI: the step must never read it
+    for y in (1, ny - 1):                 # C_SB rows, both walls
+        for x in (0, 5, nx - 1):          # including the periodic seam
+            g = o.gradient_at(C, x, y)
+            assert np.all(np.isfinite(g))
+            assert np.abs(g[:, 0]).max() < 1e-15
+            assert np.abs(g[:, 1] - b).max() < 1e-15, (y, x, g[:, 1], b)
+    # linear in x as well (no periodic wrap in the field: stay away from the seam)
+    c = np.array([0.01, -0.02, 0.01])
+    C2 = C + c[:, None, None] * xx
+    C2[:, 0] = np.nan
+    for y in (1, ny - 1):
+        for x in (3, 8):
+            g = o.gradient_at(C2, x, y)
+            assert np.abs(g[:, 0] - c).max() < 1e-15 and np.abs(g[:, 1] - b).max() < 1e-15
+    # a fluid node is Eq.(12) itself, exact on linear fields too
+    g = o.gradient_at(C2, 8, 5)
+    assert np.abs(g[:, 0] - c).max() < 1e-15 and np.abs(g[:, 1] - b).max() < 1e-15
+
+
 def test_initial_wall_values_weighted_mean(oracle_mod):
     """Before the first wetting pass a C_SB node holds the w-weighted mean of its fluid
     neighbours' C (the same mean is the fallback of a line with no valid crossing).  On a flat
@@ -513,6 +555,24 @@ def test_rotation_symmetry(oracle_mod):
     assert np.abs(-rot(u1[0]) - u2[1]).max() < 1e-12
 
 
+def test_thread_count_does_not_change_results(oracle_mod):
+    """The per-node loops on several OpenMP threads give the single-threaded result bit for
+    bit (each iteration writes only its own node; no loop sums across nodes): wetting on a
+    curved wall, the modified periodic seam and Zou-He."""
+    cases = [W.janus_cylinder(nx=64, ny=60, Rs=12.0, Rj=10.0),
+             W.capillary(nx=80, ny=24, y_lo=4, y_hi=20, s0=20, Lg=20, nu=(0.1, 0.02, 0.05)),
+             W.pillars(nx=96, ny=48, count=2, r_lo=6.0, r_hi=9.0, x_lo=40.0, x_hi=85.0, gap=4.0,
+                       seed=3, drop=(20.0, 24.0), r_core=6.0, r_shell=11.0,
+                       theta_range=(60.0, 120.0), u_in=0.02)]
+    for w in cases:
+        out = []
+        for t in (1, 4):
+            o = oracle_mod.Oracle.from_workload(w, threads=t)
+            o.step(30)
+            out.append((o.get_f(), o.wall_C()))
+        assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1]), w.name
+
+
 # --------------------------------------------------------------------------------------
 # physics closed forms
 # --------------------------------------------------------------------------------------
@@ -539,6 +599,45 @@ def test_laplace_law(oracle_mod):
         assert np.abs(u).max() < 1e-4       # spurious currents O(1e-5)
     # two radii: the pressure jump scales as 1/R
     assert abs((out[0][0] / out[1][0]) / (out[0][1] / out[1][1]) - 1.0) < 0.06
+
+
+NEUMANN_SETS = [(0.01, 0.01, 0.01), (0.010, 0.012, 0.008)]
+
+
+@pytest.mark.parametrize("sigma", NEUMANN_SETS, ids=["equal", "unequal"])
+def test_neumann_lens(oracle_mod, sigma):
+    """A free lens of fluid 1 on the flat interface between fluids 0 and 2 (Section II.A,
+    Eq.10-15 with three tensions): at each junction the three interfaces balance as the sides
+    of Neumann's triangle, sigma_12 / sin gamma_0 = sigma_02 / sin gamma_1 = sigma_01 / sin
+    gamma_2 (gamma_k inside fluid k): 120/120/120 deg for equal tensions, 138.59/97.18/124.23
+    deg for (sigma_01, sigma_02, sigma_12) = (0.010, 0.012, 0.008).  The lens (chord 40 lu)
+    starts as two circular caps near that shape and relaxes for 3000 steps; every angle must
+    lie within 3 % of Neumann's, the paper's own accuracy for static contact angles (Table I,
+    largest error 3.0 %).  A tension assigned to the wrong pair moves gamma_1 by 30-40 deg."""
+    w = P.lens_workload(sigma, nx=128, ny=64, c=20.0)
+    o = oracle_mod.Oracle.from_workload(w, threads=0)
+    o.step(3000)
+    r, u = o.fields()
+    got = P.lens_angles(r)
+    want = P.neumann_angles(sigma)
+    assert abs(sum(want) - 360.0) < 1e-9
+    for g, e in zip(got, want):
+        assert abs(g - e) <= 0.03 * e, (got, want)
+    assert np.abs(u).max() < 1e-3       # spurious currents at the junctions
+
+
+def test_neumann_angles_closed_form():
+    """The helper the lens pin compares against: the law of cosines of the tension triangle
+    reproduces its sine rule and sums to 360 deg (hand-worked for one set)."""
+    for sig in NEUMANN_SETS + [(0.01, 0.01 * math.sqrt(2.0), 0.01)]:
+        g = P.neumann_angles(sig)
+        assert abs(sum(g) - 360.0) < 1e-9
+        ratios = [sig[2] / math.sin(math.radians(g[0])), sig[1] / math.sin(math.radians(g[1])),
+                  sig[0] / math.sin(math.radians(g[2]))]
+        assert max(ratios) - min(ratios) < 1e-12 * max(ratios)
+    # sigma_01 = sigma_12 = s, sigma_02 = s sqrt(2): gamma_1 = 2 acos(1/sqrt 2) = 90 deg
+    g = P.neumann_angles((0.01, 0.01 * math.sqrt(2.0), 0.01))
+    assert abs(g[1] - 90.0) < 1e-9 and abs(g[0] - 135.0) < 1e-9 and abs(g[2] - 135.0) < 1e-9
 
 
 def test_flat_interface_segregation_balance(oracle_mod):
