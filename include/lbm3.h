@@ -106,13 +106,16 @@ int lbm3_step(lbm3* h, int32_t nsteps);
 int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3]);
 
 /* Copy the current post-streaming densities rho_k (host [3][ny][nx], 0 at solid nodes) and the
- * velocity of the most recent collision, Eq.(11) (host [2][ny][nx], may be NULL).  Synchronises. */
+ * velocity of the most recent collision, Eq.(11) (host [2][ny][nx], may be NULL).  Synchronises.
+ * Returns LBM3_ERR_CUDA (with the arrays filled) if a step kernel gave up on a bulk copy since the
+ * error was last reported (see lbm3_set_copy_wait_limit). */
 int lbm3_fields(lbm3* h, double* rho_out, double* u_out);
 
 /* Diagnostics of the current state, accumulated in FP64 on the GPU:
  * out[0..2] = sum of rho_k over fluid nodes, out[3] = sum x rho_0, out[4] = sum y rho_0,
  * out[5] = max |u| of the last collision, out[6] = min rho, out[7] = count of non-finite rho_k.
- * Returns LBM3_ERR_DIVERGED (with out filled) if out[7] > 0 or out[6] <= 0.  Synchronises. */
+ * Returns LBM3_ERR_DIVERGED (with out filled) if out[7] > 0 or out[6] <= 0, and LBM3_ERR_CUDA if
+ * a step kernel gave up on a bulk copy since the error was last reported.  Synchronises. */
 int lbm3_diag(lbm3* h, double out[8]);
 
 /* Number of C_SB nodes (the wall list) and their node indices, in increasing order
@@ -162,8 +165,20 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, dou
  * LBM3_DISABLE_TMA=1 in the environment at lbm3_create), else 0. */
 int lbm3_info(const lbm3* h, int64_t out[9]);
 
-/* Change the stream used by later calls (cudaStream_t). */
+/* Change the stream used by later calls (cudaStream_t).  Work already enqueued by the handle
+ * on the old stream is ordered before the work of later calls on the new one (an event recorded
+ * on the old stream that the new stream waits for). */
 int lbm3_set_stream(lbm3* h, void* stream);
+
+/* Failure detection.  The pure-tile kernels move each tile's populations with bulk tensor copies
+ * that complete on an mbarrier; a block polls it at most `polls` times (default 4194304, a few
+ * seconds; polls < 0 restores the default) before it gives up: it sets an error bit, waits (with
+ * the full default limit) for the copies it has in flight and returns without writing its
+ * tiles.  lbm3_fields, lbm3_diag and lbm3_adjoint_centroid then return LBM3_ERR_CUDA once (the
+ * bit is cleared when reported, and by lbm3_set_fields / lbm3_set_state, which replace the state
+ * whose tiles were skipped).  polls = 0 makes every wait give up at once, which is how the error
+ * path is tested without faulting or hanging anything.  The paper has no counterpart. */
+int lbm3_set_copy_wait_limit(lbm3* h, int32_t polls);
 
 /* Block until all work enqueued by the handle is done. */
 int lbm3_sync(lbm3* h);

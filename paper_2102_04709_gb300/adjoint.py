@@ -16,19 +16,22 @@ from . import lbm3
 class CentroidObjective(torch.autograd.Function):
     @staticmethod
     def forward(ctx, angles, u_in, sim, rho0, nsteps, checkpoint_every):
+        u_t = torch.as_tensor(u_in)
         sim.set_wall_angles(angles.detach().cpu().double().numpy())
         if sim.bc_x == 2:
-            sim.set_inflow(float(u_in))
+            sim.set_inflow(float(u_t))
         sim.set_fields(rho0)
         J, dang, du = sim.adjoint_centroid(nsteps, checkpoint_every)
-        ctx.save_for_backward(torch.as_tensor(dang, dtype=torch.float64),
-                              torch.tensor(du, dtype=torch.float64))
-        return torch.tensor(J, dtype=torch.float64)
+        # the gradients live where the inputs do, in their dtype
+        ctx.save_for_backward(torch.as_tensor(dang, dtype=angles.dtype, device=angles.device),
+                              torch.tensor(du, dtype=u_t.dtype, device=u_t.device))
+        return torch.tensor(J, dtype=torch.float64, device=angles.device)
 
     @staticmethod
     def backward(ctx, gJ):
         dang, du = ctx.saved_tensors
-        return gJ * dang, gJ * du, None, None, None, None
+        return (gJ.to(dang.device, dang.dtype) * dang, gJ.to(du.device, du.dtype) * du, None, None,
+                None, None)
 
 
 def centroid(sim: "lbm3.Lbm3", angles: torch.Tensor, u_in: torch.Tensor, rho0, nsteps: int,

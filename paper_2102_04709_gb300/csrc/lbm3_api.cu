@@ -237,6 +237,20 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 }
 
 constexpr int kGraphSteps = 8;
+// polls of an mbarrier before a step kernel gives up on a tile's bulk copies (a completed copy
+// takes a few microseconds; this is seconds of polling)
+constexpr int kCopyWaitPolls = 1 << 22;
+
+// Error bits that the kernels set (bit 0: a bulk tensor copy outlived its wait), read after the
+// stream has been synchronised and cleared once read, so that each timeout is reported once.
+int take_kernel_error(lbm3* h, int* bits)
+{
+    *bits = 0;
+    cudaError_t e = cudaMemcpyAsync(bits, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && *bits) e = cudaMemsetAsync(h->err_flag, 0, sizeof(int), h->stream);
+    return e == cudaSuccess ? LBM3_OK : fail(h, LBM3_ERR_CUDA, std::string("error bits: ") + cudaGetErrorString(e));
+}
 
 void drop_graphs(lbm3* h)
 {
@@ -490,6 +504,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (e == cudaSuccess) e = dmalloc((void**)&h->err_flag, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->err_flag, 0, sizeof(int));
     P.err = h->err_flag;
+    P.wait_polls = kCopyWaitPolls;
     if (e == cudaSuccess) e = dmalloc((void**)&h->widx, widx.size() * sizeof(int));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wnrm, wnrm.size() * sizeof(double));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wang, wang.size() * sizeof(float));
@@ -525,7 +540,13 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
             int dev = 0, sms = 0;
             e = cudaGetDevice(&dev);
             if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            if (e == cudaSuccess) e = f32 ? step_tma_prepare() : step_tma16_prepare();
+            // a kernel that cannot get the shared memory it needs leaves the pure tiles on the plain
+            // kernel (the same results), as when the tensor maps cannot be encoded
+            cudaError_t ep = cudaSuccess;
+            if (e == cudaSuccess) {
+                ep = f32 ? step_tma_prepare() : step_tma16_prepare();
+                if (ep != cudaSuccess) cudaGetLastError();
+            }
             // SMs left free for the wetting pass and the wall / edge tiles, which run on the side
             // stream while the persistent pure-tile kernel holds its SMs: their share of the step's
             // work, a wall or edge tile counted as two pure tiles (measured on 4096 x 2048 pillars:
@@ -533,7 +554,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
             const double wg = 2.0 * h->n_gen;
             const int spare = std::min(sms / 2, (int)std::lround(sms * wg / (wg + h->n_pure)));
             h->tma_blocks = (f32 ? kTmaBlocksPerSm : kTma16BlocksPerSm) * (sms - spare);
-            h->tma = e == cudaSuccess && sms > 0;
+            h->tma = e == cudaSuccess && ep == cudaSuccess && sms > 0;
         }
     }
     if (e != cudaSuccess) {
@@ -561,6 +582,7 @@ int lbm3_set_fields(lbm3* h, const double* rho)
     CUDA_TRY(h, cudaMallocAsync((void**)&drho, 3 * N * sizeof(double), h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(drho, rho, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->cur = 0;
+    CUDA_TRY(h, cudaMemsetAsync(h->err_flag, 0, sizeof(int), h->stream));
     launch_init(h->precision, h->P, drho, h->type, h->pop[0], h->stream);
     launch_wet_init(h->precision, h->P, h->nw, h->widx, h->pop[0], h->type, h->Cw, h->stream);
     CUDA_TRY(h, cudaMemsetAsync(h->u, 0, 2 * N * sizeof(float), h->stream));
@@ -625,6 +647,9 @@ int lbm3_fields(lbm3* h, double* rho_out, double* u_out)
     for (size_t i = 0; i < 3 * N; i++) rho_out[i] = tmp[i];
     if (u_out)
         for (size_t i = 0; i < 2 * N; i++) u_out[i] = tu[i];
+    int bits = 0;
+    if (int rc = take_kernel_error(h, &bits)) return rc;
+    if (bits & 1) return fail(h, LBM3_ERR_CUDA, "a bulk tensor copy of the step kernel did not complete in time");
     return LBM3_OK;
 }
 
@@ -636,8 +661,7 @@ int lbm3_diag(lbm3* h, double out[8])
     CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaMemcpyAsync(out, h->dout, 8 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     int bits = 0;
-    CUDA_TRY(h, cudaMemcpyAsync(&bits, h->err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (int rc = take_kernel_error(h, &bits)) return rc;
     if (bits & 1) return fail(h, LBM3_ERR_CUDA, "a bulk tensor copy of the step kernel did not complete in time");
     if (out[7] > 0.0 || !(out[6] > 0.0)) return fail(h, LBM3_ERR_DIVERGED, "non-finite or non-positive density");
     return LBM3_OK;
@@ -700,6 +724,7 @@ int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c)
     CUDA_TRY(h, cudaMallocAsync((void**)&dpost, 27 * N * sizeof(double), h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(dpost, f_post, 27 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->cur = 0;
+    CUDA_TRY(h, cudaMemsetAsync(h->err_flag, 0, sizeof(int), h->stream));
     launch_set_state(h->precision, h->P, dpost, h->type, h->pop[0], h->stream);
     CUDA_TRY(h, cudaMemcpyAsync(h->Cw, wall_c, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     CUDA_TRY(h, cudaMemsetAsync(h->u, 0, 2 * N * sizeof(float), h->stream));
@@ -821,6 +846,9 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cleanup();
     if (e != cudaSuccess) return fail(h, LBM3_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(e));
+    int bits = 0;
+    if (int rc = take_kernel_error(h, &bits)) return rc;
+    if (bits & 1) return fail(h, LBM3_ERR_CUDA, "a bulk tensor copy of the step kernel did not complete in time");
     *J_out = J;
     for (int w = 0; w < h->nw; w++)
         for (int j = 0; j < 3; j++) dJ_dangles[3 * w + j] = dang[(size_t)j * h->nw + w];
@@ -851,7 +879,22 @@ int lbm3_info(const lbm3* h, int64_t out[9])
 int lbm3_set_stream(lbm3* h, void* stream)
 {
     if (!h) return LBM3_ERR_INVALID;
-    h->stream = (cudaStream_t)stream;
+    const cudaStream_t next = (cudaStream_t)stream;
+    if (next != h->stream) {
+        // work already queued on the old stream (and the side stream, joined to it at the end of
+        // every step) comes before anything later enqueued on the new one
+        CUDA_TRY(h, cudaEventRecord(h->ev_fork, h->stream));
+        CUDA_TRY(h, cudaStreamWaitEvent(next, h->ev_fork, 0));
+    }
+    h->stream = next;
+    return LBM3_OK;
+}
+
+int lbm3_set_copy_wait_limit(lbm3* h, int32_t polls)
+{
+    if (!h) return LBM3_ERR_INVALID;
+    h->P.wait_polls = polls < 0 ? kCopyWaitPolls : polls;
+    drop_graphs(h);  // the graphs hold the old Params
     return LBM3_OK;
 }
 

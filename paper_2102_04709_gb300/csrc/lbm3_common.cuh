@@ -65,6 +65,9 @@ struct Params {
     int off_pull16o[27];
     // device word of error bits set by kernels (bit 0: a bulk tensor copy did not complete)
     int* err;
+    // polls of an mbarrier before a block gives up waiting for its tile's bulk copies (the wait
+    // that then drains the copies in flight always uses the full limit kWaitLimit)
+    int wait_polls;
 };
 
 // One population buffer.  FP32 storage: f[27][N], plane k*9+a, the post-collision populations

@@ -264,8 +264,10 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// polls of an mbarrier before a block gives up on a bulk copy (each poll may suspend the thread
-// for a short time; a completed copy takes a few microseconds)
+// polls of an mbarrier before a block gives up draining its bulk copies after a timeout (each
+// poll may suspend the thread for a short time; a completed copy takes a few microseconds); the
+// first wait for a tile's copies polls Params::wait_polls times (kWaitLimit unless lowered to
+// test the timeout path)
 constexpr int kWaitLimit = 1 << 22;
 
 // A C_SB node whose wall values are not all within kMixEps of one pure fluid: a fluid-fluid
@@ -820,7 +822,7 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
     // wait, so that none lands in a later block's shared memory
     auto wait_part = [&](uint32_t bar, int j) -> bool {
         bool ok = false;
-        for (int it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(bar, j & 1);
+        for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(bar, j & 1);
         if (!__syncthreads_or(!ok)) return true;
         if (tid == 0) {
             atomicOr(P.err, 1);
@@ -1282,7 +1284,7 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
         const int next = more ? tiles[t + gridDim.x] : 0;
         const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
         bool ok = false;
-        for (int it = 0; it < kWaitLimit && !ok; it++) ok = mbar_try_wait(bar, j & 1);
+        for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(bar, j & 1);
         if (__syncthreads_or(!ok)) {
             // the copies did not complete in time: record it, give them a second bounded wait
             // so that they do not land in a later block's shared memory, and stop

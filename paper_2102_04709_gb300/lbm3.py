@@ -28,8 +28,8 @@ LBM3_FP32, LBM3_FP16, LBM3_BF16 = 0, 1, 2
 EXPORTS = ("lbm3_create", "lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields",
            "lbm3_diag", "lbm3_n_wall", "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state",
            "lbm3_set_state", "lbm3_set_wall_angles", "lbm3_set_inflow", "lbm3_adjoint_centroid",
-           "lbm3_info", "lbm3_set_stream", "lbm3_sync", "lbm3_destroy", "lbm3_last_error",
-           "lbm3_diag_fields")
+           "lbm3_info", "lbm3_set_stream", "lbm3_set_copy_wait_limit", "lbm3_sync",
+           "lbm3_destroy", "lbm3_last_error", "lbm3_diag_fields")
 
 
 class lbm3_grid(ctypes.Structure):
@@ -77,6 +77,7 @@ def load(path: str | None = None):
     L.lbm3_adjoint_centroid.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, _D, _D, _D]
     L.lbm3_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.lbm3_set_stream.argtypes = [vp, vp]
+    L.lbm3_set_copy_wait_limit.argtypes = [vp, ctypes.c_int32]
     L.lbm3_sync.argtypes = [vp]
     L.lbm3_destroy.argtypes = [vp]
     L.lbm3_destroy.restype = None
@@ -84,7 +85,8 @@ def load(path: str | None = None):
     L.lbm3_diag_fields.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
     L.lbm3_last_error.restype = ctypes.c_char_p
     for name in ("lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields", "lbm3_diag", "lbm3_n_wall",
-                 "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state", "lbm3_set_state", "lbm3_info", "lbm3_set_stream", "lbm3_sync"):
+                 "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state", "lbm3_set_state", "lbm3_info", "lbm3_set_stream",
+                 "lbm3_set_copy_wait_limit", "lbm3_sync"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -249,6 +251,10 @@ class Lbm3:
 
     def set_stream(self, stream):
         _check(self._h, load().lbm3_set_stream(self._h, stream))
+
+    def set_copy_wait_limit(self, polls):
+        """Polls of a tile's bulk-copy mbarrier before a block gives up (< 0: the default)."""
+        _check(self._h, load().lbm3_set_copy_wait_limit(self._h, int(polls)))
 
     def sync(self):
         _check(self._h, load().lbm3_sync(self._h))

@@ -287,3 +287,42 @@ def lens_angles(rho, gap=2.5):
     au = float(np.degrees(np.arccos(np.clip(-(yu - y0) / Ru, -1.0, 1.0))))
     al = float(np.degrees(np.arccos(np.clip((yl - y0) / Rl, -1.0, 1.0))))
     return 180.0 - al, au + al, 180.0 - au
+
+
+def line_crossings(rho, solid, lines, k, level=0.5):
+    """Crossings of C_k = level along grid lines: lines = [("row", y) | ("col", x)], segments
+    touching a solid node skipped; returns [(kind, index, position)] in scan order."""
+    rho = np.asarray(rho, dtype=np.float64)
+    c = rho[k] / np.maximum(rho.sum(0), 1e-30)
+    s = np.asarray(solid).astype(bool)
+    out = []
+    for kind, idx in lines:
+        v, sl = (c[idx], s[idx]) if kind == "row" else (c[:, idx], s[:, idx])
+        for j in range(len(v) - 1):
+            if not sl[j] and not sl[j + 1] and (v[j] - level) * (v[j + 1] - level) < 0:
+                out.append((kind, idx, j + (v[j] - level) / (v[j] - v[j + 1])))
+    return out
+
+
+def cylinder_contact_angles(rho, solid, xc0, yc0, surf, gap=3.0):
+    """Contact angles (deg, inside the droplet) of a Janus droplet (fluid 0 left, fluid 2 right,
+    in fluid 1) sitting on a cylinder of wall radius surf centred at (xc0, yc0): a circle is
+    fitted to each side's outer interface (the C_1 = 1/2 contour left and right of the internal
+    interface, points more than gap from the wall), and the angle between that circle and the
+    wall at their intersection follows from the law of cosines (Eq.23's triangle of the two
+    centres and a contact point)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    C = rho / np.maximum(rho.sum(0), 1e-30)
+    s = np.asarray(solid).astype(bool)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        phi = np.where(C[1] < 0.5, C[0] / (C[0] + C[2]), np.nan)
+    xm = contour_points(phi, s)[:, 0].mean()
+    p = contour_points(C[1], s)
+    p = p[np.hypot(p[:, 0] - xc0, p[:, 1] - yc0) > surf + gap]
+    out = []
+    for side in (p[p[:, 0] < xm], p[p[:, 0] > xm]):
+        xc, yc, R = fit_circle(side)
+        D = float(np.hypot(xc - xc0, yc - yc0))
+        c = (surf ** 2 + R * R - D * D) / (2.0 * surf * R)
+        out.append(float(np.degrees(np.arccos(np.clip(c, -1.0, 1.0)))))
+    return out[0], out[1]

@@ -167,3 +167,26 @@ def test_adjoint_leaves_final_state(gpu):
     ra, _ = a.fields()
     rb, _ = b.fields()
     assert np.array_equal(ra, rb)
+
+
+def test_adjoint_gradients_follow_input_device(gpu):
+    """The torch.autograd.Function returns each gradient on its input's device and in its dtype:
+    angles and u_in as CUDA tensors give CUDA gradients equal to those of CPU inputs."""
+    import torch
+    from paper_2102_04709_gb300 import adjoint
+
+    w = pillar_case()
+    sim = gpu.Lbm3.from_workload(w)
+    idx = sim.wall_nodes()
+    a0 = w.angles.reshape(-1, 3)[idx].copy()
+    grads = []
+    for dev in ("cpu", "cuda"):
+        ang = torch.tensor(a0, dtype=torch.float64, device=dev, requires_grad=True)
+        u = torch.tensor(w.u_in, dtype=torch.float64, device=dev, requires_grad=True)
+        J = adjoint.centroid(sim, ang, u, w.rho, 40, 16)
+        (2.0 * J).backward()
+        assert ang.grad.device.type == dev and u.grad.device.type == dev
+        assert ang.grad.dtype == torch.float64
+        grads.append((ang.grad.cpu().numpy(), u.grad.item()))
+    assert np.array_equal(grads[0][0], grads[1][0]) and grads[0][1] == grads[1][1]
+    sim.close()

@@ -78,3 +78,43 @@ def test_step_before_fields_is_refused(gpu):
     sim.step(1)
     assert sim.diag()[7] == 0
     sim.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp32", "fp16"])
+def test_copy_wait_timeout_is_reported_once_and_recoverable(gpu, precision):
+    """The bounded wait of the bulk-copy step kernels, made to run out: with a wait limit of 0
+    polls every block of the pure-tile kernel gives up at its first tile, sets the error bit,
+    drains the copies it issued (full limit) and returns.  lbm3_diag then reports LBM3_ERR_CUDA
+    once; after a clean lbm3_set_state and the default limit the run steps on and matches an
+    untouched run bit for bit.  Nothing faults or hangs: the drained copies have completed
+    before each block exits, and the skipped tiles only leave old values in the output buffer."""
+    w = W.pillars(nx=200, ny=96, count=3, r_lo=8.0, r_hi=12.0, x_lo=90.0, x_hi=180.0, gap=6.0,
+                  seed=5, drop=(50.0, 48.0), r_core=10.0, r_shell=18.0, u_in=0.02)
+    assert w.nx % 8 == 0
+    sim = gpu.Lbm3.from_workload(w, precision=precision)
+    assert sim.info()["tma"], "the bulk-copy path must be active for this test"
+    sim.step(10)
+    f, c = sim.get_state()
+    sim.set_copy_wait_limit(0)
+    sim.step(3)
+    with pytest.raises(gpu.Lbm3Error) as e:
+        sim.diag()
+    assert e.value.code == gpu.LBM3_ERR_CUDA and "bulk tensor copy" in str(e.value)
+    sim.diag(check=False)                      # reported once, then cleared
+    sim.set_copy_wait_limit(-1)
+    sim.set_state(f, c)
+    sim.step(20)
+    sim.diag()
+    ref = gpu.Lbm3.from_workload(w, precision=precision)
+    ref.step(10)
+    ref.set_state(*ref.get_state())
+    ref.step(20)
+    assert np.array_equal(sim.fields()[0], ref.fields()[0])
+    # the error bit also reaches lbm3_fields
+    sim.set_copy_wait_limit(0)
+    sim.step(1)
+    with pytest.raises(gpu.Lbm3Error) as e:
+        sim.fields()
+    assert e.value.code == gpu.LBM3_ERR_CUDA
+    sim.close()
+    ref.close()
