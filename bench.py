@@ -11,7 +11,7 @@ Prints ONE JSON line (rank 0):  value = whole-job MLUPS (grid nodes x steps / s 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the FP64 CPU oracle (the only reference this paper has) on the box's
-host cores, one 128 x 128 window of the same workload per step.
+host cores (OpenMP), one 512 x 512 window of the same workload per step.
 """
 from __future__ import annotations
 
@@ -31,8 +31,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 FALLBACK_HBM_GBS = 6800.0
+E2E_LONG = 2000   # steps of the second end-to-end timing when the run itself is shorter
 PRECISIONS = {"fp32": 0, "fp16": 1, "bf16": 2}
 WORKLOAD = "pillars_4096x2048_theta90"
+REF_WINDOW = 512
 
 
 def parse():
@@ -197,16 +199,24 @@ def oracle_window(w, x0, y0, size):
                       w.sigma, w.nu, w.beta0)
 
 
-def cpu_baseline(w, steps=2):
-    """The FP64 oracle on `steps` full timesteps of the whole workload, one host core."""
+def cpu_baseline(w, steps_all=8, steps_one=2):
+    """The FP64 oracle on full timesteps of the whole workload: on every host core (OpenMP over
+    the per-node loops; the headline figure) and on one core."""
     from oracle import oracle as ora
-    o = ora.Oracle.from_workload(w)
+    cores = ora.host_threads()
+    o = ora.Oracle.from_workload(w, threads=cores)
+    o.step(1)                                   # first touch of the arrays on every thread
     t = time.perf_counter()
-    o.step(steps)
-    dt = time.perf_counter() - t
-    return {"value": w.n * steps / dt / 1e6, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{steps} full timesteps of {w.name} ({w.nx}x{w.ny}) by the FP64 oracle, "
-                      f"{dt:.1f} s, single-threaded C"}
+    o.step(steps_all)
+    dt_all = time.perf_counter() - t
+    o.set_threads(1)
+    t = time.perf_counter()
+    o.step(steps_one)
+    dt_one = time.perf_counter() - t
+    return {"value": w.n * steps_all / dt_all / 1e6, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "sample": f"{steps_all} full timesteps of {w.name} ({w.nx}x{w.ny}) by the FP64 oracle on "
+                      f"{cores} OpenMP threads, {dt_all:.1f} s; then {steps_one} on one core, {dt_one:.1f} s",
+            "single_core_value": w.n * steps_one / dt_one / 1e6}
 
 
 def run_reference(args):
@@ -217,8 +227,11 @@ def run_reference(args):
     from paper_2102_04709_gb300 import workloads as W
     ora.build()
     w = W.config4(args.theta)
-    win = oracle_window(w, 336, 960, 128)
-    o = ora.Oracle.from_workload(win)
+    # a 512 x 512 window holding the droplet's front and pillars, periodic on both sides (the
+    # same work per node as the full grid), on every host core
+    win = oracle_window(w, 400, 768, REF_WINDOW)
+    cores = ora.host_threads()
+    o = ora.Oracle.from_workload(win, threads=cores)
     o.step(args.warmup)
     t = time.perf_counter()
     o.step(args.steps)
@@ -228,11 +241,13 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "128x128 window of the workload per step",
+            "config": {"workload": WORKLOAD, "sample": f"{REF_WINDOW}x{REF_WINDOW} window of the "
+                                                          "workload per step",
                        "storage": "fp64 (oracle)"},
-            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": 1, "kind": "oracle",
-                             "sample": "one timestep of a 128x128 window of the pillar workload "
-                                       "per step, FP64 oracle, single-threaded C"},
+            "cpu_baseline": {"value": v, "unit": "MLUPS", "cores": cores, "kind": "oracle",
+                             "sample": f"one timestep of a {REF_WINDOW}x{REF_WINDOW} window of the "
+                                       f"pillar workload per step, FP64 oracle on {cores} OpenMP "
+                                       "threads"},
             "e2e": {"value": v, "unit": "MLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -306,7 +321,22 @@ def run_ours(args):
         e2e_ms = max_over_ranks((tb - ta) * 1e3, ws, "cuda")
         e2e = {"value": job_mlups(w.n, args.steps, ws, e2e_ms), "unit": "MLUPS",
                "h2d_bytes_per_step": int(math.ceil(rho_host.nbytes / args.steps)),
-               "d2h_bytes_per_step": int(math.ceil((rho_out.nbytes + u_out.nbytes) / args.steps))}
+               "d2h_bytes_per_step": int(math.ceil((rho_out.nbytes + u_out.nbytes) / args.steps)),
+               "steps": args.steps,
+               "note": "one call sequence per run: lbm3_set_fields (H2D of the FP64 initial "
+                       "densities), lbm3_step(steps), lbm3_fields (D2H of FP64 densities and "
+                       "velocity); the copies are amortised over `steps`"}
+        if args.steps < E2E_LONG:
+            # the same sequence over a run length where the copies no longer dominate
+            barrier()
+            ta = time.perf_counter()
+            sim.set_fields(rho_host)
+            sim.step(E2E_LONG)
+            rho_out, u_out = sim.fields()
+            barrier()
+            tb = time.perf_counter()
+            e2e["long_run"] = {"steps": E2E_LONG, "value": job_mlups(
+                w.n, E2E_LONG, ws, max_over_ranks((tb - ta) * 1e3, ws, "cuda")), "unit": "MLUPS"}
 
     # the same steps through lbm3_step itself, which replays captured CUDA graphs of 8 steps and
     # records no per-launch events (the timed region above records five events per step so that
