@@ -64,6 +64,15 @@
 #define Q 9
 #define NF 3
 
+/* Scalar type of every quantity that depends on the state or on the differentiated parameters
+ * (wall angles, inflow velocity): double here.  The reference tape (lbm3_oracle_tape.cpp)
+ * compiles this same file with a reverse-mode recording type in its place, so that its
+ * gradients are those of exactly these operations.  VAL() reads a value out of either. */
+#ifndef ORA_TAPE
+typedef double real;
+#define VAL(x) (x)
+#endif
+
 /* ---- D2Q9 lattice, Section II.A (text below Eq.3) ---- */
 static const int EX[Q] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 static const int EY[Q] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -91,7 +100,8 @@ enum { LOC_IN = 0, LOC_SOLID = 1, LOC_GHOST = 2 };
 typedef struct ora {
     int nx, ny, n;
     int per_y, bc_x;
-    double u_in, rho_out;
+    real u_in;
+    double rho_out;
     double sigma[NF][NF]; /* symmetric interfacial tensions, Eq.(10) */
     double nu[NF];        /* kinematic viscosities; mu_k = rho_k^0 nu_k with rho_k^0 = 1 */
     double rho0[NF];      /* pure-fluid densities (all 1: the method assumes equal densities) */
@@ -100,15 +110,15 @@ typedef struct ora {
     double Minv[Q][Q];
     int opp[Q];
     unsigned char *solid, *cls;
-    double *theta;        /* per node: theta_01, theta_20, theta_12 (deg) = theta_rg, theta_br, theta_gb */
+    real *theta;          /* per node: theta_01, theta_20, theta_12 (deg) = theta_rg, theta_br, theta_gb */
     double *ns;           /* outward unit normal at C_SB nodes (minus Eq.19) */
-    double *f, *fnew;     /* [k][a][node] post-streaming populations */
-    double *rho;          /* [k][node] */
-    double *C;            /* [k][node]: fluid nodes from O1, C_SB nodes from O4 */
-    double *Cw;           /* [k][node]: C_SB values of the previous step (Eq.21 input) */
-    double *T;            /* [3][node]: Txx, Txy, Tyy at C_F and C_SB nodes */
-    double *Fs;           /* [2][node] */
-    double *u;            /* [2][node]: velocity of the last collision, Eq.(11) */
+    real   *f, *fnew;     /* [k][a][node] post-streaming populations */
+    real   *rho;          /* [k][node] */
+    real   *C;            /* [k][node]: fluid nodes from O1, C_SB nodes from O4 */
+    real   *Cw;           /* [k][node]: C_SB values of the previous step (Eq.21 input) */
+    real   *T;            /* [3][node]: Txx, Txy, Tyy at C_F and C_SB nodes */
+    real   *Fs;           /* [2][node] */
+    real   *u;            /* [2][node]: velocity of the last collision, Eq.(11) */
     long steps;
     int threads;          /* OpenMP threads of the per-node loops (1 unless set) */
 } ora_t;
@@ -157,7 +167,7 @@ static int is_solid_at(const ora_t* o, int X, int Y)
 }
 
 /* C_k at a located position, seen in the frame of the caller */
-static double c_at(const ora_t* o, int idx, int sw, int k)
+static real c_at(const ora_t* o, int idx, int sw, int k)
 {
     return o->C[(size_t)(sw ? swapk(k) : k) * o->n + idx];
 }
@@ -205,19 +215,19 @@ double ora_gfun(double X)
 /* ------------------------------------------------------------------------- */
 /* Eq.(1)-(9), (11): MRT collision with the forcing term at one node          */
 /* ------------------------------------------------------------------------- */
-static void matvec(const double A[Q][Q], const double* x, double* y)
+static void matvec(const double A[Q][Q], const real* x, real* y)
 {
     for (int i = 0; i < Q; i++) {
-        double s = 0.0;
+        real s = 0.0;
         for (int j = 0; j < Q; j++) s += A[i][j] * x[j];
         y[i] = s;
     }
 }
 
-static void collide_node(const double Minv[Q][Q], const double f[Q], const double Fs[2],
-                         double tau, double fdag[Q], double u[2])
+static void collide_node(const double Minv[Q][Q], const real f[Q], const real Fs[2],
+                         real tau, real fdag[Q], real u[2])
 {
-    double rho = 0.0, jx = 0.0, jy = 0.0;
+    real rho = 0.0, jx = 0.0, jy = 0.0;
     for (int a = 0; a < Q; a++) {
         rho += f[a];
         jx += f[a] * EX[a];
@@ -226,22 +236,22 @@ static void collide_node(const double Minv[Q][Q], const double f[Q], const doubl
     /* Eq.(11) */
     u[0] = (jx + 0.5 * Fs[0]) / rho;
     u[1] = (jy + 0.5 * Fs[1]) / rho;
-    double uu = u[0] * u[0] + u[1] * u[1];
-    double feq[Q], Ft[Q], d[Q], m[Q], om[Q], mF[Q], Fbar[Q];
+    real uu = u[0] * u[0] + u[1] * u[1];
+    real feq[Q], Ft[Q], d[Q], m[Q], om[Q], mF[Q], Fbar[Q];
     for (int a = 0; a < Q; a++) {
-        double eu = EX[a] * u[0] + EY[a] * u[1];
+        real eu = EX[a] * u[0] + EY[a] * u[1];
         /* Eq.(3) */
         feq[a] = rho * WQ[a] * (1.0 + eu / CS2 + eu * eu / (2.0 * CS2 * CS2) - uu / (2.0 * CS2));
         /* Eq.(9) */
-        double cx = (EX[a] - u[0]) / CS2 + eu * EX[a] / (CS2 * CS2);
-        double cy = (EY[a] - u[1]) / CS2 + eu * EY[a] / (CS2 * CS2);
+        real cx = (EX[a] - u[0]) / CS2 + eu * EX[a] / (CS2 * CS2);
+        real cy = (EY[a] - u[1]) / CS2 + eu * EY[a] / (CS2 * CS2);
         Ft[a] = WQ[a] * (cx * Fs[0] + cy * Fs[1]);
         d[a] = f[a] - feq[a];
     }
     /* Eq.(5)-(6) */
-    double s1 = 1.0 / tau;
-    double s4 = 8.0 * (2.0 - s1) / (8.0 - s1);
-    double S[Q] = {0.0, s1, s1, 0.0, s4, 0.0, s4, s1, s1};
+    real s1 = 1.0 / tau;
+    real s4 = 8.0 * (2.0 - s1) / (8.0 - s1);
+    real S[Q] = {0.0, s1, s1, 0.0, s4, 0.0, s4, s1, s1};
     /* Eq.(2): Omega = -M^-1 S M (f - f^eq) */
     matvec(MMAT, d, m);
     for (int i = 0; i < Q; i++) m[i] *= S[i];
@@ -255,12 +265,12 @@ static void collide_node(const double Minv[Q][Q], const double f[Q], const doubl
 }
 
 /* Eq.(7): rho/mu = sum_k rho_k/mu_k, mu = (tau - 1/2) rho c_s^2 */
-static double mixture_tau(const ora_t* o, const double rk[NF])
+static real mixture_tau(const ora_t* o, const real rk[NF])
 {
-    double rho = rk[0] + rk[1] + rk[2];
-    double inv = 0.0;
+    real rho = rk[0] + rk[1] + rk[2];
+    real inv = 0.0;
     for (int k = 0; k < NF; k++) inv += rk[k] / (o->rho0[k] * o->nu[k]);
-    double mu = rho / inv;
+    real mu = rho / inv;
     return mu / (rho * CS2) + 0.5;
 }
 
@@ -269,7 +279,7 @@ static double mixture_tau(const ora_t* o, const double rk[NF])
 /* ------------------------------------------------------------------------- */
 /* C_k (frame of the caller) and rho_k at position (X, Y) that is a fluid node, a C_SB
  * node or a ghost of the open boundary */
-static void state_at(const ora_t* o, int X, int Y, double c[NF], double rk[NF])
+static void state_at(const ora_t* o, int X, int Y, real c[NF], real rk[NF])
 {
     int idx, sw;
     int loc = locate(o, X, Y, &idx, &sw);
@@ -283,7 +293,7 @@ static void state_at(const ora_t* o, int X, int Y, double c[NF], double rk[NF])
 
 /* Eq.(12) on the 9 values v[a] = psi(x + e_a): g = sum_a w_a psi(x + e_a) e_a / c_s^2 (the
  * step's gradients and the ora_gradient_periodic accessor both use it) */
-static void eq12(const double v[Q], double g[2])
+static void eq12(const real v[Q], real g[2])
 {
     g[0] = g[1] = 0.0;
     for (int a = 0; a < Q; a++) {
@@ -302,11 +312,11 @@ static int no_value(const ora_t* o, int loc, int idx)
 /* grad C_k at (X, Y) by Eq.(12).  Only a C_SB centre has neighbours without a value; such a
  * neighbour P + e_a takes the value on the straight line through the opposite neighbour and
  * the centre, 2 C(P) - C(P - e_a) (the centre's own value when P - e_a has none either) */
-static void grad_at(const ora_t* o, int X, int Y, double g[NF][2])
+static void grad_at(const ora_t* o, int X, int Y, real g[NF][2])
 {
-    double c0[NF], r0[NF];
+    real c0[NF], r0[NF];
     state_at(o, X, Y, c0, r0);
-    double v[NF][Q];
+    real v[NF][Q];
     for (int k = 0; k < NF; k++) v[k][0] = c0[k];
     for (int a = 1; a < Q; a++) {
         int idx, sw;
@@ -327,23 +337,23 @@ static void grad_at(const ora_t* o, int X, int Y, double g[NF][2])
 }
 
 /* Eq.(10) tensor sum_k sum_{l!=k} (sigma_kl A_kl / 2) |G_kl| (I - n_kl n_kl) at (X, Y) */
-static void tensor_at(const ora_t* o, int X, int Y, double T[3])
+static void tensor_at(const ora_t* o, int X, int Y, real T[3])
 {
-    double c[NF], rk[NF], g[NF][2];
+    real c[NF], rk[NF], g[NF][2];
     state_at(o, X, Y, c, rk);
     grad_at(o, X, Y, g);
     T[0] = T[1] = T[2] = 0.0;
     for (int k = 0; k < NF; k++)
         for (int l = 0; l < NF; l++) {
             if (l == k) continue;
-            double Gx = c[l] * g[k][0] - c[k] * g[l][0];
-            double Gy = c[l] * g[k][1] - c[k] * g[l][1];
-            double G2 = Gx * Gx + Gy * Gy;
+            real Gx = c[l] * g[k][0] - c[k] * g[l][0];
+            real Gy = c[l] * g[k][1] - c[k] * g[l][1];
+            real G2 = Gx * Gx + Gy * Gy;
             if (G2 <= G2_EPS) continue;
-            double Gn = sqrt(G2);
-            double nx = Gx / Gn, ny = Gy / Gn;
-            double A = fmin(1e6 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);
-            double s = 0.5 * o->sigma[k][l] * A * Gn;
+            real Gn = sqrt(G2);
+            real nx = Gx / Gn, ny = Gy / Gn;
+            real A = fmin(1e6 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);
+            real s = 0.5 * o->sigma[k][l] * A * Gn;
             T[0] += s * (1.0 - nx * nx);
             T[1] += s * (0.0 - nx * ny);
             T[2] += s * (1.0 - ny * ny);
@@ -362,9 +372,10 @@ static int fluid_at(const ora_t* o, int X, int Y, int* idx, int* sw)
 }
 
 /* w-weighted mean of C_k over the fluid D2Q9 neighbours of node (px, py) */
-static double neighbour_mean(const ora_t* o, int px, int py, int k)
+static real neighbour_mean(const ora_t* o, int px, int py, int k)
 {
-    double s = 0.0, ws = 0.0;
+    real s = 0.0;
+    double ws = 0.0;
     for (int a = 1; a < Q; a++) {
         int idx, sw;
         if (fluid_at(o, px + EX[a], py + EY[a], &idx, &sw)) {
@@ -377,15 +388,15 @@ static double neighbour_mean(const ora_t* o, int px, int py, int k)
 
 /* March P + t d (t > 0) across the grid lines; return 1 and C_D at the first crossing whose
  * bracketing nodes are both in C_F. */
-static int march(const ora_t* o, int px, int py, double dx, double dy, int k, double* CD)
+static int march(const ora_t* o, int px, int py, real dx, real dy, int k, real* CD)
 {
     int sx = dx > 0 ? 1 : -1, sy = dy > 0 ? 1 : -1;
     int useX = fabs(dx) > 1e-14, useY = fabs(dy) > 1e-14;
     int Xn = px + sx, Yn = py + sy;
-    double tv = useX ? (Xn - px) / dx : INFINITY;
-    double th = useY ? (Yn - py) / dy : INFINITY;
+    real tv = useX ? (Xn - px) / dx : INFINITY;
+    real th = useY ? (Yn - py) / dy : INFINITY;
     for (;;) {
-        double t = fmin(tv, th);
+        real t = fmin(tv, th);
         if (!(t <= RAY_TMAX)) return 0;
         int hitV = (tv - t) <= RAY_EPS, hitH = (th - t) <= RAY_EPS;
         int idx, sw, idx2, sw2;
@@ -397,7 +408,7 @@ static int march(const ora_t* o, int px, int py, double dx, double dy, int k, do
             }
         } else if (hitV) {
             /* vertical grid line x = Xn: interpolate between the lower and upper node */
-            double ys = py + t * dy;
+            real ys = py + t * dy;
             double Yr = floor(ys + 0.5);
             if (fabs(ys - Yr) < RAY_EPS) {
                 if (fluid_at(o, Xn, (int)Yr, &idx, &sw)) {
@@ -406,16 +417,16 @@ static int march(const ora_t* o, int px, int py, double dx, double dy, int k, do
                 }
             } else {
                 int Y0 = (int)floor(ys);
-                double fr = ys - Y0;
+                real fr = ys - Y0;
                 if (fluid_at(o, Xn, Y0, &idx, &sw) && fluid_at(o, Xn, Y0 + 1, &idx2, &sw2)) {
-                    double Clow = c_at(o, idx, sw, k), Cup = c_at(o, idx2, sw2, k);
+                    real Clow = c_at(o, idx, sw, k), Cup = c_at(o, idx2, sw2, k);
                     *CD = Clow + fr * (Cup - Clow);
                     return 1;
                 }
             }
         } else {
             /* horizontal grid line y = Yn: interpolate between the left and right node */
-            double xs = px + t * dx;
+            real xs = px + t * dx;
             double Xr = floor(xs + 0.5);
             if (fabs(xs - Xr) < RAY_EPS) {
                 if (fluid_at(o, (int)Xr, Yn, &idx, &sw)) {
@@ -424,9 +435,9 @@ static int march(const ora_t* o, int px, int py, double dx, double dy, int k, do
                 }
             } else {
                 int X0 = (int)floor(xs);
-                double fr = xs - X0;
+                real fr = xs - X0;
                 if (fluid_at(o, X0, Yn, &idx, &sw) && fluid_at(o, X0 + 1, Yn, &idx2, &sw2)) {
-                    double Clef = c_at(o, idx, sw, k), Crig = c_at(o, idx2, sw2, k);
+                    real Clef = c_at(o, idx, sw, k), Crig = c_at(o, idx2, sw2, k);
                     *CD = Clef + fr * (Crig - Clef);
                     return 1;
                 }
@@ -444,17 +455,17 @@ static int march(const ora_t* o, int px, int py, double dx, double dy, int k, do
 }
 
 /* C_P for fluid k with local contact angle theta_k (deg) at C_SB node p; Eq.(22) */
-static double wet_value(const ora_t* o, int p, int k, double theta_k, double* CD1, double* CD2)
+static real wet_value(const ora_t* o, int p, int k, real theta_k, real* CD1, real* CD2)
 {
     int px = p % o->nx, py = p / o->nx;
     double nx = o->ns[2 * (size_t)p], ny = o->ns[2 * (size_t)p + 1];
     double tx = -ny, ty = nx; /* tangent */
     /* |pi/2 - theta_k|; within 1e-6 deg of 90 both lines run along n_s */
-    double phi = fabs(90.0 - theta_k) < PHI_SNAP ? 0.0 : fabs(90.0 - theta_k) * (M_PI / 180.0);
-    double cphi = cos(phi), sphi = sin(phi);
-    double d1x = cphi * nx + sphi * tx, d1y = cphi * ny + sphi * ty;
-    double d2x = cphi * nx - sphi * tx, d2y = cphi * ny - sphi * ty;
-    double c1, c2;
+    real phi = fabs(90.0 - theta_k) < PHI_SNAP ? 0.0 : fabs(90.0 - theta_k) * (M_PI / 180.0);
+    real cphi = cos(phi), sphi = sin(phi);
+    real d1x = cphi * nx + sphi * tx, d1y = cphi * ny + sphi * ty;
+    real d2x = cphi * nx - sphi * tx, d2y = cphi * ny - sphi * ty;
+    real c1, c2;
     if (!march(o, px, py, d1x, d1y, k, &c1)) c1 = neighbour_mean(o, px, py, k);
     if (!march(o, px, py, d2x, d2y, k, &c2)) c2 = neighbour_mean(o, px, py, k);
     if (CD1) *CD1 = c1;
@@ -463,14 +474,14 @@ static double wet_value(const ora_t* o, int p, int k, double theta_k, double* CD
 }
 
 /* Eq.(21) with the previous C_SB values at node p */
-static void local_angles(const ora_t* o, int p, double th[2])
+static void local_angles(const ora_t* o, int p, real th[2])
 {
     size_t n = o->n;
-    double Cr = o->Cw[p], Cg = o->Cw[n + p], Cb = o->Cw[2 * n + p];
-    double t_rg = o->theta[3 * (size_t)p + 0];
-    double t_br = o->theta[3 * (size_t)p + 1];
-    double t_gb = o->theta[3 * (size_t)p + 2];
-    double t_rb = 180.0 - t_br, t_gr = 180.0 - t_rg; /* theta_lk = pi - theta_kl */
+    real Cr = o->Cw[p], Cg = o->Cw[n + p], Cb = o->Cw[2 * n + p];
+    real t_rg = o->theta[3 * (size_t)p + 0];
+    real t_br = o->theta[3 * (size_t)p + 1];
+    real t_gb = o->theta[3 * (size_t)p + 2];
+    real t_rb = 180.0 - t_br, t_gr = 180.0 - t_rg; /* theta_lk = pi - theta_kl */
     /* Eq.(21) with 1 - C_r = C_b + C_g (the fractions sum to 1), written as a convex combination
      * so that it is exact when one of the two weights vanishes; both weights below 1e-12 (the
      * 0/0 of a wall node filled by fluid k): the mean of the two angles */
@@ -492,16 +503,16 @@ static void wetting(ora_t* o)
 #pragma omp parallel for num_threads(o->threads) schedule(dynamic, 64) if (o->threads > 1)
     for (int p = 0; p < o->n; p++) {
         if (o->cls[p] != CL_SB) continue;
-        double th[2];
+        real th[2];
         local_angles(o, p, th);
-        double cr = wet_value(o, p, 0, th[0], NULL, NULL);
-        double cg = wet_value(o, p, 1, th[1], NULL, NULL);
-        double s = cr + cg;
+        real cr = wet_value(o, p, 0, th[0], NULL, NULL);
+        real cg = wet_value(o, p, 1, th[1], NULL, NULL);
+        real s = cr + cg;
         if (s > 1.0) {
             cr /= s;
             cg /= s;
         }
-        double cb = fmax(0.0, 1.0 - cr - cg);
+        real cb = fmax(0.0, 1.0 - cr - cg);
         o->C[p] = cr;
         o->C[n + p] = cg;
         o->C[2 * n + p] = cb;
@@ -623,17 +634,17 @@ ora_t* ora_create(int nx, int ny, int per_y, int bc_x, double u_in, double rho_o
     o->solid = (unsigned char*)malloc(n);
     o->cls = (unsigned char*)malloc(n);
     memcpy(o->solid, solid, n);
-    o->theta = (double*)malloc(3 * n * sizeof(double));
-    memcpy(o->theta, angles_deg, 3 * n * sizeof(double));
+    o->theta = (real*)malloc(3 * n * sizeof(real));
+    for (size_t j = 0; j < 3 * n; j++) o->theta[j] = angles_deg[j];
     o->ns = (double*)calloc(2 * n, sizeof(double));
-    o->f = (double*)calloc((size_t)NF * Q * n, sizeof(double));
-    o->fnew = (double*)calloc((size_t)NF * Q * n, sizeof(double));
-    o->rho = (double*)calloc(NF * n, sizeof(double));
-    o->C = (double*)calloc(NF * n, sizeof(double));
-    o->Cw = (double*)calloc(NF * n, sizeof(double));
-    o->T = (double*)calloc(3 * n, sizeof(double));
-    o->Fs = (double*)calloc(2 * n, sizeof(double));
-    o->u = (double*)calloc(2 * n, sizeof(double));
+    o->f = (real*)calloc((size_t)NF * Q * n, sizeof(real));
+    o->fnew = (real*)calloc((size_t)NF * Q * n, sizeof(real));
+    o->rho = (real*)calloc(NF * n, sizeof(real));
+    o->C = (real*)calloc(NF * n, sizeof(real));
+    o->Cw = (real*)calloc(NF * n, sizeof(real));
+    o->T = (real*)calloc(3 * n, sizeof(real));
+    o->Fs = (real*)calloc(2 * n, sizeof(real));
+    o->u = (real*)calloc(2 * n, sizeof(real));
     o->threads = 1;
     classify(o);
     normals(o);
@@ -655,9 +666,9 @@ static void densities(ora_t* o)
 #pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (size_t i = 0; i < n; i++) {
         if (o->solid[i]) continue;
-        double r = 0.0;
+        real r = 0.0;
         for (int k = 0; k < NF; k++) {
-            double s = 0.0;
+            real s = 0.0;
             for (int a = 0; a < Q; a++) s += o->f[((size_t)k * Q + a) * n + i];
             o->rho[k * n + i] = s;
             r += s;
@@ -666,7 +677,7 @@ static void densities(ora_t* o)
     }
 }
 
-static void zou_he(ora_t* o, double* F);
+static void zou_he(ora_t* o, real* F);
 
 /* rest equilibrium f_ak = w_a rho_k, taken as a post-streaming state (so the open-boundary
  * populations are completed by Zou-He as after any streaming step); lagged C_SB values =
@@ -674,8 +685,8 @@ static void zou_he(ora_t* o, double* F);
 void ora_set_fields(ora_t* o, const double* rho_in)
 {
     size_t n = o->n;
-    memset(o->f, 0, sizeof(double) * NF * Q * n);
-    memset(o->u, 0, sizeof(double) * 2 * n);
+    memset(o->f, 0, sizeof(real) * NF * Q * n);
+    memset(o->u, 0, sizeof(real) * 2 * n);
     for (size_t i = 0; i < n; i++) {
         if (o->solid[i]) continue;
         for (int k = 0; k < NF; k++)
@@ -695,21 +706,21 @@ void ora_set_fields(ora_t* o, const double* rho_in)
 
 /* O10 tail: Zou-He non-equilibrium bounce-back on the open columns of the post-streaming
  * populations F */
-static void zou_he(ora_t* o, double* F)
+static void zou_he(ora_t* o, real* F)
 {
     size_t n = o->n;
     for (int y = 0; y < o->ny; y++) {
         /* velocity inlet, x = 0: unknown a = 1, 5, 8 */
         size_t i = (size_t)y * o->nx;
-        double f[Q];
+        real f[Q];
         for (int a = 0; a < Q; a++) f[a] = F[(0 * Q + a) * n + i] + F[(1 * Q + a) * n + i] + F[(2 * Q + a) * n + i];
-        double U = o->u_in;
-        double rho = (f[0] + f[2] + f[4] + 2.0 * (f[3] + f[6] + f[7])) / (1.0 - U);
-        double g1 = f[3] + 2.0 / 3.0 * rho * U;
-        double g5 = f[7] - 0.5 * (f[2] - f[4]) + 1.0 / 6.0 * rho * U;
-        double g8 = f[6] + 0.5 * (f[2] - f[4]) + 1.0 / 6.0 * rho * U;
+        real U = o->u_in;
+        real rho = (f[0] + f[2] + f[4] + 2.0 * (f[3] + f[6] + f[7])) / (1.0 - U);
+        real g1 = f[3] + 2.0 / 3.0 * rho * U;
+        real g5 = f[7] - 0.5 * (f[2] - f[4]) + 1.0 / 6.0 * rho * U;
+        real g8 = f[6] + 0.5 * (f[2] - f[4]) + 1.0 / 6.0 * rho * U;
         int un[3] = {1, 5, 8};
-        double gv[3] = {g1, g5, g8};
+        real gv[3] = {g1, g5, g8};
         for (int j = 0; j < 3; j++) {
             F[(0 * Q + un[j]) * n + i] = 0.0;
             F[(1 * Q + un[j]) * n + i] = 0.0;
@@ -719,19 +730,19 @@ static void zou_he(ora_t* o, double* F)
         i = (size_t)y * o->nx + (o->nx - 1);
         for (int a = 0; a < Q; a++) f[a] = F[(0 * Q + a) * n + i] + F[(1 * Q + a) * n + i] + F[(2 * Q + a) * n + i];
         double ro = o->rho_out;
-        double ux = -1.0 + (f[0] + f[2] + f[4] + 2.0 * (f[1] + f[5] + f[8])) / ro;
-        double h3 = f[1] - 2.0 / 3.0 * ro * ux;
-        double h7 = f[5] + 0.5 * (f[2] - f[4]) - 1.0 / 6.0 * ro * ux;
-        double h6 = f[8] - 0.5 * (f[2] - f[4]) - 1.0 / 6.0 * ro * ux;
+        real ux = -1.0 + (f[0] + f[2] + f[4] + 2.0 * (f[1] + f[5] + f[8])) / ro;
+        real h3 = f[1] - 2.0 / 3.0 * ro * ux;
+        real h7 = f[5] + 0.5 * (f[2] - f[4]) - 1.0 / 6.0 * ro * ux;
+        real h6 = f[8] - 0.5 * (f[2] - f[4]) - 1.0 / 6.0 * ro * ux;
         int kn[6] = {0, 1, 2, 4, 5, 8};
-        double part[NF], tot = 0.0;
+        real part[NF], tot = 0.0;
         for (int k = 0; k < NF; k++) {
             part[k] = 0.0;
             for (int j = 0; j < 6; j++) part[k] += F[((size_t)k * Q + kn[j]) * n + i];
             tot += part[k];
         }
         int uo[3] = {3, 6, 7};
-        double hv[3] = {h3, h6, h7};
+        real hv[3] = {h3, h6, h7};
         for (int j = 0; j < 3; j++)
             for (int k = 0; k < NF; k++) F[((size_t)k * Q + uo[j]) * n + i] = hv[j] * part[k] / tot;
     }
@@ -739,10 +750,10 @@ static void zou_he(ora_t* o, double* F)
 
 /* Eq.(14): segregation parameters beta_kl of a node with densities rho_k (beta_kk = 0); the
  * recolouring of the step and the ora_beta accessor both take them from here */
-static void segregation(const ora_t* o, const double rk[NF], double beta[NF][NF])
+static void segregation(const ora_t* o, const real rk[NF], real beta[NF][NF])
 {
-    double rho = rk[0] + rk[1] + rk[2];
-    double trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);
+    real rho = rk[0] + rk[1] + rk[2];
+    real trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);
     for (int k = 0; k < NF; k++)
         for (int l = 0; l < NF; l++) beta[k][l] = (k == l) ? 0.0 : o->beta0 + o->beta0 * trip * o->gX[k][l];
 }
@@ -760,7 +771,7 @@ static void one_step(ora_t* o)
         for (int x = 0; x < o->nx; x++) {
             int i = y * o->nx + x;
             if (o->cls[i] == CL_SI) continue;
-            double T[3];
+            real T[3];
             tensor_at(o, x, y, T);
             for (int c = 0; c < 3; c++) o->T[c * n + i] = T[c];
         }
@@ -769,11 +780,11 @@ static void one_step(ora_t* o)
         for (int x = 0; x < o->nx; x++) {
             int i = y * o->nx + x;
             if (o->solid[i]) continue;
-            double Fx = 0.0, Fy = 0.0;
+            real Fx = 0.0, Fy = 0.0;
             for (int a = 1; a < Q; a++) {
                 int idx, sw;
                 int loc = locate(o, x + EX[a], y + EY[a], &idx, &sw);
-                double T[3];
+                real T[3];
                 if (loc == LOC_GHOST) {
                     tensor_at(o, x + EX[a], y + EY[a], T);
                 } else {
@@ -788,13 +799,13 @@ static void one_step(ora_t* o)
         }
     /* O7-O9 per fluid node: collision, then recolouring; results into fnew in place of
      * the post-collision populations of the node (streamed below) */
-    double* fdd = (double*)malloc(sizeof(double) * NF * Q * n);
+    real* fdd = (real*)malloc(sizeof(real) * NF * Q * n);
 #pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
             int i = y * o->nx + x;
             if (o->solid[i]) continue;
-            double f[Q], rk[NF], rho = 0.0;
+            real f[Q], rk[NF], rho = 0.0;
             for (int a = 0; a < Q; a++) {
                 f[a] = 0.0;
                 for (int k = 0; k < NF; k++) f[a] += o->f[((size_t)k * Q + a) * n + i];
@@ -803,44 +814,44 @@ static void one_step(ora_t* o)
                 rk[k] = o->rho[k * n + i];
                 rho += rk[k];
             }
-            double Fs[2] = {o->Fs[i], o->Fs[n + i]}, u[2], fdag[Q];
-            double tau = mixture_tau(o, rk);
+            real Fs[2] = {o->Fs[i], o->Fs[n + i]}, u[2], fdag[Q];
+            real tau = mixture_tau(o, rk);
             collide_node(o->Minv, f, Fs, tau, fdag, u);
             o->u[i] = u[0];
             o->u[n + i] = u[1];
             /* Eq.(13)-(15) */
-            double g[NF][2], c[NF];
+            real g[NF][2], c[NF];
             grad_at(o, x, y, g);
             for (int k = 0; k < NF; k++) c[k] = o->C[k * n + i];
-            double nkl[NF][NF][2];
+            real nkl[NF][NF][2];
             for (int k = 0; k < NF; k++)
                 for (int l = 0; l < NF; l++) {
                     nkl[k][l][0] = nkl[k][l][1] = 0.0;
                     if (k == l) continue;
-                    double Gx = c[l] * g[k][0] - c[k] * g[l][0];
-                    double Gy = c[l] * g[k][1] - c[k] * g[l][1];
-                    double G2 = Gx * Gx + Gy * Gy;
+                    real Gx = c[l] * g[k][0] - c[k] * g[l][0];
+                    real Gy = c[l] * g[k][1] - c[k] * g[l][1];
+                    real G2 = Gx * Gx + Gy * Gy;
                     if (G2 <= G2_EPS) continue;
-                    double Gn = sqrt(G2);
+                    real Gn = sqrt(G2);
                     nkl[k][l][0] = Gx / Gn;
                     nkl[k][l][1] = Gy / Gn;
                 }
-            double beta_kl[NF][NF];
+            real beta_kl[NF][NF];
             segregation(o, rk, beta_kl);
             for (int k = 0; k < NF; k++)
                 for (int a = 0; a < Q; a++) {
-                    double v = rk[k] / rho * fdag[a];
+                    real v = rk[k] / rho * fdag[a];
                     for (int l = 0; l < NF; l++) {
                         if (l == k) continue;
-                        double beta = beta_kl[k][l];
-                        double ne = nkl[k][l][0] * EX[a] + nkl[k][l][1] * EY[a];
+                        real beta = beta_kl[k][l];
+                        real ne = nkl[k][l][0] * EX[a] + nkl[k][l][1] * EY[a];
                         v += beta * WQ[a] * rk[k] * rk[l] / rho * ne;
                     }
                     fdd[((size_t)k * Q + a) * n + i] = v;
                 }
         }
     /* O10: streaming, Eq.(16) */
-    memset(o->fnew, 0, sizeof(double) * NF * Q * n);
+    memset(o->fnew, 0, sizeof(real) * NF * Q * n);
 #pragma omp parallel for num_threads(o->threads) schedule(static) if (o->threads > 1)
     for (int y = 0; y < o->ny; y++)
         for (int x = 0; x < o->nx; x++) {
@@ -850,7 +861,7 @@ static void one_step(ora_t* o)
                 int idx, sw;
                 int loc = locate(o, x + EX[a], y + EY[a], &idx, &sw);
                 for (int k = 0; k < NF; k++) {
-                    double v = fdd[((size_t)k * Q + a) * n + i];
+                    real v = fdd[((size_t)k * Q + a) * n + i];
                     if (loc == LOC_SOLID || (loc == LOC_IN && o->solid[idx])) {
                         /* halfway bounce-back */
                         o->fnew[((size_t)k * Q + o->opp[a]) * n + i] = v;
@@ -863,7 +874,7 @@ static void one_step(ora_t* o)
         }
     if (o->bc_x == BC_ZOUHE) zou_he(o, o->fnew);
     free(fdd);
-    double* t = o->f;
+    real* t = o->f;
     o->f = o->fnew;
     o->fnew = t;
     o->steps++;
@@ -883,9 +894,9 @@ void ora_fields(ora_t* o, double* rho_out, double* u_out)
     size_t n = o->n;
     densities(o);
     for (size_t i = 0; i < n; i++)
-        for (int k = 0; k < NF; k++) rho_out[k * n + i] = o->solid[i] ? 0.0 : o->rho[k * n + i];
+        for (int k = 0; k < NF; k++) rho_out[k * n + i] = o->solid[i] ? 0.0 : VAL(o->rho[k * n + i]);
     if (u_out)
-        for (size_t i = 0; i < 2 * n; i++) u_out[i] = o->u[i];
+        for (size_t i = 0; i < 2 * n; i++) u_out[i] = VAL(o->u[i]);
 }
 
 /* masses, x- and y-moments of fluid 0, max|u|, min rho, non-finite count */
@@ -899,14 +910,15 @@ void ora_diag(ora_t* o, double out[8])
         if (o->solid[i]) continue;
         double r = 0.0;
         for (int k = 0; k < NF; k++) {
-            double v = o->rho[k * n + i];
+            double v = VAL(o->rho[k * n + i]);
             out[k] += v;
             r += v;
             if (!isfinite(v)) out[7] += 1.0;
         }
-        out[3] += (double)(i % o->nx) * o->rho[i];
-        out[4] += (double)(i / o->nx) * o->rho[i];
-        double um = sqrt(o->u[i] * o->u[i] + o->u[n + i] * o->u[n + i]);
+        out[3] += (double)(i % o->nx) * VAL(o->rho[i]);
+        out[4] += (double)(i / o->nx) * VAL(o->rho[i]);
+        double ux = VAL(o->u[i]), uy = VAL(o->u[n + i]);
+        double um = sqrt(ux * ux + uy * uy);
         if (um > out[5]) out[5] = um;
         if (r < out[6]) out[6] = r;
     }
@@ -939,6 +951,7 @@ int ora_check(ora_t* o)
     return 0;
 }
 
+#ifndef ORA_TAPE
 /* ---- accessors used by the pinning tests ---- */
 void ora_get_f(ora_t* o, double* out) { memcpy(out, o->f, sizeof(double) * NF * Q * o->n); }
 void ora_set_f(ora_t* o, const double* in) { memcpy(o->f, in, sizeof(double) * NF * Q * o->n); }
@@ -1021,3 +1034,4 @@ void ora_gradient_at(ora_t* o, const double* Cfield, int x, int y, double* g)
         g[2 * k + 1] = gg[k][1];
     }
 }
+#endif /* ORA_TAPE */

@@ -14,7 +14,10 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm3_oracle.c")
 _LIB = os.path.join(_HERE, "liblbm3_oracle.so")
+_TAPE_SRC = os.path.join(_HERE, "lbm3_oracle_tape.cpp")
+_TAPE_LIB = os.path.join(_HERE, "liblbm3_oracle_tape.so")
 _lib = None
+_tape = None
 
 _D = ctypes.POINTER(ctypes.c_double)
 _U8 = ctypes.POINTER(ctypes.c_uint8)
@@ -32,6 +35,51 @@ def build(force: bool = False) -> str:
             subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
+
+
+def build_tape(force: bool = False) -> str:
+    """Compile the reference tape: the oracle's source again, with a recording scalar type, and
+    its reverse sweep (g++, portable flags)."""
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_TAPE_SRC))
+    if force or not os.path.exists(_TAPE_LIB) or os.path.getmtime(_TAPE_LIB) < newest:
+        tmp = _TAPE_LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-D_GNU_SOURCE", "-fPIC", "-shared",
+                               "-ffp-contract=off", "-Wno-unknown-pragmas", "-o", tmp, _TAPE_SRC])
+        os.replace(tmp, _TAPE_LIB)
+    return _TAPE_LIB
+
+
+def tape_lib():
+    global _tape
+    if _tape is None:
+        build_tape()
+        T = ctypes.CDLL(_TAPE_LIB)
+        T.tape_centroid_gradient.restype = ctypes.c_int
+        T.tape_centroid_gradient.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_double, ctypes.c_double, _U8, _D, _D, _D,
+                                             ctypes.c_double, _D, ctypes.c_int, _D, _D, _D]
+        _tape = T
+    return _tape
+
+
+def tape_centroid_gradient(w, steps, angles=None, u_in=None):
+    """Reference tape of the oracle: (J, dJ/dangles [ny, nx, 3], dJ/du_in) for J = x-centroid of
+    fluid 0 after `steps` oracle steps of workload w from its initial densities (angles and u_in
+    default to the workload's)."""
+    ang = _c(w.angles if angles is None else angles).reshape(-1)
+    u = float(w.u_in if u_in is None else u_in)
+    solid = _c(w.solid, np.uint8).reshape(-1)
+    rho = _c(w.rho).reshape(-1)
+    J = np.zeros(1)
+    g = np.zeros(3 * w.nx * w.ny)
+    du = np.zeros(1)
+    rc = tape_lib().tape_centroid_gradient(
+        int(w.nx), int(w.ny), int(w.periodic_y), int(w.bc_x), u, float(w.rho_out),
+        solid.ctypes.data_as(_U8), _dp(ang), _dp(_c(w.sigma)), _dp(_c(w.nu)), float(w.beta0),
+        _dp(rho), int(steps), _dp(J), _dp(g), _dp(du))
+    if rc != 0:
+        raise ValueError("oracle tape: invalid configuration")
+    return float(J[0]), g.reshape(w.ny, w.nx, 3), float(du[0])
 
 
 def host_threads() -> int:

@@ -427,6 +427,10 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         for (int ty = 0; ty < nty; ty++)
             for (int tx = 0; tx < ntx; tx++) {
                 const int x0 = tx * kTX, y0 = ty * kTY;
+                const int x1 = std::min(nx, x0 + kTX), y1 = std::min(ny, y0 + kTY);
+                // a tile without a fluid node has nothing to update (solid nodes are never
+                // written and their populations never read): no block is launched for it
+                if (box(x0, y0, x1, y1) == (long long)(x1 - x0) * (y1 - y0)) continue;
                 const bool inner = x0 >= 3 && y0 >= 3 && x0 + kTX + 3 <= nx && y0 + kTY + 3 <= ny;
                 if (inner && box(x0 - 3, y0 - 3, x0 + kTX + 3, y0 + kTY + 3) == 0) {
                     tp.push_back(ty * ntx + tx);
