@@ -38,6 +38,7 @@ struct lbm3 {
     int* widx = nullptr;
     double* wnrm = nullptr;
     float* wang = nullptr;
+    WetCache* wcache = nullptr;  // [4 nw] characteristic-line crossings of the wetting lanes
     int nw = 0;
     long long n_fluid = 0;
     // tiles of the fused step kernel: pure tiles (no solid within 3 nodes, away from the domain
@@ -128,7 +129,7 @@ void release(lbm3* h)
 {
     void* ptrs[] = {h->pop[0].f, h->pop[1].f, h->pop[0].rho, h->pop[1].rho, h->pop[0].off,
                     h->pop[1].off, h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
-                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag};
+                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag, h->wcache};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->pop[0] = h->pop[1] = Pop{nullptr, nullptr, nullptr};
@@ -223,7 +224,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
                     h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (ev) cudaEventRecord(ev[2], h->side);
-    launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->side);
+    launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side);
     if (ev) cudaEventRecord(ev[3], h->side);
     launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
                 h->side);
@@ -512,6 +513,11 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     if (e == cudaSuccess) e = dmalloc((void**)&h->widx, widx.size() * sizeof(int));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wnrm, wnrm.size() * sizeof(double));
     if (e == cudaSuccess) e = dmalloc((void**)&h->wang, wang.size() * sizeof(float));
+    if (e == cudaSuccess) e = dmalloc((void**)&h->wcache, 4 * widx.size() * sizeof(WetCache));
+    if (e == cudaSuccess) {
+        reset_wet_cache(h->wcache, (int)widx.size(), nullptr);
+        e = cudaGetLastError();
+    }
     if (e == cudaSuccess) e = dmalloc((void**)&h->tiles_pure, tp.size() * sizeof(int));
     if (e == cudaSuccess) e = dmalloc((void**)&h->tiles_gen, tg.size() * sizeof(int));
     if (e == cudaSuccess && !tp.empty()) e = cudaMemcpy(h->tiles_pure, tp.data(), tp.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -553,10 +559,13 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
             }
             // SMs left free for the wetting pass and the wall / edge tiles, which run on the side
             // stream while the persistent pure-tile kernel holds its SMs: their share of the step's
-            // work, a wall or edge tile counted as two pure tiles (measured on 4096 x 2048 pillars:
-            // 39 of 152 SMs, 20.3k instead of 18.6k MLUPS with every SM given to pure tiles)
-            const double wg = 2.0 * h->n_gen;
-            const int spare = std::min(sms / 2, (int)std::lround(sms * wg / (wg + h->n_pure)));
+            // work, in units of a pure tile's SM time as measured on the 4096 x 2048 pillars (a
+            // wall or edge tile 1.8, the wetting pass 0.038 per C_SB node: 30 of 152 SMs there).
+            // LBM3_SPARE_SMS=<n> in the environment at lbm3_create sets the count instead.
+            const double wg = 1.8 * h->n_gen + 0.038 * h->nw;
+            int spare = std::min(sms / 2, (int)std::lround(sms * wg / (wg + h->n_pure)));
+            if (const char* ov = std::getenv("LBM3_SPARE_SMS"))
+                spare = std::max(0, std::min(sms - 1, std::atoi(ov)));
             h->tma_blocks = (f32 ? kTmaBlocksPerSm : kTma16BlocksPerSm) * (sms - spare);
             h->tma = e == cudaSuccess && ep == cudaSuccess && sms > 0;
         }

@@ -295,9 +295,20 @@ __device__ void pull_global(const Params& P, const S& st, const uint8_t* __restr
     if (outlet) zou_he(P, p, false);
 }
 
+// Where the characteristic line of one lane of the wetting pass (C_SB node, wetted fluid, side)
+// met the fluid for the local contact angle th of Eq.(21) it was marched with: the line depends
+// on th and the fixed geometry only, so while a node's th repeats bit for bit (every node away
+// from a moving contact line) the march is skipped and its crossing reused.  th = NaN: none yet.
+struct WetCache {
+    double th, fr;
+    int kind, ax, ay, bx, by, pad;
+};
+
 // ---- kernel launchers (lbm3_step.cu); `store` is kStoreF32 / kStoreF16 / kStoreBF16 ----
 void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
-                const float* wang, const Pop& f, const uint8_t* type, double* Cw, cudaStream_t s);
+                const float* wang, const Pop& f, const uint8_t* type, double* Cw, WetCache* cache,
+                cudaStream_t s);
+void reset_wet_cache(WetCache* cache, int nw, cudaStream_t s);
 void launch_wet_init(int store, const Params& P, int nw, const int* widx, const Pop& f,
                      const uint8_t* type, double* Cw, cudaStream_t s);
 // tile of the fused step kernel (interior nodes per CTA)

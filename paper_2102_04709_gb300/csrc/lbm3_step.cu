@@ -29,7 +29,8 @@ template <class S>
 __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const int* __restrict__ widx,
                                              const double* __restrict__ wnrm,
                                              const float* __restrict__ wang, const S st,
-                                             const uint8_t* __restrict__ type, double* __restrict__ Cw)
+                                             const uint8_t* __restrict__ type, double* __restrict__ Cw,
+                                             WetCache* __restrict__ cache)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = g >> 2;
@@ -46,14 +47,21 @@ __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const
         const double Cr = Cw[i], Cg = Cw[P.N + i], Cb = Cw[2 * P.N + i];
         const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
         th = k == 0 ? local_angle(Cb, 180.0 - t_br, Cg, t_rg) : local_angle(Cb, t_gb, Cr, 180.0 - t_rg);
-        const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
-        const double dev = fabs(90.0 - th);
-        const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
-        double sn, cs;
-        sincos(phi, &sn, &cs);
-        if (side) sn = -sn;
-        // the line makes the angle phi with n_s (tangent (-n_y, n_x))
-        cr = characteristic_line<S>(P, type, px, py, cs * nx_ - sn * ny_, cs * ny_ + sn * nx_);
+        WetCache c = cache[g];
+        if (c.th == th) {
+            // the same angle as when this lane last marched: the same line, the same crossing
+            cr = Crossing{c.kind, c.ax, c.ay, c.bx, c.by, c.fr};
+        } else {
+            const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
+            const double dev = fabs(90.0 - th);
+            const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
+            double sn, cs;
+            sincos(phi, &sn, &cs);
+            if (side) sn = -sn;
+            // the line makes the angle phi with n_s (tangent (-n_y, n_x))
+            cr = characteristic_line<S>(P, type, px, py, cs * nx_ - sn * ny_, cs * ny_ + sn * nx_);
+            cache[g] = WetCache{th, cr.fr, cr.kind, cr.ax, cr.ay, cr.bx, cr.by, 0};
+        }
     }
     double ca = 0.0, cb = 0.0;
     if (valid && cr.kind >= 1) ca = node_C(P, st, type, cr.ax, cr.ay, k);
@@ -302,6 +310,19 @@ __device__ __forceinline__ int single_fluid_or(int present)
     const int f1 = __syncthreads_or(present & 2);
     const int f2 = __syncthreads_or(present & 4);
     return (f0 != 0) + (f1 != 0) + (f2 != 0);
+}
+
+// The same count with one barrier, for the persistent kernels: each warp ORs its lanes' bits
+// into the shared word flags[j & 1] of tile iteration j, the barrier publishes them, and thread 0
+// clears the word of the next iteration (nobody writes it before the next tile's barriers).
+__device__ __forceinline__ int fluids_present(int present, int* flags, int j, int tid)
+{
+    const int w = __reduce_or_sync(0xffffffffu, present);
+    if ((tid & 31) == 0 && w) atomicOr(&flags[j & 1], w);
+    __syncthreads();
+    const int v = flags[j & 1];
+    if (tid == 0) flags[(j + 1) & 1] = 0;
+    return __popc(v & 7);
 }
 
 // F_s = div T at (rx, ry) of the stress region: Eq.(10) with the Eq.(12) derivative
@@ -787,6 +808,7 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
     __shared__ __align__(8) uint64_t s_bar[2];  // completion of copy A (planes 0..13) and B (14..26)
+    __shared__ int s_flags[2];                  // fluids present in the tile, by iteration parity
     extern __shared__ unsigned char dsm[];
     float* box = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [27][BY][BX]
     float* outb = box + NBOXP;                                                              // [27][TY][TX]
@@ -814,6 +836,7 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
         fence_mbar_init();
         issue_a(tile);
         issue_b(tile);
+        s_flags[0] = s_flags[1] = 0;
     }
     __syncthreads();
 
@@ -895,13 +918,13 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
         for (int a = 0; a < kQ; a++) f[a] = a < 5 ? q[a] + q[9 + a] : q[a];
         r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
         r1 = (q[9] + (q[10] + q[12])) + (q[11] + q[13]);
-        __syncthreads();
-        // part A is free: fetch the next tile's while part B is pulled and this tile computes
+        // the wait for part B is a barrier: past it every thread has pulled from part A, which
+        // is then free for the next tile's copy while part B is pulled and this tile computes
+        if (!wait_part(bar_b, j)) return;
         if (tid == 0 && more) {
             issue_a(next);
             last_a = j + 1;
         }
-        if (!wait_part(bar_b, j)) return;
         int present = 0;
         if (ring) {
             pull(rcx, rcy, q, kTmaPlanesA, kQ * kNF);
@@ -915,7 +938,7 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
         r1 = r1 + ((q[14] + q[16]) + (q[15] + q[17]));
         r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
         present |= store_phase(lx + 2, ly + 2, r0, r1, r2);
-        const bool mixed = single_fluid_or(present) != 1;
+        const bool mixed = fluids_present(present, s_flags, j, tid) != 1;
         if (tid == 0 && more) {
             issue_b(next);
             last_b = j + 1;
@@ -1151,13 +1174,27 @@ void with_store(int store, const Pop& p, long long N, Fn fn)
 }
 
 void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
-                const float* wang, const Pop& f, const uint8_t* type, double* Cw, cudaStream_t s)
+                const float* wang, const Pop& f, const uint8_t* type, double* Cw, WetCache* cache,
+                cudaStream_t s)
 {
     if (nw <= 0) return;
     const long long threads = 4LL * nw;
     with_store(store, f, P.N, [&](auto st) {
-        k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw);
+        k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw, cache);
     });
+}
+
+__global__ void k_wet_cache_reset(WetCache* cache, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cache[i].th = __longlong_as_double(0x7ff8000000000000LL);  // NaN: never equal
+}
+
+void reset_wet_cache(WetCache* cache, int nw, cudaStream_t s)
+{
+    if (nw <= 0) return;
+    const int n = 4 * nw;
+    k_wet_cache_reset<<<(n + 255) / 256, 256, 0, s>>>(cache, n);
 }
 
 void launch_wet_init(int store, const Params& P, int nw, const int* widx, const Pop& f,
@@ -1221,6 +1258,7 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
     __shared__ __align__(8) uint64_t s_bar;
+    __shared__ int s_flags[2];  // fluids present in the tile, by iteration parity
     extern __shared__ unsigned char dsm[];
     float* rbox = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [3][BY][BX]
     const unsigned short* obox = reinterpret_cast<const unsigned short*>(rbox + NRP);          // [24][BY][OX]
@@ -1242,6 +1280,7 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
         mbar_init(bar, 1);
         fence_mbar_init();
         issue(tile);
+        s_flags[0] = s_flags[1] = 0;
     }
     __syncthreads();
 
@@ -1330,7 +1369,7 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
             r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
             r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
         }
-        const bool mixed = single_fluid_or(present) != 1;
+        const bool mixed = fluids_present(present, s_flags, j, tid) != 1;
         // the boxes are free: fetch the next tile's while this one computes
         if (tid == 0 && more) {
             issue(next);
