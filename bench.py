@@ -430,8 +430,10 @@ def run_ours(args):
                    "max_u": float(d[5])},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                     "kernel": "k_step_tma (pure tiles, bulk tensor copies)" if info["tma"]
-                     else "k_step<pure tiles>",
+                     "kernel": {"ring": "k_step_ring (pure tiles, warp-specialised ring of bulk "
+                                        "tensor copies)",
+                                "bulk copies": "k_step_tma (pure tiles, bulk tensor copies)",
+                                "plain": "k_step<pure tiles>"}[info["pure_kernel"]],
                      "algorithmic_bytes_per_launch": bytes_launch},
         "gpu_launches": (info["step_kernels"] + info["wet_kernels"]) * args.steps,
         "clocks": clocks,

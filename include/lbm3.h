@@ -160,9 +160,11 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, dou
  * fused step per timestep (216 B per fluid node with FP32 storage, 120 B with 16-bit offsets,
  * + 1 class byte per node), out[3] = fused-step launches per timestep, out[4] = wetting launches
  * per timestep, out[5] = device bytes held by the handle, out[6] = algorithmic bytes of the
- * pure-tile launch, out[7] = nodes in pure tiles, out[8] = 1 if the pure tiles move their
- * populations with bulk tensor copies (nx a multiple of 4 and not disabled by
- * LBM3_DISABLE_TMA=1 in the environment at lbm3_create), else 0. */
+ * pure-tile launch, out[7] = nodes in pure tiles, out[8] = how the pure tiles move their
+ * populations: 0 plain loads, 1 bulk tensor copies with two blocks per SM, 2 bulk tensor copies
+ * through the warp-specialised ring (FP32 storage; LBM3_PURE_KERNEL=tma in the environment at
+ * lbm3_create selects 1 instead).  Bulk copies need nx a multiple of 4 (FP32) or 8 (16-bit
+ * offsets) and are disabled by LBM3_DISABLE_TMA=1. */
 int lbm3_info(const lbm3* h, int64_t out[9]);
 
 /* Change the stream used by later calls (cudaStream_t).  Work already enqueued by the handle

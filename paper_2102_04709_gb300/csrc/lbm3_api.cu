@@ -35,6 +35,11 @@ struct lbm3 {
     bool tma = false;
     int tma_blocks = 0;  // persistent blocks of that kernel: kTmaBlocksPerSm per SM
     CUtensorMap tm_in_a[2], tm_in_b[2], tm_out[2];
+    // FP32 pure tiles through the ring kernel (one producer warp, two consumer groups, one block
+    // per SM): tensor maps of each buffer with the whole pull box, and its block count
+    bool ring = false;
+    int ring_blocks = 0;
+    CUtensorMap tm_box[2];
     int* widx = nullptr;
     double* wnrm = nullptr;
     float* wang = nullptr;
@@ -162,6 +167,21 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
     return encode;
 }
 
+// Tensor map of one [27][ny][nx] FP32 population buffer with the whole pull box of a pure tile,
+// (kTX + 8) x (kTY + 6) x 27, for the ring kernel.
+bool make_box_map(const Params& P, float* f, CUtensorMap* box)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny, 27};
+    const cuuint64_t strides[2] = {(cuuint64_t)P.nx * sizeof(float), (cuuint64_t)P.N * sizeof(float)};
+    const cuuint32_t bx[3] = {kTX + 8, kTY + 6, 27};
+    const cuuint32_t unit[3] = {1, 1, 1};
+    return encode(box, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, bx, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_tensor_maps(const Params& P, float* f, CUtensorMap* in_a, CUtensorMap* in_b, CUtensorMap* out)
 {
     const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
@@ -213,7 +233,9 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
-    if (h->tma && h->precision == LBM3_FP32)
+    if (h->ring)
+        launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, h->tm_box[h->cur], h->stream);
+    else if (h->tma && h->precision == LBM3_FP32)
         launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
                         h->tm_in_b[h->cur], h->tm_out[1 - h->cur], h->stream);
     else if (h->tma)
@@ -568,6 +590,19 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                 spare = std::max(0, std::min(sms - 1, std::atoi(ov)));
             h->tma_blocks = (f32 ? kTmaBlocksPerSm : kTma16BlocksPerSm) * (sms - spare);
             h->tma = e == cudaSuccess && ep == cudaSuccess && sms > 0;
+            // FP32: the warp-specialised ring kernel, unless LBM3_PURE_KERNEL=tma asks for the
+            // two-blocks-per-SM kernel (both give the same results)
+            const char* pk = std::getenv("LBM3_PURE_KERNEL");
+            if (h->tma && f32 && !(pk && std::strcmp(pk, "tma") == 0)) {
+                bool rm = true;
+                for (int b = 0; b < 2 && rm; b++) rm = make_box_map(P, h->pop[b].f, &h->tm_box[b]);
+                if (rm && step_ring_prepare() == cudaSuccess) {
+                    h->ring = true;
+                    h->ring_blocks = sms - spare;
+                } else {
+                    cudaGetLastError();
+                }
+            }
         }
     }
     if (e != cudaSuccess) {
@@ -885,7 +920,7 @@ int lbm3_info(const lbm3* h, int64_t out[9])
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes
     out[6] = h->pure_fluid * per;
     out[7] = h->pure_fluid;
-    out[8] = h->tma ? 1 : 0;
+    out[8] = h->ring ? 2 : (h->tma ? 1 : 0);
     return LBM3_OK;
 }
 

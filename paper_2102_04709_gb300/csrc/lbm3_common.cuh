@@ -327,6 +327,13 @@ cudaError_t step_tma_prepare();
 cudaError_t step_tma16_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
                      const CUtensorMap& tin_a, const CUtensorMap& tin_b, const CUtensorMap& tout, cudaStream_t s);
+// pure FP32 tiles through a ring of three bulk-copy buffers, one producer warp and two consumer
+// groups per block, one block per SM (nblocks blocks): tensor map of fin with the whole pull box
+// (kTX + 8, kTY + 6, 27) over the [27][ny][nx] buffer
+size_t step_ring_smem_bytes();
+cudaError_t step_ring_prepare();
+void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
+                      const CUtensorMap& tin, cudaStream_t s);
 // pure tiles of the 16-bit storage through bulk tensor copies (persistent, nblocks blocks): tensor
 // maps of the densities (box (kTX + 8, kTY + 6, 3) of [3][ny][nx] FP32) and of the offset planes
 // (box (kTX + 16, kTY + 6, 24) of [24][ny][nx] 16-bit words)

@@ -994,6 +994,237 @@ __global__ void __launch_bounds__(TX* TY, kTmaBlocksPerSm) k_step_tma(const Para
     if (STAGE && tid == 0) bulk_wait_read0();
 }
 
+// ---- named barriers of one consumer group and a plain mbarrier arrival ----
+__device__ __forceinline__ void group_sync(int id, int nthreads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+// barrier of the group that also ORs a predicate over its threads
+__device__ __forceinline__ bool group_or(bool v, int id, int nthreads)
+{
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "bar.red.or.pred q, %2, %3, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)v), "r"(id), "r"(nthreads)
+        : "memory");
+    return r != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Pure FP32 tiles through a ring of bulk tensor copies, warp-specialised: one producer warp and
+// two consumer groups of TX x TY threads per block, one block per SM (persistent).  Tile j of the
+// block (tiles[blockIdx.x + j gridDim.x]) lands in ring buffer j % 3 -- its 27-plane pull box,
+// (TX + 8) x (TY + 6) nodes from (x0 - 4, y0 - 3), by one copy -- and is computed by group j % 2.
+// A group releases its buffer as soon as its pulls are done (one arrival per warp on the buffer's
+// "empty" barrier), and the producer refills it at once with tile j + 3, so up to three boxes are
+// in flight or waiting while the groups compute their force, collision and recolouring.  The
+// "full" barrier of tile j is full[j % 6]: its tiles j, j + 6, ... are consumed in order by the
+// same group, so a wait never meets a phase two behind (no parity aliasing).  Every wait is
+// bounded: a consumer that gives up sets the error bit and its group returns; the producer gives
+// up on a buffer that is never released, and before exiting it waits (full limit) for every copy
+// it issued, so no copy lands in the shared memory of a later block.  The arithmetic is that of
+// k_step_tma and k_step<PURE>, so the results are identical.
+constexpr int kRingBufs = 3;
+template <int TX, int TY>
+__global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params P, const int* __restrict__ tiles,
+                                                                    const int ntiles, float* __restrict__ fout,
+                                                                    float* __restrict__ uout,
+                                                                    const __grid_constant__ CUtensorMap tm_in)
+{
+    constexpr int NT = TX * TY;               // threads of a consumer group
+    constexpr int NW = NT / 32;               // warps of a consumer group
+    constexpr int CX = TX + 4, CY = TY + 4;  // phase-field region (halo 2)
+    constexpr int RX = TX + 2, RY = TY + 2;  // stress region (halo 1)
+    constexpr int BX = TX + 8, BY = TY + 6;  // pull-source box
+    constexpr int NBOX = kQ * kNF * BY * BX;
+    constexpr int NBOXP = (NBOX + 31) / 32 * 32;  // keeps every buffer 128-byte aligned
+    constexpr int NRING = CX * CY - TX * TY;
+    static_assert(NRING <= NT, "the ring of the halo-2 region must not exceed one node per thread");
+    static_assert(NT % 32 == 0, "whole warps per group");
+    __shared__ float s_ch[2][kNF][CY][CX];
+    __shared__ float s_rho[2][CY][CX];
+    __shared__ float s_txx[2][RY][RX], s_txy[2][RY][RX], s_tyy[2][RY][RX];
+    __shared__ __align__(8) uint64_t s_full[2 * kRingBufs], s_empty[kRingBufs];
+    __shared__ int s_flags[2][2];
+    extern __shared__ unsigned char dsm[];
+    float* ring = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [3][27][BY][BX]
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntx = (P.nx + TX - 1) / TX;
+    if ((int)blockIdx.x >= ntiles) return;
+    const int njobs = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    if (threadIdx.x == 0) {
+        for (int m = 0; m < 2 * kRingBufs; m++) mbar_init(smem_u32(&s_full[m]), 1);
+        for (int b = 0; b < kRingBufs; b++) mbar_init(smem_u32(&s_empty[b]), NW);
+        fence_mbar_init();
+        s_flags[0][0] = s_flags[0][1] = s_flags[1][0] = s_flags[1][1] = 0;
+    }
+    __syncthreads();
+
+    // ---------------- producer warp ----------------
+    if (warp == 2 * NW) {
+        if (lane != 0) return;
+        int issued = 0;
+        for (int j = 0; j < njobs; j++) {
+            const int b = j % kRingBufs;
+            if (j >= kRingBufs) {
+                // buffer b is free once the group that computed tile j - 3 has pulled from it
+                bool ok = false;
+                const uint32_t par = (uint32_t)((j / kRingBufs - 1) & 1);
+                for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(smem_u32(&s_empty[b]), par);
+                if (!ok) {
+                    atomicOr(P.err, 1);
+                    break;
+                }
+            }
+            const int tile = tiles[blockIdx.x + j * gridDim.x];
+            const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+            const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
+            mbar_arrive_expect_tx(full, (uint32_t)NBOX * 4u);
+            tma_load_3d(smem_u32(ring + b * NBOXP), &tm_in, x0 - 4, y0 - 3, 0, full);
+            issued = j + 1;
+        }
+        // every copy issued has landed before the block may exit
+        for (int m = 0; m < 2 * kRingBufs; m++) {
+            int last = -1;
+            for (int j = issued - 1; j >= 0 && j >= issued - 2 * kRingBufs; j--)
+                if (j % (2 * kRingBufs) == m) {
+                    last = j;
+                    break;
+                }
+            if (last < 0) continue;
+            const uint32_t par = (uint32_t)((last / (2 * kRingBufs)) & 1);
+            for (int it = 0; it < kWaitLimit && !mbar_try_wait(smem_u32(&s_full[m]), par); it++) {
+            }
+        }
+        return;
+    }
+
+    // ---------------- consumer groups ----------------
+    const int g = warp / NW;
+    const int bar_id = 1 + g;  // named barrier of the group (0 is the block-wide one)
+    const int tid = threadIdx.x - g * NT;
+    const int lx = tid % TX, ly = tid / TX;
+    float(*ch)[CY][CX] = s_ch[g];
+    float(*rh)[CX] = s_rho[g];
+    int* flags = s_flags[g];
+    const bool ring_node = tid < NRING;
+    int rcx = 0, rcy = 0;
+    if (ring_node) {
+        if (tid < 2 * CX) {
+            rcx = tid % CX;
+            rcy = tid / CX;
+        } else if (tid < 4 * CX) {
+            rcx = (tid - 2 * CX) % CX;
+            rcy = CY - 2 + (tid - 2 * CX) / CX;
+        } else {
+            const int rr0 = tid - 4 * CX;  // 4 * TY side nodes
+            const int side = rr0 / (2 * TY), rr = rr0 % (2 * TY);
+            rcy = 2 + rr / 2;
+            rcx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
+        }
+    }
+    auto store_phase = [&](int cx, int cy, float r0, float r1, float r2) {
+        const float rho = (r0 + r1) + r2;
+        const float ir = __fdividef(1.0f, rho);
+        ch[0][cy][cx] = r0 * ir;
+        ch[1][cy][cx] = r1 * ir;
+        ch[2][cy][cx] = r2 * ir;
+        rh[cy][cx] = rho;
+        return (r0 != 0.0f ? 1 : 0) | (r1 != 0.0f ? 2 : 0) | (r2 != 0.0f ? 4 : 0);
+    };
+
+    for (int j = g, jj = 0; j < njobs; j += 2, jj++) {
+        const float* box = ring + (j % kRingBufs) * NBOXP;
+        const int tile = tiles[blockIdx.x + j * gridDim.x];
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        {
+            bool ok = false;
+            const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
+            const uint32_t par = (uint32_t)((j / (2 * kRingBufs)) & 1);
+            for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(full, par);
+            if (group_or(!ok, bar_id, NT)) {
+                if (tid == 0) atomicOr(P.err, 1);
+                return;
+            }
+        }
+        // ---- phase 1: pulls, densities and phase fields of the halo-2 region ----
+        auto pull = [&](int cx, int cy, float q[27]) {
+#pragma unroll
+            for (int p = 0; p < kQ * kNF; p++) {
+                const int a = p % kQ;
+                q[p] = box[(p * BY + cy + 1 - ey(a)) * BX + cx + 2 - ex(a)];
+            }
+        };
+        int present = 0;
+        float q[27];
+        if (ring_node) {
+            pull(rcx, rcy, q);
+            const float a0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+            const float a1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
+            const float a2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+            present |= store_phase(rcx, rcy, a0, a1, a2);
+        }
+        float f[kQ], r0, r1, r2;
+        pull(lx + 2, ly + 2, q);
+        // the box is not read again: release it to the producer (all lanes of the warp are done)
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&s_empty[j % kRingBufs]));
+#pragma unroll
+        for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
+        r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
+        r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
+        r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
+        present |= store_phase(lx + 2, ly + 2, r0, r1, r2);
+        // fluids present in the group's phase-field region (one barrier; see fluids_present)
+        int cnt;
+        {
+            const int w = __reduce_or_sync(0xffffffffu, present);
+            if (lane == 0 && w) atomicOr(&flags[jj & 1], w);
+            group_sync(bar_id, NT);
+            const int v = flags[jj & 1];
+            if (tid == 0) flags[(jj + 1) & 1] = 0;
+            cnt = __popc(v & 7);
+        }
+        const bool mixed = cnt != 1;
+
+        // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
+        if (mixed) stress_halo1<TX, TY>(P, ch, rh, s_txx[g], s_txy[g], s_tyy[g], tid);
+        group_sync(bar_id, NT);
+
+        // ---- phase 3: force, collision, recolouring, 27 stores per node ----
+        float Fx = 0.0f, Fy = 0.0f, gr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        if (mixed) {
+            div_stress<RX>(s_txx[g], s_txy[g], s_tyy[g], lx + 1, ly + 1, Fx, Fy);
+#pragma unroll
+            for (int k = 0; k < kNF; k++) grad9_f<CX>(ch[k], lx + 2, ly + 2, gr[2 * k], gr[2 * k + 1]);
+        }
+        float ux, uy;
+        const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, gr, ux, uy);
+        if (uout) {
+            const int i = (y0 + ly) * P.nx + x0 + lx;
+            uout[i] = ux;
+            uout[P.N + i] = uy;
+        }
+        float* o = fout + (y0 + ly) * P.nx + x0 + lx;
+#pragma unroll
+        for (int k = 0; k < kNF; k++)
+#pragma unroll
+            for (int a = 0; a < kQ; a++)
+                o[P.off_plane[k * kQ + a]] =
+                    rc.C[k] * f[a] + wq(a) * (rc.Vx[k] * (float)ex(a) + rc.Vy[k] * (float)ey(a));
+        // the next tile's phase fields overwrite ch / rh only after its own barriers; the stress
+        // arrays after its phase-1 barrier, by which time every thread here has read them
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 // initial state, fields, diagnostics
 // ------------------------------------------------------------------------------------------
@@ -1429,6 +1660,26 @@ void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks,
     const int nb = nblocks < ntiles ? nblocks : ntiles;
     k_step_tma<kTX, kTY, kTmaStage>
         <<<nb, dim3(kTX, kTY), step_tma_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin_a, tin_b, tout);
+}
+
+size_t step_ring_smem_bytes()
+{
+    const size_t nbox = ((size_t)kQ * kNF * (kTY + 6) * (kTX + 8) + 31) / 32 * 32;
+    return (size_t)kRingBufs * nbox * sizeof(float) + 128u;
+}
+
+cudaError_t step_ring_prepare()
+{
+    return cudaFuncSetAttribute(k_step_ring<kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)step_ring_smem_bytes());
+}
+
+void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
+                      const CUtensorMap& tin, cudaStream_t s)
+{
+    if (ntiles <= 0) return;
+    const int nb = nblocks < ntiles ? nblocks : ntiles;
+    k_step_ring<kTX, kTY><<<nb, 2 * kTX * kTY + 32, step_ring_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin);
 }
 
 size_t step_tma16_smem_bytes()
