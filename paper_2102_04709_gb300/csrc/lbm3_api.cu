@@ -40,11 +40,6 @@ struct lbm3 {
     bool ring = false;
     int ring_blocks = 0;
     CUtensorMap tm_box[2];
-    // FP32 wall tiles through the ring as well (nx a multiple of 16: the class-byte rows are
-    // copied from a 16-byte boundary), one block per SM left to the side stream
-    bool wall_ring = false;
-    int wall_blocks = 0;
-    CUtensorMap tm_type;
     int* widx = nullptr;
     double* wnrm = nullptr;
     float* wang = nullptr;
@@ -61,6 +56,11 @@ struct lbm3 {
     long long pure_fluid = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // edge tiles without a solid node within 3 nodes (wrap included) read no wall value, so they
+    // run on a third stream alongside the wetting pass; tiles_gen lists them last
+    int n_edge_free = 0;
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t ev_join2 = nullptr;
     // CUDA graphs of kGraphSteps consecutive steps (an even count: a graph starts and ends on the
     // same population buffer), one per starting buffer, captured on the internal stream gcap
     // when lbm3_step first needs them and replayed on the caller's stream; dropped when a
@@ -148,6 +148,8 @@ void release(lbm3* h)
     if (h->gcap) cudaStreamDestroy(h->gcap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
+    if (h->side2) cudaStreamDestroy(h->side2);
     if (h->side) cudaStreamDestroy(h->side);
 }
 
@@ -183,21 +185,6 @@ bool make_box_map(const Params& P, float* f, CUtensorMap* box)
     const cuuint32_t bx[3] = {kTX + 8, kTY + 6, 27};
     const cuuint32_t unit[3] = {1, 1, 1};
     return encode(box, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, bx, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Tensor map of the class bytes [ny][nx] with a box of (kTX + 32) x (kTY + 6) bytes (row pitch nx
-// bytes: nx a multiple of 16).
-bool make_type_map(const Params& P, uint8_t* type, CUtensorMap* m)
-{
-    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-    if (!encode) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny};
-    const cuuint64_t strides[1] = {(cuuint64_t)P.nx};
-    const cuuint32_t bx[2] = {kTX + 32, kTY + 6};
-    const cuuint32_t unit[2] = {1, 1};
-    return encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, type, dims, strides, bx, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -252,6 +239,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     float* u = last ? h->u : nullptr;
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
+    if (h->n_edge_free > 0 && (e = cudaStreamWaitEvent(h->side2, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->ring)
         launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, h->tm_box[h->cur], h->stream);
@@ -268,17 +256,19 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if (ev) cudaEventRecord(ev[2], h->side);
     launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side);
     if (ev) cudaEventRecord(ev[3], h->side);
-    if (h->wall_ring)
-        launch_step_wall_ring(h->P, h->tiles_gen, h->n_walltiles, h->wall_blocks, fo, h->Cw, u, h->tm_box[h->cur],
-                              h->tm_type, h->side);
-    else
-        launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
-                    h->side);
-    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge, fin,
-                fo, h->type, h->Cw, u, h->side);
+    launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
+                h->side);
+    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles - h->n_edge_free,
+                kTilesEdge, fin, fo, h->type, h->Cw, u, h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
+    if (h->n_edge_free > 0) {
+        launch_step(h->precision, h->P, h->tiles_gen + h->n_gen - h->n_edge_free, h->n_edge_free, kTilesEdge, fin,
+                    fo, h->type, h->Cw, u, h->side2);
+        if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->stream, h->ev_join2, 0)) != cudaSuccess) return e;
+    }
     h->cur = 1 - h->cur;
     return cudaGetLastError();
 }
@@ -456,7 +446,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     }
 
     // ---- tiles of the fused step kernel (2-D prefix sums of the solid mask)
-    std::vector<int> tp, tg, te;
+    std::vector<int> tp, tg, te, tf;
     long long pure_fluid = 0;
     {
         std::vector<long long> ps((size_t)(nx + 1) * (ny + 1), 0);
@@ -485,12 +475,19 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                 } else if (inner) {
                     tg.push_back(ty * ntx + tx);
                 } else {
-                    te.push_back(ty * ntx + tx);
+                    // an edge tile reads wall values only if a solid node lies within 3 nodes
+                    // of it (across the periodic sides too)
+                    bool free = true;
+                    for (int dy = -3; dy < kTY + 3 && free; dy++)
+                        for (int dx = -3; dx < kTX + 3 && free; dx++)
+                            if (S(x0 + dx, y0 + dy)) free = false;
+                    (free ? tf : te).push_back(ty * ntx + tx);
                 }
             }
     }
     const int n_wall_tiles = (int)tg.size();
     tg.insert(tg.end(), te.begin(), te.end());
+    tg.insert(tg.end(), tf.begin(), tf.end());
 
     // ---- parameters
     lbm3* h = new lbm3();
@@ -528,6 +525,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     h->n_pure = (int)tp.size();
     h->n_gen = (int)tg.size();
     h->n_walltiles = n_wall_tiles;
+    h->n_edge_free = (int)tf.size();
     h->pure_fluid = pure_fluid;
     h->wall_host = widx;
 
@@ -572,10 +570,12 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gcap, cudaStreamNonBlocking);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpy(h->type, cls.data(), N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !widx.empty()) e = cudaMemcpy(h->widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !wnrm.empty()) e = cudaMemcpy(h->wnrm, wnrm.data(), wnrm.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -625,16 +625,6 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                     h->ring_blocks = sms - spare;
                 } else {
                     cudaGetLastError();
-                }
-                // the wall tiles through the ring on the side stream's SMs
-                if (h->ring && nx % 16 == 0 && h->n_walltiles > 0 && spare > 0 &&
-                    make_type_map(P, h->type, &h->tm_type)) {
-                    if (step_wall_ring_prepare() == cudaSuccess) {
-                        h->wall_ring = true;
-                        h->wall_blocks = spare;
-                    } else {
-                        cudaGetLastError();
-                    }
                 }
             }
         }
@@ -948,13 +938,14 @@ int lbm3_info(const lbm3* h, int64_t out[9])
     // and 8 16-bit offsets (120 B); plus one class byte per node
     const long long per = h->precision == LBM3_FP32 ? 216 : 120;
     out[2] = h->n_fluid * per + h->P.N;
-    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_gen > h->n_walltiles);
+    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_gen - h->n_walltiles - h->n_edge_free > 0) +
+             (h->n_edge_free > 0);
     out[4] = h->nw > 0 ? 1 : 0;
     out[5] = (int64_t)h->bytes;
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes
     out[6] = h->pure_fluid * per;
     out[7] = h->pure_fluid;
-    out[8] = (h->ring ? 2 : (h->tma ? 1 : 0)) + (h->wall_ring ? 4 : 0);
+    out[8] = h->ring ? 2 : (h->tma ? 1 : 0);
     return LBM3_OK;
 }
 

@@ -334,14 +334,6 @@ size_t step_ring_smem_bytes();
 cudaError_t step_ring_prepare();
 void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
                       const CUtensorMap& tin, cudaStream_t s);
-// FP32 wall tiles (solids within 3 nodes, halo inside the domain) through the same ring, with the
-// class bytes of each tile's rows by a second copy (tensor map of the [ny][nx] class bytes, box
-// (kTX + 32, kTY + 6))
-size_t step_wall_ring_smem_bytes();
-cudaError_t step_wall_ring_prepare();
-void launch_step_wall_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
-                           const double* Cw, float* u, const CUtensorMap& tin, const CUtensorMap& ttype,
-                           cudaStream_t s);
 // pure tiles of the 16-bit storage through bulk tensor copies (persistent, nblocks blocks): tensor
 // maps of the densities (box (kTX + 8, kTY + 6, 3) of [3][ny][nx] FP32) and of the offset planes
 // (box (kTX + 16, kTY + 6, 24) of [24][ny][nx] 16-bit words)

@@ -249,23 +249,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
-        "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src)
 {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
@@ -1284,258 +1267,6 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
     }
 }
 
-// Wall tiles (solids within 3 nodes, halo inside the domain) of the FP32 storage through the
-// same warp-specialised ring as k_step_ring.  Each ring buffer holds a tile's 27-plane pull box
-// and, by a second copy on the same "full" barrier, the class bytes of its rows (TX + 32 bytes
-// from x0 - 16, a 16-byte-aligned start); the consumer group copies the class bytes of the
-// halo-3 region to its own shared memory, reads the wall values of the C_SB nodes from the
-// wetting pass (FP64), pulls with halfway bounce-back from the box (a solid source takes the
-// node's own population of the opposite direction, from its own position in the box), releases
-// the buffer, and goes on exactly as k_step<wall tiles>: the float-float phase fields where a
-// C_SB node of the halo-2 region has mixed wall values, the extrapolation at C_SB centres of the
-// Eq.(12) stencil, force, collision, recolouring, and 27 stores per fluid node.  Same arithmetic,
-// same results; bounded waits as in k_step_ring.
-template <int TX, int TY>
-__global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_wall_ring(const Params P, const int* __restrict__ tiles,
-                                                                         const int ntiles, float* __restrict__ fout,
-                                                                         const double* __restrict__ Cw,
-                                                                         float* __restrict__ uout,
-                                                                         const __grid_constant__ CUtensorMap tm_in,
-                                                                         const __grid_constant__ CUtensorMap tm_type)
-{
-    constexpr int NT = TX * TY;
-    constexpr int NW = NT / 32;
-    constexpr int HX = TX + 6, HY = TY + 6;  // geometry region (halo 3)
-    constexpr int CX = TX + 4, CY = TY + 4;  // phase-field region (halo 2)
-    constexpr int RX = TX + 2, RY = TY + 2;  // stress region (halo 1)
-    constexpr int BX = TX + 8, BY = TY + 6;  // pull-source box
-    constexpr int TBX = TX + 32;             // class-byte box row (from x0 - 16)
-    constexpr int NBOX = kQ * kNF * BY * BX;
-    constexpr int NBOXP = (NBOX + 31) / 32 * 32;
-    constexpr int NBUF = NBOXP + TBX * BY / 4;  // floats per ring buffer: box, then class bytes
-    constexpr int NRING = CX * CY - TX * TY;
-    static_assert((TBX * BY) % 128 == 0, "class-byte box keeps the buffers 128-byte aligned");
-    static_assert(NRING <= NT, "the ring of the halo-2 region must not exceed one node per thread");
-    __shared__ uint8_t s_t[2][HY][HX];
-    __shared__ float s_ch[2][kNF][CY][CX], s_cl[2][kNF][CY][CX];
-    __shared__ float s_rho[2][CY][CX];
-    __shared__ float s_txx[2][RY][RX], s_txy[2][RY][RX], s_tyy[2][RY][RX];
-    __shared__ __align__(8) uint64_t s_full[2 * kRingBufs], s_empty[kRingBufs];
-    __shared__ int s_flags[2][2];
-    extern __shared__ unsigned char dsm[];
-    float* ring = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntx = (P.nx + TX - 1) / TX;
-    const int nx = P.nx;
-    if ((int)blockIdx.x >= ntiles) return;
-    const int njobs = (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    if (threadIdx.x == 0) {
-        for (int m = 0; m < 2 * kRingBufs; m++) mbar_init(smem_u32(&s_full[m]), 1);
-        for (int b = 0; b < kRingBufs; b++) mbar_init(smem_u32(&s_empty[b]), NW);
-        fence_mbar_init();
-        s_flags[0][0] = s_flags[0][1] = s_flags[1][0] = s_flags[1][1] = 0;
-    }
-    __syncthreads();
-
-    // ---------------- producer warp ----------------
-    if (warp == 2 * NW) {
-        if (lane != 0) return;
-        int issued = 0;
-        for (int j = 0; j < njobs; j++) {
-            const int b = j % kRingBufs;
-            if (j >= kRingBufs) {
-                bool ok = false;
-                const uint32_t par = (uint32_t)((j / kRingBufs - 1) & 1);
-                for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(smem_u32(&s_empty[b]), par);
-                if (!ok) {
-                    atomicOr(P.err, 1);
-                    break;
-                }
-            }
-            const int tile = tiles[blockIdx.x + j * gridDim.x];
-            const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-            const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
-            float* buf = ring + b * NBUF;
-            mbar_arrive_expect_tx(full, (uint32_t)NBOX * 4u + (uint32_t)(TBX * BY));
-            tma_load_3d(smem_u32(buf), &tm_in, x0 - 4, y0 - 3, 0, full);
-            tma_load_2d(smem_u32(buf + NBOXP), &tm_type, x0 - 16, y0 - 3, full);
-            issued = j + 1;
-        }
-        for (int m = 0; m < 2 * kRingBufs; m++) {
-            int last = -1;
-            for (int j = issued - 1; j >= 0 && j >= issued - 2 * kRingBufs; j--)
-                if (j % (2 * kRingBufs) == m) {
-                    last = j;
-                    break;
-                }
-            if (last < 0) continue;
-            const uint32_t par = (uint32_t)((last / (2 * kRingBufs)) & 1);
-            for (int it = 0; it < kWaitLimit && !mbar_try_wait(smem_u32(&s_full[m]), par); it++) {
-            }
-        }
-        return;
-    }
-
-    // ---------------- consumer groups ----------------
-    const int g = warp / NW;
-    const int bar_id = 1 + g;
-    const int tid = threadIdx.x - g * NT;
-    const int lx = tid % TX, ly = tid / TX;
-    uint8_t(*st)[HX] = s_t[g];
-    float(*ch)[CY][CX] = s_ch[g];
-    float(*cl)[CY][CX] = s_cl[g];
-    float(*rh)[CX] = s_rho[g];
-    int* flags = s_flags[g];
-    const bool ring_node = tid < NRING;
-    int rcx = 0, rcy = 0;
-    if (ring_node) {
-        if (tid < 2 * CX) {
-            rcx = tid % CX;
-            rcy = tid / CX;
-        } else if (tid < 4 * CX) {
-            rcx = (tid - 2 * CX) % CX;
-            rcy = CY - 2 + (tid - 2 * CX) / CX;
-        } else {
-            const int rr0 = tid - 4 * CX;
-            const int side = rr0 / (2 * TY), rr = rr0 % (2 * TY);
-            rcy = 2 + rr / 2;
-            rcx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
-        }
-    }
-
-    for (int j = g, jj = 0; j < njobs; j += 2, jj++) {
-        const float* box = ring + (j % kRingBufs) * NBUF;
-        const uint8_t* tbox = reinterpret_cast<const uint8_t*>(box + NBOXP);
-        const int tile = tiles[blockIdx.x + j * gridDim.x];
-        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-        {
-            bool ok = false;
-            const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
-            const uint32_t par = (uint32_t)((j / (2 * kRingBufs)) & 1);
-            for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(full, par);
-            if (group_or(!ok, bar_id, NT)) {
-                if (tid == 0) atomicOr(P.err, 1);
-                return;
-            }
-        }
-        // ---- phase 0: class bytes of the halo-3 region, and whether a C_SB node of the
-        // halo-2 region has mixed wall values (float-float phase fields) ----
-        int wall = 0;
-        for (int q = tid; q < HX * HY; q += NT) {
-            const int hx = q % HX, hy = q / HX;
-            const uint8_t t = tbox[hy * TBX + hx + 13];
-            st[hy][hx] = t;
-            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY &&
-                mixed_wall(Cw, P.N, (y0 + hy - 3) * nx + (x0 + hx - 3)))
-                wall = 1;
-        }
-        const bool df = group_or(wall, bar_id, NT);
-
-        // ---- phase 1: pulls (halfway bounce-back at solid sources), phase fields ----
-        int present = 0;
-        auto pull = [&](int cx, int cy, const uint8_t t, float q[27]) {
-            const int hx = cx + 1, hy = cy + 1;
-            const bool fi = (t & 3) == kFI;
-#pragma unroll
-            for (int a = 0; a < kQ; a++) {
-                const bool bb = !fi && (st[hy - ey(a)][hx - ex(a)] & 2);
-#pragma unroll
-                for (int k = 0; k < kNF; k++)
-                    q[9 * k + a] = bb ? box[((k * kQ + opp(a)) * BY + cy + 1) * BX + cx + 2]
-                                      : box[((k * kQ + a) * BY + cy + 1 - ey(a)) * BX + cx + 2 - ex(a)];
-            }
-        };
-        auto fill = [&](int cx, int cy, float q[27]) -> bool {
-            const uint8_t t = st[cy + 1][cx + 1];
-            if (!(t & 2)) {
-                pull(cx, cy, t, q);
-                present |= phase_fields<CX, CY>(df, q, ch, cl, rh, cx, cy);
-                return true;
-            }
-            if ((t & 3) == kSB) {
-                present |= wall_fields<CX, CY>(Cw, P.N, (y0 + cy - 2) * nx + (x0 + cx - 2), false, ch, cl, rh, cx, cy);
-            } else {
-#pragma unroll
-                for (int k = 0; k < kNF; k++) ch[k][cy][cx] = cl[k][cy][cx] = 0.0f;
-                rh[cy][cx] = 0.0f;
-            }
-            return false;
-        };
-        float q[27];
-        if (ring_node) fill(rcx, rcy, q);
-        float f[kQ], r0 = 0.0f, r1 = 0.0f, r2 = 0.0f;
-        const bool own_fluid = fill(lx + 2, ly + 2, q);
-        // the box and its class bytes are not read again: release the buffer
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&s_empty[j % kRingBufs]));
-        if (own_fluid) {
-#pragma unroll
-            for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
-            r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
-            r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
-            r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
-        }
-        int cnt;
-        {
-            const int w = __reduce_or_sync(0xffffffffu, present);
-            if (lane == 0 && w) atomicOr(&flags[jj & 1], w);
-            group_sync(bar_id, NT);
-            const int v = flags[jj & 1];
-            if (tid == 0) flags[(jj + 1) & 1] = 0;
-            cnt = __popc(v & 7);
-        }
-        const bool mixed = cnt != 1;
-
-        // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
-        for (int r = mixed ? tid : RX * RY; r < RX * RY; r += NT) {
-            const int rx = r % RX, ry = r / RX;
-            float gxk[kNF], gyk[kNF], Txx, Txy, Tyy;
-            stress_at<HX, CX, CY>(P, st, ch, cl, rh, df, rx, ry, gxk, gyk, Txx, Txy, Tyy);
-            s_txx[g][ry][rx] = Txx;
-            s_txy[g][ry][rx] = Txy;
-            s_tyy[g][ry][rx] = Tyy;
-        }
-        group_sync(bar_id, NT);
-
-        // ---- phase 3: force, collision, recolouring, 27 stores per fluid node ----
-        if (own_fluid) {
-            float Fx = 0.0f, Fy = 0.0f, gr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            if (mixed) {
-                div_stress<RX>(s_txx[g], s_txy[g], s_tyy[g], lx + 1, ly + 1, Fx, Fy);
-                // own colour gradients, the phase-2 stencil at a fluid node
-                float gxk[kNF], gyk[kNF];
-                if (df) {
-#pragma unroll
-                    for (int k = 0; k < kNF; k++) grad9_df<CX>(ch[k], cl[k], lx + 2, ly + 2, gxk[k], gyk[k]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kNF; k++) grad9_f<CX>(ch[k], lx + 2, ly + 2, gxk[k], gyk[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < kNF; k++) {
-                    gr[2 * k] = gxk[k];
-                    gr[2 * k + 1] = gyk[k];
-                }
-            }
-            float ux, uy;
-            const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, gr, ux, uy);
-            const int i = (y0 + ly) * nx + x0 + lx;
-            if (uout) {
-                uout[i] = ux;
-                uout[P.N + i] = uy;
-            }
-            float* o = fout + i;
-#pragma unroll
-            for (int k = 0; k < kNF; k++)
-#pragma unroll
-                for (int a = 0; a < kQ; a++)
-                    o[P.off_plane[k * kQ + a]] =
-                        rc.C[k] * f[a] + wq(a) * (rc.Vx[k] * (float)ex(a) + rc.Vy[k] * (float)ey(a));
-        }
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // initial state, fields, diagnostics
 // ------------------------------------------------------------------------------------------
@@ -1991,29 +1722,6 @@ void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks
     if (ntiles <= 0) return;
     const int nb = nblocks < ntiles ? nblocks : ntiles;
     k_step_ring<kTX, kTY><<<nb, 2 * kTX * kTY + 32, step_ring_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin);
-}
-
-size_t step_wall_ring_smem_bytes()
-{
-    const size_t nbox = ((size_t)kQ * kNF * (kTY + 6) * (kTX + 8) + 31) / 32 * 32;
-    const size_t nbuf = nbox + (size_t)(kTX + 32) * (kTY + 6) / 4;
-    return (size_t)kRingBufs * nbuf * sizeof(float) + 128u;
-}
-
-cudaError_t step_wall_ring_prepare()
-{
-    return cudaFuncSetAttribute(k_step_wall_ring<kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_wall_ring_smem_bytes());
-}
-
-void launch_step_wall_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
-                           const double* Cw, float* u, const CUtensorMap& tin, const CUtensorMap& ttype,
-                           cudaStream_t s)
-{
-    if (ntiles <= 0) return;
-    const int nb = nblocks < ntiles ? nblocks : ntiles;
-    k_step_wall_ring<kTX, kTY>
-        <<<nb, 2 * kTX * kTY + 32, step_wall_ring_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, Cw, u, tin, ttype);
 }
 
 size_t step_tma16_smem_bytes()
