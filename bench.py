@@ -298,7 +298,8 @@ def run_ours(args):
     barrier()
     t0 = time.time()
     e0.record(stream)
-    ms_wet, ms_pure, ms_gen = sim.step_timed(args.steps)
+    ms_wet, ms_pure, ms_wall, ms_edge = sim.step_timed_detail(args.steps)
+    ms_gen = ms_wall + ms_edge
     e1.record(stream)
     barrier()
     t1 = time.time()
@@ -424,6 +425,8 @@ def run_ours(args):
                    "replicas": ws, "ms_wet_per_step": ms_wet / args.steps,
                    "ms_step_pure_tiles_per_step": ms_pure / args.steps,
                    "ms_step_other_tiles_per_step": ms_gen / args.steps,
+                   "ms_step_wall_tiles_per_step": ms_wall / args.steps,
+                   "ms_step_edge_tiles_per_step": ms_edge / args.steps,
                    "pure_tile_nodes": info["pure_nodes"],
                    "step_algorithmic_bytes": info["step_bytes"],
                    "step_effective_gbs": info["step_bytes"] / (ms / args.steps * 1e-3) / 1e9,

@@ -105,6 +105,11 @@ int lbm3_step(lbm3* h, int32_t nsteps);
  * wetting pass).  The pure-tile launch overlaps the other two. */
 int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3]);
 
+/* lbm3_step_timed with the other tiles split by kind: ms_out[0] = wetting pass, ms_out[1] = pure
+ * tiles, ms_out[2] = wall tiles (solids within 3 nodes, halo inside the domain), ms_out[3] = edge
+ * tiles (halo crossing the domain edge), summed over the steps in ms.  Synchronises. */
+int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[4]);
+
 /* Copy the current post-streaming densities rho_k (host [3][ny][nx], 0 at solid nodes) and the
  * velocity of the most recent collision, Eq.(11) (host [2][ny][nx], may be NULL).  Synchronises.
  * Returns LBM3_ERR_CUDA (with the arrays filled) if a step kernel gave up on a bulk copy since the

@@ -56,11 +56,6 @@ struct lbm3 {
     long long pure_fluid = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-    // edge tiles without a solid node within 3 nodes (wrap included) read no wall value, so they
-    // run on a third stream alongside the wetting pass; tiles_gen lists them last
-    int n_edge_free = 0;
-    cudaStream_t side2 = nullptr;
-    cudaEvent_t ev_join2 = nullptr;
     // CUDA graphs of kGraphSteps consecutive steps (an even count: a graph starts and ends on the
     // same population buffer), one per starting buffer, captured on the internal stream gcap
     // when lbm3_step first needs them and replayed on the caller's stream; dropped when a
@@ -148,8 +143,6 @@ void release(lbm3* h)
     if (h->gcap) cudaStreamDestroy(h->gcap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
-    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
-    if (h->side2) cudaStreamDestroy(h->side2);
     if (h->side) cudaStreamDestroy(h->side);
 }
 
@@ -230,7 +223,8 @@ bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtens
 
 // One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
 // while the side stream runs the wetting pass and then the remaining tiles, join.  With ev != NULL
-// the launches are bracketed by the events ev[0..5] (main: 0-1 pure; side: 2-3 wet, 4-5 rest).
+// the launches are bracketed by the events ev[0..5] (main: 0-1 pure tiles; side: 2-3 wetting pass,
+// 3-4 wall tiles, 4-5 edge tiles).
 cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 {
     cudaError_t e;
@@ -239,7 +233,6 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     float* u = last ? h->u : nullptr;
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    if (h->n_edge_free > 0 && (e = cudaStreamWaitEvent(h->side2, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->ring)
         launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, h->tm_box[h->cur], h->stream);
@@ -258,17 +251,12 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if (ev) cudaEventRecord(ev[3], h->side);
     launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
                 h->side);
-    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles - h->n_edge_free,
-                kTilesEdge, fin, fo, h->type, h->Cw, u, h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
+    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge, fin,
+                fo, h->type, h->Cw, u, h->side);
+    if (ev) cudaEventRecord(ev[5], h->side);
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
-    if (h->n_edge_free > 0) {
-        launch_step(h->precision, h->P, h->tiles_gen + h->n_gen - h->n_edge_free, h->n_edge_free, kTilesEdge, fin,
-                    fo, h->type, h->Cw, u, h->side2);
-        if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(h->stream, h->ev_join2, 0)) != cudaSuccess) return e;
-    }
     h->cur = 1 - h->cur;
     return cudaGetLastError();
 }
@@ -446,7 +434,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     }
 
     // ---- tiles of the fused step kernel (2-D prefix sums of the solid mask)
-    std::vector<int> tp, tg, te, tf;
+    std::vector<int> tp, tg, te;
     long long pure_fluid = 0;
     {
         std::vector<long long> ps((size_t)(nx + 1) * (ny + 1), 0);
@@ -475,19 +463,12 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                 } else if (inner) {
                     tg.push_back(ty * ntx + tx);
                 } else {
-                    // an edge tile reads wall values only if a solid node lies within 3 nodes
-                    // of it (across the periodic sides too)
-                    bool free = true;
-                    for (int dy = -3; dy < kTY + 3 && free; dy++)
-                        for (int dx = -3; dx < kTX + 3 && free; dx++)
-                            if (S(x0 + dx, y0 + dy)) free = false;
-                    (free ? tf : te).push_back(ty * ntx + tx);
+                    te.push_back(ty * ntx + tx);
                 }
             }
     }
     const int n_wall_tiles = (int)tg.size();
     tg.insert(tg.end(), te.begin(), te.end());
-    tg.insert(tg.end(), tf.begin(), tf.end());
 
     // ---- parameters
     lbm3* h = new lbm3();
@@ -525,7 +506,6 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     h->n_pure = (int)tp.size();
     h->n_gen = (int)tg.size();
     h->n_walltiles = n_wall_tiles;
-    h->n_edge_free = (int)tf.size();
     h->pure_fluid = pure_fluid;
     h->wall_host = widx;
 
@@ -570,12 +550,10 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
-        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gcap, cudaStreamNonBlocking);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpy(h->type, cls.data(), N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !widx.empty()) e = cudaMemcpy(h->widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !wnrm.empty()) e = cudaMemcpy(h->wnrm, wnrm.data(), wnrm.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -677,27 +655,38 @@ int lbm3_step(lbm3* h, int32_t nsteps)
     return LBM3_OK;
 }
 
-int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3])
+int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[4])
 {
     if (!h || !ms_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
     if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
-    ms_out[0] = ms_out[1] = ms_out[2] = 0.0;
-    std::vector<cudaEvent_t> ev(5 * (size_t)nsteps);
+    for (int j = 0; j < 4; j++) ms_out[j] = 0.0;
+    std::vector<cudaEvent_t> ev(6 * (size_t)nsteps);
     for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
-    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[5 * (size_t)s]));
+    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[6 * (size_t)s]));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     for (int s = 0; s < nsteps; s++) {
-        float a = 0.f, b = 0.f, c = 0.f;
-        const cudaEvent_t* E = &ev[5 * (size_t)s];
-        CUDA_TRY(h, cudaEventElapsedTime(&a, E[2], E[3]));
-        CUDA_TRY(h, cudaEventElapsedTime(&b, E[0], E[1]));
-        CUDA_TRY(h, cudaEventElapsedTime(&c, E[3], E[4]));
-        ms_out[0] += a;
-        ms_out[1] += b;
-        ms_out[2] += c;
+        const cudaEvent_t* E = &ev[6 * (size_t)s];
+        const int from[4] = {2, 0, 3, 4}, to[4] = {3, 1, 4, 5};
+        for (int j = 0; j < 4; j++) {
+            float t = 0.f;
+            CUDA_TRY(h, cudaEventElapsedTime(&t, E[from[j]], E[to[j]]));
+            ms_out[j] += t;
+        }
     }
     for (auto& e : ev) cudaEventDestroy(e);
+    return LBM3_OK;
+}
+
+int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3])
+{
+    if (!ms_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
+    double d[4];
+    const int rc = lbm3_step_timed_detail(h, nsteps, d);
+    if (rc != LBM3_OK) return rc;
+    ms_out[0] = d[0];
+    ms_out[1] = d[1];
+    ms_out[2] = d[2] + d[3];
     return LBM3_OK;
 }
 
@@ -938,8 +927,7 @@ int lbm3_info(const lbm3* h, int64_t out[9])
     // and 8 16-bit offsets (120 B); plus one class byte per node
     const long long per = h->precision == LBM3_FP32 ? 216 : 120;
     out[2] = h->n_fluid * per + h->P.N;
-    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_gen - h->n_walltiles - h->n_edge_free > 0) +
-             (h->n_edge_free > 0);
+    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_gen > h->n_walltiles);
     out[4] = h->nw > 0 ? 1 : 0;
     out[5] = (int64_t)h->bytes;
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes

@@ -25,7 +25,8 @@ LBM3_ERR_TOO_LARGE = -6
 LBM3_FP32, LBM3_FP16, LBM3_BF16 = 0, 1, 2
 
 # every entry point declared in include/lbm3.h
-EXPORTS = ("lbm3_create", "lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields",
+EXPORTS = ("lbm3_create", "lbm3_set_fields", "lbm3_step", "lbm3_step_timed",
+           "lbm3_step_timed_detail", "lbm3_fields",
            "lbm3_diag", "lbm3_n_wall", "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state",
            "lbm3_set_state", "lbm3_set_wall_angles", "lbm3_set_inflow", "lbm3_adjoint_centroid",
            "lbm3_info", "lbm3_set_stream", "lbm3_set_copy_wait_limit", "lbm3_sync",
@@ -65,6 +66,7 @@ def load(path: str | None = None):
     L.lbm3_set_fields.argtypes = [vp, _D]
     L.lbm3_step.argtypes = [vp, ctypes.c_int32]
     L.lbm3_step_timed.argtypes = [vp, ctypes.c_int32, _D]
+    L.lbm3_step_timed_detail.argtypes = [vp, ctypes.c_int32, _D]
     L.lbm3_fields.argtypes = [vp, _D, _D]
     L.lbm3_diag.argtypes = [vp, _D]
     L.lbm3_n_wall.argtypes = [vp]
@@ -84,7 +86,7 @@ def load(path: str | None = None):
     L.lbm3_last_error.argtypes = [vp]
     L.lbm3_diag_fields.argtypes = [vp, vp, vp, ctypes.c_int32, ctypes.c_int32, vp, vp]
     L.lbm3_last_error.restype = ctypes.c_char_p
-    for name in ("lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_fields", "lbm3_diag", "lbm3_n_wall",
+    for name in ("lbm3_set_fields", "lbm3_step", "lbm3_step_timed", "lbm3_step_timed_detail", "lbm3_fields", "lbm3_diag", "lbm3_n_wall",
                  "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state", "lbm3_set_state", "lbm3_info", "lbm3_set_stream",
                  "lbm3_set_copy_wait_limit", "lbm3_sync"):
         getattr(L, name).restype = ctypes.c_int
@@ -183,6 +185,13 @@ class Lbm3:
         out = np.zeros(3)
         _check(self._h, load().lbm3_step_timed(self._h, int(n), _dp(out)))
         return float(out[0]), float(out[1]), float(out[2])
+
+    def step_timed_detail(self, n):
+        """Advance n steps; return CUDA-event times in ms summed over the steps: (wetting pass,
+        pure tiles, wall tiles, edge tiles)."""
+        out = np.zeros(4)
+        _check(self._h, load().lbm3_step_timed_detail(self._h, int(n), _dp(out)))
+        return tuple(float(v) for v in out)
 
     def fields(self):
         rho = np.empty(3 * self.n)
