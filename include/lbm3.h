@@ -168,10 +168,8 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, dou
  * pure-tile launch, out[7] = nodes in pure tiles, out[8] = how the pure tiles move their
  * populations: 0 plain loads, 1 bulk tensor copies with two blocks per SM, 2 bulk tensor copies
  * through the warp-specialised ring (FP32 storage; LBM3_PURE_KERNEL=tma in the environment at
- * lbm3_create selects 1 instead), plus 4 if the wall tiles also go through a ring of bulk copies
- * (with the FP32 ring, nx a multiple of 16; LBM3_WALL_KERNEL=plain keeps the one-tile-per-block
- * kernel).  Bulk copies need nx a multiple of 4 (FP32) or 8 (16-bit offsets) and are disabled by
- * LBM3_DISABLE_TMA=1. */
+ * lbm3_create selects 1 instead).  Bulk copies need nx a multiple of 4 (FP32) or 8 (16-bit
+ * offsets) and are disabled by LBM3_DISABLE_TMA=1. */
 int lbm3_info(const lbm3* h, int64_t out[9]);
 
 /* Change the stream used by later calls (cudaStream_t).  Work already enqueued by the handle

@@ -40,13 +40,6 @@ struct lbm3 {
     bool ring = false;
     int ring_blocks = 0;
     CUtensorMap tm_box[2];
-    // FP32 wall tiles through a ring as well (nx a multiple of 16: the class-byte rows are copied
-    // from a 16-byte boundary), one block per SM left to the side stream; tile_df: per tile, mixed
-    // wall values in its halo-2 region this step (set by the wetting pass, cleared by the kernel)
-    bool wall_ring = false;
-    int wall_blocks = 0;
-    int* tile_df = nullptr;
-    CUtensorMap tm_type;
     int* widx = nullptr;
     double* wnrm = nullptr;
     float* wang = nullptr;
@@ -141,8 +134,7 @@ void release(lbm3* h)
 {
     void* ptrs[] = {h->pop[0].f, h->pop[1].f, h->pop[0].rho, h->pop[1].rho, h->pop[0].off,
                     h->pop[1].off, h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
-                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag, h->wcache,
-                    h->tile_df};
+                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag, h->wcache};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->pop[0] = h->pop[1] = Pop{nullptr, nullptr, nullptr};
@@ -186,21 +178,6 @@ bool make_box_map(const Params& P, float* f, CUtensorMap* box)
     const cuuint32_t bx[3] = {kTX + 8, kTY + 6, 27};
     const cuuint32_t unit[3] = {1, 1, 1};
     return encode(box, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, f, dims, strides, bx, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                  CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Tensor map of the class bytes [ny][nx] with a box of (kTX + 32) x (kTY + 6) bytes (row pitch nx
-// bytes: nx a multiple of 16).
-bool make_type_map(const Params& P, uint8_t* type, CUtensorMap* m)
-{
-    const PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
-    if (!encode) return false;
-    const cuuint64_t dims[2] = {(cuuint64_t)P.nx, (cuuint64_t)P.ny};
-    const cuuint64_t strides[1] = {(cuuint64_t)P.nx};
-    const cuuint32_t bx[2] = {kTX + 32, kTY + 6};
-    const cuuint32_t unit[2] = {1, 1};
-    return encode(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, type, dims, strides, bx, unit, CU_TENSOR_MAP_INTERLEAVE_NONE,
                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -270,15 +247,10 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
                     h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (ev) cudaEventRecord(ev[2], h->side);
-    launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache,
-               h->wall_ring ? h->tile_df : nullptr, h->side);
+    launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side);
     if (ev) cudaEventRecord(ev[3], h->side);
-    if (h->wall_ring)
-        launch_step_wall_ring(h->P, h->tiles_gen, h->n_walltiles, h->wall_blocks, fo, h->Cw, u, h->tile_df,
-                              h->tm_box[h->cur], h->tm_type, h->side);
-    else
-        launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
-                    h->side);
+    launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
+                h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
     launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge, fin,
                 fo, h->type, h->Cw, u, h->side);
@@ -632,22 +604,6 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                 } else {
                     cudaGetLastError();
                 }
-                // the wall tiles through their ring on the side stream's SMs, unless
-                // LBM3_WALL_KERNEL=plain keeps the one-tile-per-block kernel (the same results)
-                const char* wk = std::getenv("LBM3_WALL_KERNEL");
-                if (h->ring && nx % 16 == 0 && h->n_walltiles > 0 && spare > 0 &&
-                    !(wk && std::strcmp(wk, "plain") == 0) && make_type_map(P, h->type, &h->tm_type)) {
-                    const int ntiles = ((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY);
-                    cudaError_t ew = dmalloc((void**)&h->tile_df, (size_t)ntiles * sizeof(int));
-                    if (ew == cudaSuccess) ew = cudaMemset(h->tile_df, 0, (size_t)ntiles * sizeof(int));
-                    if (ew == cudaSuccess) ew = step_wall_ring_prepare();
-                    if (ew == cudaSuccess) {
-                        h->wall_ring = true;
-                        h->wall_blocks = spare;
-                    } else {
-                        cudaGetLastError();
-                    }
-                }
             }
         }
     }
@@ -977,7 +933,7 @@ int lbm3_info(const lbm3* h, int64_t out[9])
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes
     out[6] = h->pure_fluid * per;
     out[7] = h->pure_fluid;
-    out[8] = (h->ring ? 2 : (h->tma ? 1 : 0)) + (h->wall_ring ? 4 : 0);
+    out[8] = h->ring ? 2 : (h->tma ? 1 : 0);
     return LBM3_OK;
 }
 

@@ -305,11 +305,9 @@ struct WetCache {
 };
 
 // ---- kernel launchers (lbm3_step.cu); `store` is kStoreF32 / kStoreF16 / kStoreBF16 ----
-// tile_df (nullable): per 32 x 8 tile, set to 1 where a C_SB node of the tile's halo-2 region
-// gets mixed wall values (for the wall-tile ring kernel, which reads and clears it)
 void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
                 const float* wang, const Pop& f, const uint8_t* type, double* Cw, WetCache* cache,
-                int* tile_df, cudaStream_t s);
+                cudaStream_t s);
 void reset_wet_cache(WetCache* cache, int nw, cudaStream_t s);
 void launch_wet_init(int store, const Params& P, int nw, const int* widx, const Pop& f,
                      const uint8_t* type, double* Cw, cudaStream_t s);
@@ -329,14 +327,6 @@ cudaError_t step_tma_prepare();
 cudaError_t step_tma16_prepare();
 void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
                      const CUtensorMap& tin_a, const CUtensorMap& tin_b, const CUtensorMap& tout, cudaStream_t s);
-// FP32 wall tiles (solids within 3 nodes, halo inside the domain) through the same ring: class
-// bytes of each tile's rows by a second copy (tensor map of the [ny][nx] class bytes, box
-// (kTX + 32, kTY + 6)); tile_df as set by the wetting pass of the step (read and cleared)
-size_t step_wall_ring_smem_bytes();
-cudaError_t step_wall_ring_prepare();
-void launch_step_wall_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
-                           const double* Cw, float* u, int* tile_df, const CUtensorMap& tin,
-                           const CUtensorMap& ttype, cudaStream_t s);
 // pure FP32 tiles through a ring of three bulk-copy buffers, one producer warp and two consumer
 // groups per block, one block per SM (nblocks blocks): tensor map of fin with the whole pull box
 // (kTX + 8, kTY + 6, 27) over the [27][ny][nx] buffer

@@ -21,20 +21,6 @@ namespace lbm3k {
 
 namespace {
 
-// A C_SB node whose wall values are not all within kMixEps of one pure fluid: a fluid-fluid
-// interface reaches the wall there (a contact line, or one within a few nodes of it), where the
-// lagged wetting feedback amplifies the rounding of single-precision phase fields.  Away from
-// such nodes the phase fields near walls are those of one fluid and a float suffices.
-constexpr double kMixEps = 1e-6;
-__device__ __forceinline__ bool mixed_values(double c0, double c1, double c2)
-{
-    return fmax(fmax(c0, c1), c2) < 1.0 - kMixEps;
-}
-__device__ __forceinline__ bool mixed_wall(const double* __restrict__ Cw, long long N, long long i)
-{
-    return mixed_values(Cw[i], Cw[N + i], Cw[2 * N + i]);
-}
-
 // Four lanes per C_SB node: lane = 2 * k + side, for the wetted fluids k = 0, 1 and the two
 // characteristic lines (rotated by +phi and -phi from n_s).  Each lane marches its line over the
 // class bytes, then gathers C at the one or two nodes it found; Eq.(22) combines the two lines
@@ -44,7 +30,7 @@ __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const
                                              const double* __restrict__ wnrm,
                                              const float* __restrict__ wang, const S st,
                                              const uint8_t* __restrict__ type, double* __restrict__ Cw,
-                                             WetCache* __restrict__ cache, int* __restrict__ tile_df)
+                                             WetCache* __restrict__ cache)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = g >> 2;
@@ -94,21 +80,9 @@ __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const
             c0 /= s;
             c1 /= s;
         }
-        const double c2 = fmax(0.0, 1.0 - c0 - c1);
         Cw[i] = c0;
         Cw[P.N + i] = c1;
-        Cw[2 * P.N + i] = c2;
-        // mixed wall values: every 32 x 8 tile whose halo-2 region holds this node takes the
-        // float-float phase fields in this step (read and cleared by the wall-tile ring kernel)
-        if (tile_df && mixed_values(c0, c1, c2)) {
-            const int ntx = (P.nx + kTX - 1) / kTX, nty = (P.ny + kTY - 1) / kTY;
-            for (int ty = max(0, floordiv_i(py - kTY - 1, kTY)); ty <= min(nty - 1, floordiv_i(py + 2, kTY)); ty++)
-                for (int tx = max(0, floordiv_i(px - kTX - 1, kTX)); tx <= min(ntx - 1, floordiv_i(px + 2, kTX)); tx++) {
-                    const int x0 = tx * kTX, y0 = ty * kTY;
-                    if (px >= x0 - 2 && px <= x0 + kTX + 1 && py >= y0 - 2 && py <= y0 + kTY + 1)
-                        atomicOr(&tile_df[ty * ntx + tx], 1);
-                }
-        }
+        Cw[2 * P.N + i] = fmax(0.0, 1.0 - c0 - c1);
     }
 }
 
@@ -275,14 +249,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(map), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
 __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, int x, int y, int z, uint32_t src)
 {
     asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];" ::"l"(map),
@@ -303,6 +269,16 @@ __device__ __forceinline__ void fence_proxy_async_smem()
 // test the timeout path)
 constexpr int kWaitLimit = 1 << 22;
 
+// A C_SB node whose wall values are not all within kMixEps of one pure fluid: a fluid-fluid
+// interface reaches the wall there (a contact line, or one within a few nodes of it), where the
+// lagged wetting feedback amplifies the rounding of single-precision phase fields.  Away from
+// such nodes the phase fields near walls are those of one fluid and a float suffices.
+constexpr double kMixEps = 1e-6;
+__device__ __forceinline__ bool mixed_wall(const double* __restrict__ Cw, long long N, long long i)
+{
+    const double m = fmax(fmax(Cw[i], Cw[N + i]), Cw[2 * N + i]);
+    return m < 1.0 - kMixEps;
+}
 
 // Eq.(12) derivative of a float field held in shared memory
 template <int W>
@@ -442,29 +418,21 @@ __device__ __forceinline__ int phase_fields(bool df, const float q[27], float (*
 // split into hi + lo; labels relabelled across a modified periodic seam when par); rho := 1 at
 // solid nodes.  Returns the fluids with a nonzero wall value.
 template <int CX, int CY>
-__device__ __forceinline__ int wall_values(const double c[kNF], float (*ch)[CY][CX], float (*cl)[CY][CX],
-                                           float (*rh)[CX], int cx, int cy)
-{
-    int present = 0;
-#pragma unroll
-    for (int k = 0; k < kNF; k++) {
-        const float h = (float)c[k];
-        ch[k][cy][cx] = h;
-        cl[k][cy][cx] = (float)(c[k] - (double)h);
-        if (c[k] != 0.0) present |= 1 << k;
-    }
-    rh[cy][cx] = 1.0f;
-    return present;
-}
-template <int CX, int CY>
 __device__ __forceinline__ int wall_fields(const double* __restrict__ Cw, long long N, int in, bool par,
                                            float (*ch)[CY][CX], float (*cl)[CY][CX], float (*rh)[CX], int cx,
                                            int cy)
 {
-    double c[kNF];
+    int present = 0;
 #pragma unroll
-    for (int k = 0; k < kNF; k++) c[k] = Cw[(long long)relabel(k, par) * N + in];
-    return wall_values<CX, CY>(c, ch, cl, rh, cx, cy);
+    for (int k = 0; k < kNF; k++) {
+        const double c = Cw[(long long)relabel(k, par) * N + in];
+        const float h = (float)c;
+        ch[k][cy][cx] = h;
+        cl[k][cy][cx] = (float)(c - (double)h);
+        if (c != 0.0) present |= 1 << k;
+    }
+    rh[cy][cx] = 1.0f;
+    return present;
 }
 
 // Eq.(12) gradients (gxk, gyk) and the Eq.(10) stress of position (rx, ry) of the stress region
@@ -1299,283 +1267,6 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
     }
 }
 
-constexpr int kWallJobs = 512;  // tiles per block of k_step_wall_ring
-// Wall tiles (solids within 3 nodes, halo inside the domain) of the FP32 storage through the
-// same warp-specialised ring as k_step_ring.  Each ring buffer holds a tile's 27-plane pull box
-// and, by a second copy on the same "full" barrier, the class bytes of its rows (TX + 32 bytes
-// from x0 - 16, a 16-byte-aligned start).  The block's tile list and, per tile, whether a C_SB
-// node of its halo-2 region has mixed wall values (set by this step's wetting pass in tile_df,
-// read and cleared here) are staged in shared memory first, so neither the producer nor the
-// consumers wait on global memory for them.  A consumer group issues the wall-value loads of its
-// C_SB nodes (FP64) as soon as the box is in, copies the class bytes of the halo-3 region to its
-// own shared memory, pulls with halfway bounce-back from the box (a solid source takes the
-// node's own population of the opposite direction, from its own position in the box), releases
-// the buffer, and goes on exactly as k_step<wall tiles>: float-float phase fields where the tile
-// has mixed wall values, the extrapolation at C_SB centres of the Eq.(12) stencil, force,
-// collision, recolouring, and 27 stores per fluid node.  Same arithmetic, same results; bounded
-// waits as in k_step_ring.  At most kWallJobs tiles per block (the launcher sizes the grid).
-template <int TX, int TY>
-__global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_wall_ring(const Params P, const int* __restrict__ tiles,
-                                                                         const int ntiles, float* __restrict__ fout,
-                                                                         const double* __restrict__ Cw,
-                                                                         float* __restrict__ uout,
-                                                                         int* __restrict__ tile_df,
-                                                                         const __grid_constant__ CUtensorMap tm_in,
-                                                                         const __grid_constant__ CUtensorMap tm_type)
-{
-    constexpr int NT = TX * TY;
-    constexpr int NW = NT / 32;
-    constexpr int HX = TX + 6, HY = TY + 6;  // geometry region (halo 3)
-    constexpr int CX = TX + 4, CY = TY + 4;  // phase-field region (halo 2)
-    constexpr int RX = TX + 2, RY = TY + 2;  // stress region (halo 1)
-    constexpr int BX = TX + 8, BY = TY + 6;  // pull-source box
-    constexpr int TBX = TX + 32;             // class-byte box row (from x0 - 16)
-    constexpr int NBOX = kQ * kNF * BY * BX;
-    constexpr int NBOXP = (NBOX + 31) / 32 * 32;
-    constexpr int NBUF = NBOXP + TBX * BY / 4;  // floats per ring buffer: box, then class bytes
-    constexpr int NRING = CX * CY - TX * TY;
-    static_assert((TBX * BY) % 128 == 0, "class-byte box keeps the buffers 128-byte aligned");
-    static_assert(NRING <= NT, "the ring of the halo-2 region must not exceed one node per thread");
-    __shared__ uint8_t s_t[2][HY][HX];
-    __shared__ float s_ch[2][kNF][CY][CX], s_cl[2][kNF][CY][CX];
-    __shared__ float s_rho[2][CY][CX];
-    __shared__ float s_txx[2][RY][RX], s_txy[2][RY][RX], s_tyy[2][RY][RX];
-    __shared__ __align__(8) uint64_t s_full[2 * kRingBufs], s_empty[kRingBufs];
-    __shared__ int s_flags[2][2];
-    __shared__ int s_job[kWallJobs];    // tile index of job j
-    __shared__ uint8_t s_jdf[kWallJobs];  // float-float phase fields for job j
-    extern __shared__ unsigned char dsm[];
-    float* ring = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntx = (P.nx + TX - 1) / TX;
-    const int nx = P.nx;
-    if ((int)blockIdx.x >= ntiles) return;
-    const int njobs = min(kWallJobs, (ntiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
-    for (int j = threadIdx.x; j < njobs; j += blockDim.x) {
-        const int tile = tiles[blockIdx.x + j * gridDim.x];
-        s_job[j] = tile;
-        s_jdf[j] = tile_df[tile] != 0;
-        tile_df[tile] = 0;  // for the next step's wetting pass
-    }
-    if (threadIdx.x == 0) {
-        for (int m = 0; m < 2 * kRingBufs; m++) mbar_init(smem_u32(&s_full[m]), 1);
-        for (int b = 0; b < kRingBufs; b++) mbar_init(smem_u32(&s_empty[b]), NW);
-        fence_mbar_init();
-        s_flags[0][0] = s_flags[0][1] = s_flags[1][0] = s_flags[1][1] = 0;
-    }
-    __syncthreads();
-
-    // ---------------- producer warp ----------------
-    if (warp == 2 * NW) {
-        if (lane != 0) return;
-        int issued = 0;
-        for (int j = 0; j < njobs; j++) {
-            const int b = j % kRingBufs;
-            if (j >= kRingBufs) {
-                bool ok = false;
-                const uint32_t par = (uint32_t)((j / kRingBufs - 1) & 1);
-                for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(smem_u32(&s_empty[b]), par);
-                if (!ok) {
-                    atomicOr(P.err, 1);
-                    break;
-                }
-            }
-            const int tile = s_job[j];
-            const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-            const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
-            float* buf = ring + b * NBUF;
-            mbar_arrive_expect_tx(full, (uint32_t)NBOX * 4u + (uint32_t)(TBX * BY));
-            tma_load_3d(smem_u32(buf), &tm_in, x0 - 4, y0 - 3, 0, full);
-            tma_load_2d(smem_u32(buf + NBOXP), &tm_type, x0 - 16, y0 - 3, full);
-            issued = j + 1;
-        }
-        for (int m = 0; m < 2 * kRingBufs; m++) {
-            int last = -1;
-            for (int j = issued - 1; j >= 0 && j >= issued - 2 * kRingBufs; j--)
-                if (j % (2 * kRingBufs) == m) {
-                    last = j;
-                    break;
-                }
-            if (last < 0) continue;
-            const uint32_t par = (uint32_t)((last / (2 * kRingBufs)) & 1);
-            for (int it = 0; it < kWaitLimit && !mbar_try_wait(smem_u32(&s_full[m]), par); it++) {
-            }
-        }
-        return;
-    }
-
-    // ---------------- consumer groups ----------------
-    const int g = warp / NW;
-    const int bar_id = 1 + g;
-    const int tid = threadIdx.x - g * NT;
-    const int lx = tid % TX, ly = tid / TX;
-    uint8_t(*st)[HX] = s_t[g];
-    float(*ch)[CY][CX] = s_ch[g];
-    float(*cl)[CY][CX] = s_cl[g];
-    float(*rh)[CX] = s_rho[g];
-    int* flags = s_flags[g];
-    const bool ring_node = tid < NRING;
-    int rcx = 0, rcy = 0;
-    if (ring_node) {
-        if (tid < 2 * CX) {
-            rcx = tid % CX;
-            rcy = tid / CX;
-        } else if (tid < 4 * CX) {
-            rcx = (tid - 2 * CX) % CX;
-            rcy = CY - 2 + (tid - 2 * CX) / CX;
-        } else {
-            const int rr0 = tid - 4 * CX;
-            const int side = rr0 / (2 * TY), rr = rr0 % (2 * TY);
-            rcy = 2 + rr / 2;
-            rcx = side == 0 ? (rr & 1) : CX - 2 + (rr & 1);
-        }
-    }
-
-    for (int j = g, jj = 0; j < njobs; j += 2, jj++) {
-        const float* box = ring + (j % kRingBufs) * NBUF;
-        const uint8_t* tbox = reinterpret_cast<const uint8_t*>(box + NBOXP);
-        const int tile = s_job[j];
-        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
-        const bool df = s_jdf[j];
-        {
-            bool ok = false;
-            const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
-            const uint32_t par = (uint32_t)((j / (2 * kRingBufs)) & 1);
-            for (int it = 0; it < P.wait_polls && !ok; it++) ok = mbar_try_wait(full, par);
-            if (group_or(!ok, bar_id, NT)) {
-                if (tid == 0) atomicOr(P.err, 1);
-                return;
-            }
-        }
-        // wall values of this thread's C_SB nodes (ring node, own node), loaded first so that
-        // they arrive while the class bytes are copied and the populations pulled
-        double cw_ring[kNF] = {0.0, 0.0, 0.0}, cw_own[kNF] = {0.0, 0.0, 0.0};
-        {
-            const uint8_t tr = ring_node ? tbox[(rcy + 1) * TBX + rcx + 1 + 13] : (uint8_t)kFI;
-            const uint8_t to = tbox[(ly + 3) * TBX + lx + 3 + 13];
-            if ((tr & 3) == kSB) {
-                const int in = (y0 + rcy - 2) * nx + (x0 + rcx - 2);
-#pragma unroll
-                for (int k = 0; k < kNF; k++) cw_ring[k] = Cw[(long long)k * P.N + in];
-            }
-            if ((to & 3) == kSB) {
-                const int in = (y0 + ly) * nx + (x0 + lx);
-#pragma unroll
-                for (int k = 0; k < kNF; k++) cw_own[k] = Cw[(long long)k * P.N + in];
-            }
-        }
-        // ---- phase 0: class bytes of the halo-3 region ----
-        for (int q = tid; q < HX * HY; q += NT) {
-            const int hx = q % HX, hy = q / HX;
-            st[hy][hx] = tbox[hy * TBX + hx + 13];
-        }
-        group_sync(bar_id, NT);
-
-        // ---- phase 1: pulls (halfway bounce-back at solid sources), phase fields ----
-        int present = 0;
-        auto pull = [&](int cx, int cy, const uint8_t t, float q[27]) {
-            const int hx = cx + 1, hy = cy + 1;
-            const bool fi = (t & 3) == kFI;
-#pragma unroll
-            for (int a = 0; a < kQ; a++) {
-                const bool bb = !fi && (st[hy - ey(a)][hx - ex(a)] & 2);
-#pragma unroll
-                for (int k = 0; k < kNF; k++)
-                    q[9 * k + a] = bb ? box[((k * kQ + opp(a)) * BY + cy + 1) * BX + cx + 2]
-                                      : box[((k * kQ + a) * BY + cy + 1 - ey(a)) * BX + cx + 2 - ex(a)];
-            }
-        };
-        auto fill = [&](int cx, int cy, const double* cw, float q[27]) -> bool {
-            const uint8_t t = st[cy + 1][cx + 1];
-            if (!(t & 2)) {
-                pull(cx, cy, t, q);
-                present |= phase_fields<CX, CY>(df, q, ch, cl, rh, cx, cy);
-                return true;
-            }
-            if ((t & 3) == kSB) {
-                present |= wall_values<CX, CY>(cw, ch, cl, rh, cx, cy);
-            } else {
-#pragma unroll
-                for (int k = 0; k < kNF; k++) ch[k][cy][cx] = cl[k][cy][cx] = 0.0f;
-                rh[cy][cx] = 0.0f;
-            }
-            return false;
-        };
-        float q[27];
-        if (ring_node) fill(rcx, rcy, cw_ring, q);
-        float f[kQ], r0 = 0.0f, r1 = 0.0f, r2 = 0.0f;
-        const bool own_fluid = fill(lx + 2, ly + 2, cw_own, q);
-        // the box and its class bytes are not read again: release the buffer
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&s_empty[j % kRingBufs]));
-        if (own_fluid) {
-#pragma unroll
-            for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
-            r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
-            r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
-            r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
-        }
-        int cnt;
-        {
-            const int w = __reduce_or_sync(0xffffffffu, present);
-            if (lane == 0 && w) atomicOr(&flags[jj & 1], w);
-            group_sync(bar_id, NT);
-            const int v = flags[jj & 1];
-            if (tid == 0) flags[(jj + 1) & 1] = 0;
-            cnt = __popc(v & 7);
-        }
-        const bool mixed = cnt != 1;
-
-        // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
-        for (int r = mixed ? tid : RX * RY; r < RX * RY; r += NT) {
-            const int rx = r % RX, ry = r / RX;
-            float gxk[kNF], gyk[kNF], Txx, Txy, Tyy;
-            stress_at<HX, CX, CY>(P, st, ch, cl, rh, df, rx, ry, gxk, gyk, Txx, Txy, Tyy);
-            s_txx[g][ry][rx] = Txx;
-            s_txy[g][ry][rx] = Txy;
-            s_tyy[g][ry][rx] = Tyy;
-        }
-        group_sync(bar_id, NT);
-
-        // ---- phase 3: force, collision, recolouring, 27 stores per fluid node ----
-        if (own_fluid) {
-            float Fx = 0.0f, Fy = 0.0f, gr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-            if (mixed) {
-                div_stress<RX>(s_txx[g], s_txy[g], s_tyy[g], lx + 1, ly + 1, Fx, Fy);
-                // own colour gradients, the phase-2 stencil at a fluid node
-                float gxk[kNF], gyk[kNF];
-                if (df) {
-#pragma unroll
-                    for (int k = 0; k < kNF; k++) grad9_df<CX>(ch[k], cl[k], lx + 2, ly + 2, gxk[k], gyk[k]);
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kNF; k++) grad9_f<CX>(ch[k], lx + 2, ly + 2, gxk[k], gyk[k]);
-                }
-#pragma unroll
-                for (int k = 0; k < kNF; k++) {
-                    gr[2 * k] = gxk[k];
-                    gr[2 * k + 1] = gyk[k];
-                }
-            }
-            float ux, uy;
-            const Recolour rc = collide_node(P, f, r0, r1, r2, Fx, Fy, gr, ux, uy);
-            const int i = (y0 + ly) * nx + x0 + lx;
-            if (uout) {
-                uout[i] = ux;
-                uout[P.N + i] = uy;
-            }
-            float* o = fout + i;
-#pragma unroll
-            for (int k = 0; k < kNF; k++)
-#pragma unroll
-                for (int a = 0; a < kQ; a++)
-                    o[P.off_plane[k * kQ + a]] =
-                        rc.C[k] * f[a] + wq(a) * (rc.Vx[k] * (float)ex(a) + rc.Vy[k] * (float)ey(a));
-        }
-    }
-}
-
 // ------------------------------------------------------------------------------------------
 // initial state, fields, diagnostics
 // ------------------------------------------------------------------------------------------
@@ -1757,13 +1448,12 @@ void with_store(int store, const Pop& p, long long N, Fn fn)
 
 void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
                 const float* wang, const Pop& f, const uint8_t* type, double* Cw, WetCache* cache,
-                int* tile_df, cudaStream_t s)
+                cudaStream_t s)
 {
     if (nw <= 0) return;
     const long long threads = 4LL * nw;
     with_store(store, f, P.N, [&](auto st) {
-        k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw, cache,
-                                                                tile_df);
+        k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw, cache);
     });
 }
 
@@ -2032,30 +1722,6 @@ void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks
     if (ntiles <= 0) return;
     const int nb = nblocks < ntiles ? nblocks : ntiles;
     k_step_ring<kTX, kTY><<<nb, 2 * kTX * kTY + 32, step_ring_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin);
-}
-
-size_t step_wall_ring_smem_bytes()
-{
-    const size_t nbox = ((size_t)kQ * kNF * (kTY + 6) * (kTX + 8) + 31) / 32 * 32;
-    const size_t nbuf = nbox + (size_t)(kTX + 32) * (kTY + 6) / 4;
-    return (size_t)kRingBufs * nbuf * sizeof(float) + 128u;
-}
-
-cudaError_t step_wall_ring_prepare()
-{
-    return cudaFuncSetAttribute(k_step_wall_ring<kTX, kTY>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)step_wall_ring_smem_bytes());
-}
-
-void launch_step_wall_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
-                           const double* Cw, float* u, int* tile_df, const CUtensorMap& tin,
-                           const CUtensorMap& ttype, cudaStream_t s)
-{
-    if (ntiles <= 0) return;
-    int nb = nblocks < ntiles ? nblocks : ntiles;
-    if (nb < (ntiles + kWallJobs - 1) / kWallJobs) nb = (ntiles + kWallJobs - 1) / kWallJobs;
-    k_step_wall_ring<kTX, kTY><<<nb, 2 * kTX * kTY + 32, step_wall_ring_smem_bytes(), s>>>(
-        P, tiles, ntiles, fout.f, Cw, u, tile_df, tin, ttype);
 }
 
 size_t step_tma16_smem_bytes()

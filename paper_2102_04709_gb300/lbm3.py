@@ -256,9 +256,8 @@ class Lbm3:
         _check(self._h, load().lbm3_info(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return {"n_fluid": int(out[0]), "n_wall": int(out[1]), "step_bytes": int(out[2]),
                 "step_kernels": int(out[3]), "wet_kernels": int(out[4]), "device_bytes": int(out[5]),
-                "pure_bytes": int(out[6]), "pure_nodes": int(out[7]), "tma": bool(out[8] & 3),
-                "pure_kernel": {0: "plain", 1: "bulk copies", 2: "ring"}[int(out[8]) & 3],
-                "wall_ring": bool(out[8] & 4)}
+                "pure_bytes": int(out[6]), "pure_nodes": int(out[7]), "tma": bool(out[8]),
+                "pure_kernel": {0: "plain", 1: "bulk copies", 2: "ring"}[int(out[8])]}
 
     def set_stream(self, stream):
         _check(self._h, load().lbm3_set_stream(self._h, stream))
