@@ -107,7 +107,9 @@ int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3]);
 
 /* lbm3_step_timed with the other tiles split by kind: ms_out[0] = wetting pass, ms_out[1] = pure
  * tiles, ms_out[2] = wall tiles (solids within 3 nodes, halo inside the domain), ms_out[3] = edge
- * tiles (halo crossing the domain edge), summed over the steps in ms.  Synchronises. */
+ * tiles (halo crossing the domain edge; on a second internal stream, concurrently with the wall
+ * tiles once the wetting pass is done), summed over the steps in ms.  Synchronises.  lbm3_step_timed's
+ * ms_out[2] is the sum of the last two. */
 int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[4]);
 
 /* Copy the current post-streaming densities rho_k (host [3][ny][nx], 0 at solid nodes) and the

@@ -56,6 +56,10 @@ struct lbm3 {
     long long pure_fluid = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // the edge tiles run on a second side stream once the wetting pass is done, concurrently with
+    // the wall tiles (the two sets are independent)
+    cudaStream_t side2 = nullptr;
+    cudaEvent_t ev_wet = nullptr, ev_join2 = nullptr;
     // CUDA graphs of kGraphSteps consecutive steps (an even count: a graph starts and ends on the
     // same population buffer), one per starting buffer, captured on the internal stream gcap
     // when lbm3_step first needs them and replayed on the caller's stream; dropped when a
@@ -143,6 +147,9 @@ void release(lbm3* h)
     if (h->gcap) cudaStreamDestroy(h->gcap);
     if (h->ev_fork) cudaEventDestroy(h->ev_fork);
     if (h->ev_join) cudaEventDestroy(h->ev_join);
+    if (h->ev_wet) cudaEventDestroy(h->ev_wet);
+    if (h->ev_join2) cudaEventDestroy(h->ev_join2);
+    if (h->side2) cudaStreamDestroy(h->side2);
     if (h->side) cudaStreamDestroy(h->side);
 }
 
@@ -223,8 +230,8 @@ bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtens
 
 // One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
 // while the side stream runs the wetting pass and then the remaining tiles, join.  With ev != NULL
-// the launches are bracketed by the events ev[0..5] (main: 0-1 pure tiles; side: 2-3 wetting pass,
-// 3-4 wall tiles, 4-5 edge tiles).
+// the launches are bracketed by the events ev[0..6] (main: 0-1 pure tiles; side: 2-3 wetting pass,
+// 3-4 wall tiles; second side stream: 5-6 edge tiles).
 cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 {
     cudaError_t e;
@@ -249,12 +256,25 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if (ev) cudaEventRecord(ev[2], h->side);
     launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side);
     if (ev) cudaEventRecord(ev[3], h->side);
+    const bool edges = h->n_gen > h->n_walltiles;
+    if (edges) {
+        if ((e = cudaEventRecord(h->ev_wet, h->side)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->side2, h->ev_wet, 0)) != cudaSuccess) return e;
+    }
     launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
                 h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
-    launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge, fin,
-                fo, h->type, h->Cw, u, h->side);
-    if (ev) cudaEventRecord(ev[5], h->side);
+    if (edges) {
+        if (ev) cudaEventRecord(ev[5], h->side2);
+        launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge,
+                    fin, fo, h->type, h->Cw, u, h->side2);
+        if (ev) cudaEventRecord(ev[6], h->side2);
+        if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->stream, h->ev_join2, 0)) != cudaSuccess) return e;
+    } else if (ev) {
+        cudaEventRecord(ev[5], h->side);
+        cudaEventRecord(ev[6], h->side);
+    }
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
     h->cur = 1 - h->cur;
@@ -550,10 +570,13 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         int lo = 0, hi = 0;
         e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&h->side2, cudaStreamNonBlocking, hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->gcap, cudaStreamNonBlocking);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_wet, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->ev_join2, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMemcpy(h->type, cls.data(), N, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !widx.empty()) e = cudaMemcpy(h->widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !wnrm.empty()) e = cudaMemcpy(h->wnrm, wnrm.data(), wnrm.size() * sizeof(double), cudaMemcpyHostToDevice);
@@ -661,13 +684,13 @@ int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[4])
     if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
     for (int j = 0; j < 4; j++) ms_out[j] = 0.0;
-    std::vector<cudaEvent_t> ev(6 * (size_t)nsteps);
+    std::vector<cudaEvent_t> ev(7 * (size_t)nsteps);
     for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
-    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[6 * (size_t)s]));
+    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[7 * (size_t)s]));
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     for (int s = 0; s < nsteps; s++) {
-        const cudaEvent_t* E = &ev[6 * (size_t)s];
-        const int from[4] = {2, 0, 3, 4}, to[4] = {3, 1, 4, 5};
+        const cudaEvent_t* E = &ev[7 * (size_t)s];
+        const int from[4] = {2, 0, 3, 5}, to[4] = {3, 1, 4, 6};
         for (int j = 0; j < 4; j++) {
             float t = 0.f;
             CUDA_TRY(h, cudaEventElapsedTime(&t, E[from[j]], E[to[j]]));
