@@ -497,6 +497,13 @@ __device__ __forceinline__ void stress_at(const Params& P, const uint8_t (*t)[HX
     pair_stress(P.sig12, c[1], c[2], gxk[1], gyk[1], gxk[2], gyk[2], rho2, Txx, Txy, Tyy);
 }
 
+// resident blocks per SM the wall-tile specialisation of the one-tile-per-block step kernel is
+// compiled for (registers capped at 65536 / (256 x this)); the others for four
+#ifndef LBM3_STEP_BLOCKS_PER_SM
+#define LBM3_STEP_BLOCKS_PER_SM 5
+#endif
+constexpr int kStepBlocksPerSm = LBM3_STEP_BLOCKS_PER_SM;
+
 // One CTA per TX x TY tile of interior nodes.
 //   phase 0: class bytes (and, for tiles touching the domain edge, storage indices and seam
 //            parities) of the halo-3 region into shared memory
@@ -510,7 +517,7 @@ __device__ __forceinline__ void stress_at(const Params& P, const uint8_t (*t)[HX
 // wall values (a contact line at or near it) carry the float-float phase fields, decided anew
 // every step from the wall values of this step's wetting pass.
 template <int TX, int TY, bool PURE, bool INNER, int STORE>
-__global__ void __launch_bounds__(TX* TY) k_step(const Params P, const int* __restrict__ tiles,
+__global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 4) k_step(const Params P, const int* __restrict__ tiles,
                                                   const Pop fin, const Pop fout,
                                                   const uint8_t* __restrict__ type,
                                                   const double* __restrict__ Cw,
