@@ -66,8 +66,10 @@ __device__ __forceinline__ bool node_is_fluid(const Params& P, const uint8_t* __
 // C_k at the fluid node at unwrapped (X, Y), in the frame of the home domain.  The populations
 // are summed with error-free transformations and divided with the FMA residual, so the value is
 // the FP64 fraction of the stored FP32 populations (a node holding one fluid gives exactly 0 or 1).
+// (kept out of line: the wetting pass calls it up to ten times per lane, and inlining each call
+// made that kernel wait on its instruction cache)
 template <class S>
-__device__ double node_C(const Params& P, const S& st, const uint8_t* __restrict__ type, int X,
+__device__ __noinline__ double node_C(const Params& P, const S& st, const uint8_t* __restrict__ type, int X,
                          int Y, int k)
 {
     float q[27];

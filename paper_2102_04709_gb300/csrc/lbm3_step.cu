@@ -534,8 +534,10 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
     __shared__ float s_g[2 * kNF][TY][TX];   // colour gradients of the tile's own nodes
+    __shared__ int s_flags[2];                // fluids present (wall and edge tiles)
 
     const int tid = threadIdx.x + TX * threadIdx.y;
+    if (!PURE && tid == 0) s_flags[0] = 0;  // published by the phase-0 barrier
     const int ntx = (P.nx + TX - 1) / TX;
     const int tile = tiles[blockIdx.x];
     const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
@@ -718,7 +720,9 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
         r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
         r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
     }
-    const bool mixed = single_fluid_or(present) != 1;
+    // fluids present in the phase-field region: one barrier for tiles that had one already (the
+    // word was cleared before the phase-0 barrier), three for the pure tiles of the plain path
+    const bool mixed = (PURE ? single_fluid_or(present) : fluids_present(present, s_flags, 0, tid)) != 1;
 
     // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
     for (int j = mixed ? tid : RX * RY; j < RX * RY; j += NT) {
