@@ -1426,18 +1426,28 @@ __global__ void __launch_bounds__(kDiagThreads) k_diag(const Params P, const S s
     if (threadIdx.x < 8) partials[blockIdx.x * 8 + threadIdx.x] = sh[threadIdx.x][0];
 }
 
+// one warp: lane j strides over the block partials, then a shuffle reduction
 __global__ void k_diag_final(const int nb, const double* __restrict__ partials, double* __restrict__ out)
 {
-    if (threadIdx.x != 0) return;
     double acc[8] = {0, 0, 0, 0, 0, 0, DBL_MAX, 0};
-    for (int b = 0; b < nb; b++) {
+    for (int b = threadIdx.x; b < nb; b += 32) {
         const double* q = partials + 8 * b;
+#pragma unroll
         for (int j = 0; j < 5; j++) acc[j] += q[j];
         acc[5] = fmax(acc[5], q[5]);
         acc[6] = fmin(acc[6], q[6]);
         acc[7] += q[7];
     }
-    for (int j = 0; j < 8; j++) out[j] = acc[j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int j = 0; j < 5; j++) acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], o);
+        acc[5] = fmax(acc[5], __shfl_xor_sync(0xffffffffu, acc[5], o));
+        acc[6] = fmin(acc[6], __shfl_xor_sync(0xffffffffu, acc[6], o));
+        acc[7] += __shfl_xor_sync(0xffffffffu, acc[7], o);
+    }
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 8; j++) out[j] = acc[j];
 }
 
 }  // namespace
