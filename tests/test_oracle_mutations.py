@@ -29,12 +29,12 @@ MUTATIONS = [
      "return mu / (rho * CS2) + 1.0;",
      "test_shear_wave_decay", ()),
     ("s_4 = s_1 instead of Eq.6's 8(2 - s_1)/(8 - s_1)",
-     "double s4 = 8.0 * (2.0 - s1) / (8.0 - s1);",
-     "double s4 = s1;",
+     "real s4 = 8.0 * (2.0 - s1) / (8.0 - s1);",
+     "real s4 = s1;",
      "test_halfway_walls_in_poiseuille_flow", ()),
     ("an arithmetic instead of a harmonic mixture viscosity in Eq.7",
-     "for (int k = 0; k < NF; k++) inv += rk[k] / (o->rho0[k] * o->nu[k]);\n    double mu = rho / inv;",
-     "for (int k = 0; k < NF; k++) inv += rk[k] * (o->rho0[k] * o->nu[k]);\n    double mu = inv / rho;",
+     "for (int k = 0; k < NF; k++) inv += rk[k] / (o->rho0[k] * o->nu[k]);\n    real mu = rho / inv;",
+     "for (int k = 0; k < NF; k++) inv += rk[k] * (o->rho0[k] * o->nu[k]);\n    real mu = inv / rho;",
      "test_mixture_viscosity_is_harmonic", ()),
     ("the Eq.12 stencil without its 1/c_s^2",
      "g[0] += WQ[a] * v[a] * EX[a] / CS2;\n        g[1] += WQ[a] * v[a] * EY[a] / CS2;",
@@ -45,16 +45,16 @@ MUTATIONS = [
      "T[0] += s * (1.0 + nx * nx);",
      "test_laplace_law", ()),
     ("A_kl of Eq.10 without its factor 1e6",
-     "double A = fmin(1e6 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);",
-     "double A = fmin(1.0 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);",
+     "real A = fmin(1e6 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);",
+     "real A = fmin(1.0 * rk[k] * rk[l] / (o->rho0[k] * o->rho0[l]), 1.0);",
      "test_laplace_law", ()),
     ("halfway bounce-back that does not reverse the population",
      "o->fnew[((size_t)k * Q + o->opp[a]) * n + i] = v;",
      "o->fnew[((size_t)k * Q + a) * n + i] = v;",
      "test_uniform_fluid_at_rest_stays_at_rest", ()),
     ("the triple-point term of Eq.14 with 3.5 for 35",
-     "double trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);",
-     "double trip = fmin(3.5 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);",
+     "real trip = fmin(35.0 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);",
+     "real trip = fmin(3.5 * rk[0] * rk[1] * rk[2] / (rho * rho * rho), 1.0);",
      "test_beta_table", ()),
     ("the X > 0 branch of g(X) in Eq.15 with the wrong sign",
      "    if (X <= 1.0) return sin(acos(X)) - 1.0;",
@@ -65,12 +65,12 @@ MUTATIONS = [
      "v -= beta * WQ[a] * rk[k] * rk[l] / rho * ne;",
      "test_flat_interface_segregation_balance", ()),
     ("the Zou-He inlet population with the wrong sign of U",
-     "double g1 = f[3] + 2.0 / 3.0 * rho * U;",
-     "double g1 = f[3] - 2.0 / 3.0 * rho * U;",
+     "real g1 = f[3] + 2.0 / 3.0 * rho * U;",
+     "real g1 = f[3] - 2.0 / 3.0 * rho * U;",
      "test_zou_he_uniform_inflow", ()),
     ("the Zou-He outlet population with the wrong sign of u",
-     "double h3 = f[1] - 2.0 / 3.0 * ro * ux;",
-     "double h3 = f[1] + 2.0 / 3.0 * ro * ux;",
+     "real h3 = f[1] - 2.0 / 3.0 * ro * ux;",
+     "real h3 = f[1] + 2.0 / 3.0 * ro * ux;",
      "test_zou_he_uniform_inflow", ()),
     ("Eq.21 for fluid 1 weighted by the wrong fluid",
      "        th[1] = t_gr + Cb / (Cb + Cr) * (t_gb - t_gr);",
@@ -105,8 +105,8 @@ MUTATIONS = [
      "            s += c_at(o, idx, sw, k);\n            ws += 1.0;",
      "test_initial_wall_values_weighted_mean", ()),
     ("the third wall value without C_1 in 1 - C_0 - C_1",
-     "        double cb = fmax(0.0, 1.0 - cr - cg);",
-     "        double cb = fmax(0.0, 1.0 - cr);",
+     "        real cb = fmax(0.0, 1.0 - cr - cg);",
+     "        real cb = fmax(0.0, 1.0 - cr);",
      "test_wall_values_close_to_one", ()),
     ("Eq.22's max and min exchanged",
      "return theta_k <= 90.0 ? fmax(c1, c2) : fmin(c1, c2);",
@@ -117,8 +117,8 @@ MUTATIONS = [
      "    o->sigma[0][2] = o->sigma[2][0] = sigma[2];\n    o->sigma[1][2] = o->sigma[2][1] = sigma[1];",
      "test_neumann_lens", ((0.010, 0.012, 0.008),)),
     ("the Eq.10 stress of a pair weighted by the tension of another pair",
-     "double s = 0.5 * o->sigma[k][l] * A * Gn;",
-     "double s = 0.5 * o->sigma[k][3 - k - l] * A * Gn;",
+     "real s = 0.5 * o->sigma[k][l] * A * Gn;",
+     "real s = 0.5 * o->sigma[k][3 - k - l] * A * Gn;",
      "test_neumann_lens", ((0.010, 0.012, 0.008),)),
     ("X_kl of Eq.15 built around the wrong pair (sigma_kl and sigma_ml exchanged)",
      "            double X = (o->sigma[m][k] * o->sigma[m][k] + o->sigma[m][l] * o->sigma[m][l] -\n                        o->sigma[k][l] * o->sigma[k][l]) /\n                       (2.0 * o->sigma[m][k] * o->sigma[m][l]);",
