@@ -154,12 +154,15 @@ int lbm3_set_inflow(lbm3* h, double u_in);
  * J = sum_x x rho_0(x) / sum_x rho_0(x), the x-centroid of fluid 0 over the post-streaming fluid
  * nodes of the final state, and returns dJ/d(theta_01, theta_20, theta_12) for every C_SB node
  * (host [n_wall][3], lbm3_wall_nodes order) and dJ/du_in (0 unless LBM3_BC_ZOUHE).  The states
- * at every checkpoint_every-th step are kept on the device; each segment is recomputed forward
- * by the step kernels and then traversed backward by the adjoint kernels (vector-Jacobian
- * products of Eq.1-16, 21, 22 and the characteristic lines, FP32 with FP64 accumulators).
+ * at every checkpoint_every-th step are kept on the device, and the forward pass keeps every
+ * state of the last segment; each other segment is recomputed forward by the step kernels from
+ * its checkpoint, and every segment is then traversed backward by the adjoint kernels
+ * (vector-Jacobian products of Eq.1-16, 21, 22 and the characteristic lines, FP32 with FP64
+ * accumulators).  checkpoint_every >= nsteps keeps every state and recomputes nothing.
  * FP32 storage only, not with LBM3_BC_MODPER.  On return the simulation holds its final state.
- * Device memory: about nsteps / checkpoint_every + checkpoint_every states (132 B per node each)
- * plus ~300 B per node of work arrays, allocated and released by the call.  Synchronises. */
+ * Device memory: about nsteps / checkpoint_every + min(checkpoint_every, nsteps) states (132 B
+ * per node each) plus ~300 B per node of work arrays, allocated and released by the call.
+ * Synchronises. */
 int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, double* J_out,
                           double* dJ_dangles, double* dJ_du);
 

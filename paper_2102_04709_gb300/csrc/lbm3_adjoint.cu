@@ -24,6 +24,12 @@ namespace lbm3k {
 
 namespace {
 
+// the last march of a wetting lane: the same angle gives the same line, crossing and derivative
+struct AdjLine {
+    double th, fr, dfr;
+    int kind, ax, ay, bx, by, pad;
+};
+
 struct Adj {
     int nxp;  // nx + 2
     // forward intermediates
@@ -32,7 +38,7 @@ struct Adj {
     float* rho;    // [NP]
     float* g;      // [6][NP]   (dC0/dx, dC0/dy, dC1/dx, ...)
     float* T;      // [3][NP]
-    float* F;      // [2][N]
+    AdjLine* wline;  // [4 Nw] by lane 4 w + 2 k + side
     // wetting decisions, lane = 2 k + side
     int* wkind;    // [4][Nw]
     int* wa;       // [4][Nw] in-domain node index of the first bracketing node
@@ -46,8 +52,7 @@ struct Adj {
     // adjoint fields
     float* l_fpost;  // [27][N]
     float* l_F;      // [2][N]
-    float* l_g;      // [6][NP]
-    float* l_T;      // [3][NP]
+    float* l_g;      // [6][NP]  (written at fluid positions only; zero elsewhere)
     float* l_C;      // [3][NP]
     float* l_rho;    // [NP]
     float* l_fs;     // [27][N] adjoint of the stored populations
@@ -59,37 +64,63 @@ struct Adj {
 
 __device__ __forceinline__ int pad(const Adj& A, int x, int y) { return y * A.nxp + x + 1; }
 
+// The lattice position (X, Y), unwrapped, brought into the domain in place, as locate() does but
+// without dividing its index back into coordinates: 0 inside, 1 solid beyond a wall side (X, Y
+// then meaningless), 2 beyond an open x side (X clamped to the boundary column).  (The adjoint
+// has no modified-periodic seam.)
+__device__ __forceinline__ int wrap_xy(const Params& P, int& X, int& Y)
+{
+    if (Y < 0 || Y >= P.ny) {
+        if (!P.per_y) return 1;
+        Y -= floordiv_i(Y, P.ny) * P.ny;
+    }
+    if (X < 0 || X >= P.nx) {
+        if (P.bc_x == kWalls) return 1;
+        if (P.bc_x == kZouHe) {
+            X = X < 0 ? 0 : P.nx - 1;
+            return 2;
+        }
+        X -= floordiv_i(X, P.nx) * P.nx;
+    }
+    return 0;
+}
+
 // position of C / rho seen from an unwrapped lattice position: kind 0 = an in-domain node
 // (padded index), 1 = solid beyond a wall side; beyond an open side: the boundary-column node
 __device__ __forceinline__ int cpos(const Params& P, const Adj& A, int X, int Y, int& kind)
 {
-    const Loc L = locate(P, X, Y);
-    kind = L.kind == 1 ? 1 : 0;
-    if (kind) return 0;
-    return pad(A, L.idx % P.nx, L.idx / P.nx);
+    kind = wrap_xy(P, X, Y) == 1;
+    return kind ? 0 : pad(A, X, Y);
 }
 
 // position of T seen from an unwrapped lattice position: the ghost columns are their own slots
 __device__ __forceinline__ int tpos(const Params& P, const Adj& A, int X, int Y)
 {
     if (P.bc_x == kZouHe && (X == -1 || X == P.nx)) {
-        const Loc L = locate(P, 0, Y);
-        return pad(A, X, L.idx / P.nx);
+        int x0 = 0;
+        if (wrap_xy(P, x0, Y) == 1) Y = 0;
+        return pad(A, X, Y);
     }
-    const Loc L = locate(P, X, Y);
-    return pad(A, L.idx % P.nx, L.idx / P.nx);
+    if (wrap_xy(P, X, Y) == 1) return pad(A, 0, 0);
+    return pad(A, X, Y);
 }
 
 // ------------------------------------------------------------------------------------------
 // forward intermediates
 // ------------------------------------------------------------------------------------------
-// A1: post-streaming populations, densities and fractions (fluid nodes and ghost columns)
+// A1: post-streaming populations, densities and fractions (fluid nodes and ghost columns); also
+// clears the step's adjoint accumulators lambda_C, lambda_rho at every padded position
 __global__ void a_dens(const Params P, const Adj A, const float* __restrict__ fs,
                        const uint8_t* __restrict__ type)
 {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, y = blockIdx.y;
     if (gx > P.nx || y >= P.ny) return;
     const int p = pad(A, gx, y);
+    {
+        const int NP = P.ny * A.nxp;
+        for (int k = 0; k < kNF; k++) A.l_C[k * NP + p] = 0.0f;
+        A.l_rho[p] = 0.0f;
+    }
     const bool ghost = gx < 0 || gx >= P.nx;
     if (ghost && P.bc_x != kZouHe) return;
     const int x = gx < 0 ? 0 : (gx >= P.nx ? P.nx - 1 : gx);
@@ -138,23 +169,30 @@ __global__ void a_wet(const Params P, const Adj A, int nw, const int* __restrict
         const double Cr = cw_lag[i], Cg = cw_lag[P.N + i], Cb = cw_lag[2 * P.N + i];
         const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
         th = k == 0 ? local_angle(Cb, 180.0 - t_br, Cg, t_rg) : local_angle(Cb, t_gb, Cr, 180.0 - t_rg);
-        const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
-        const double dev = fabs(90.0 - th);
-        const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
-        const double sg = side ? -1.0 : 1.0;
-        double sn, cs;
-        sincos(phi, &sn, &cs);
-        const double dx = cs * nx_ - sg * sn * ny_, dy = cs * ny_ + sg * sn * nx_;
-        cr = characteristic_line<Store<kStoreF32>>(P, type, px, py, dx, dy);
-        if (cr.kind == 2 && dev >= kPhiSnap) {
-            // d(position along the crossed line)/d phi, then d phi / d theta_k
-            const double ddx = -sn * nx_ - sg * cs * ny_, ddy = -sn * ny_ + sg * cs * nx_;
-            double ds;
-            if (cr.ax == cr.bx)
-                ds = (double)(cr.ax - px) * (ddy * dx - dy * ddx) / (dx * dx);
-            else
-                ds = (double)(cr.ay - py) * (ddx * dy - dx * ddy) / (dy * dy);
-            dfr = ds * (90.0 - th > 0 ? -1.0 : 1.0) * (M_PI / 180.0);
+        const AdjLine c = A.wline[g];
+        if (c.th == th) {
+            cr = Crossing{c.kind, c.ax, c.ay, c.bx, c.by, c.fr};
+            dfr = c.dfr;
+        } else {
+            const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
+            const double dev = fabs(90.0 - th);
+            const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
+            const double sg = side ? -1.0 : 1.0;
+            double sn, cs;
+            sincos(phi, &sn, &cs);
+            const double dx = cs * nx_ - sg * sn * ny_, dy = cs * ny_ + sg * sn * nx_;
+            cr = characteristic_line<Store<kStoreF32>>(P, type, px, py, dx, dy);
+            if (cr.kind == 2 && dev >= kPhiSnap) {
+                // d(position along the crossed line)/d phi, then d phi / d theta_k
+                const double ddx = -sn * nx_ - sg * cs * ny_, ddy = -sn * ny_ + sg * cs * nx_;
+                double ds;
+                if (cr.ax == cr.bx)
+                    ds = (double)(cr.ax - px) * (ddy * dx - dy * ddx) / (dx * dx);
+                else
+                    ds = (double)(cr.ay - py) * (ddx * dy - dx * ddy) / (dy * dy);
+                dfr = ds * (90.0 - th > 0 ? -1.0 : 1.0) * (M_PI / 180.0);
+            }
+            A.wline[g] = AdjLine{th, cr.fr, dfr, cr.kind, cr.ax, cr.ay, cr.bx, cr.by, 0};
         }
     }
     double ca = 0.0, cb = 0.0;
@@ -210,40 +248,46 @@ __device__ __forceinline__ bool is_active(const Params& P, const Adj& A, const u
     return cls != kSI;
 }
 
-// gather of the 9-point stencil of C_k around the position (gx, gy) (in-domain or ghost):
-// v[a] = m[a] C[src[a]] - C[src2[a]], the second term only where src2[a] >= 0.  At a C_SB centre
-// a neighbour without a value of its own (C_SI, or solid beyond a wall side) is the
+// The 9-point stencil of C around the position (gx, gy) (in-domain or ghost), the same for every
+// fluid: value a is m[a] C[src[a]] - C[src2[a]], the second term only where src2[a] >= 0.  At a
+// C_SB centre a neighbour without a value of its own (C_SI, or solid beyond a wall side) is the
 // extrapolation 2 C(centre) - C(opposite neighbour), or C(centre) when the opposite neighbour
 // has no value either.
-__device__ __forceinline__ void stencil_C(const Params& P, const Adj& A, const uint8_t* type, int gx,
-                                          int gy, int cls, int k, float v[kQ], int src[kQ], int src2[kQ],
-                                          float m[kQ])
+__device__ __forceinline__ void stencil_geom(const Params& P, const Adj& A, const uint8_t* type, int gx,
+                                             int gy, int cls, int src[kQ], int src2[kQ], float m[kQ])
 {
-    const int NP = P.ny * A.nxp;
     int kind;
     const int pc = cpos(P, A, gx, gy, kind);
     // kd == 1: solid beyond a wall side; otherwise the class of the node (or of the boundary
     // column node a ghost copies)
-    auto no_value = [&](int kd, int q) { return kd == 1 || (type[(q / A.nxp) * P.nx + q % A.nxp - 1] & 3) == kSI; };
+    auto no_value = [&](int kd, int X, int Y) { return kd == 1 || (type[Y * P.nx + X] & 3) == kSI; };
     for (int a = 0; a < kQ; a++) {
-        int kd;
-        int q = cpos(P, A, gx + ex(a), gy + ey(a), kd);
+        int X = gx + ex(a), Y = gy + ey(a);
+        const int kd = wrap_xy(P, X, Y);
+        int q = kd == 1 ? 0 : pad(A, X, Y);
         int q2 = -1;
         float mm = 1.0f;
-        if (cls == kSB && a > 0 && no_value(kd, q)) {
-            int kd2;
-            const int qo = cpos(P, A, gx - ex(a), gy - ey(a), kd2);
+        if (cls == kSB && a > 0 && no_value(kd, X, Y)) {
+            int Xo = gx - ex(a), Yo = gy - ey(a);
+            const int kd2 = wrap_xy(P, Xo, Yo);
             q = pc;
-            if (!no_value(kd2, qo)) {
-                q2 = qo;
+            if (!no_value(kd2, Xo, Yo)) {
+                q2 = pad(A, Xo, Yo);
                 mm = 2.0f;
             }
         }
         src[a] = q;
         src2[a] = q2;
         m[a] = mm;
-        v[a] = q2 < 0 ? A.C[k * NP + q] : mm * A.C[k * NP + q] - A.C[k * NP + q2];
     }
+}
+
+// values of the stencil for fluid k
+__device__ __forceinline__ void stencil_C(const Params& P, const Adj& A, int k, const int src[kQ],
+                                          const int src2[kQ], const float m[kQ], float v[kQ])
+{
+    const float* C = A.C + k * (P.ny * A.nxp);
+    for (int a = 0; a < kQ; a++) v[a] = src2[a] < 0 ? C[src[a]] : m[a] * C[src[a]] - C[src2[a]];
 }
 
 // A3: gradients (Eq.12) and the Eq.(10) stress at fluid, C_SB and ghost positions
@@ -256,11 +300,12 @@ __global__ void a_grad_stress(const Params P, const Adj A, const uint8_t* __rest
     if (!is_active(P, A, type, gx, y, cls)) return;
     const int NP = P.ny * A.nxp;
     const int p = pad(A, gx, y);
-    float c[kNF], gxk[kNF], gyk[kNF];
+    float c[kNF], gxk[kNF], gyk[kNF], m[kQ];
+    int src[kQ], src2[kQ];
+    stencil_geom(P, A, type, gx, y, cls, src, src2, m);
     for (int k = 0; k < kNF; k++) {
-        float v[kQ], m[kQ];
-        int src[kQ], src2[kQ];
-        stencil_C(P, A, type, gx, y, cls, k, v, src, src2, m);
+        float v[kQ];
+        stencil_C(P, A, k, src, src2, m, v);
         c[k] = v[0];
         gxk[k] = (1.0f / 3.0f) * (v[1] - v[3]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[8] - v[6]));
         gyk[k] = (1.0f / 3.0f) * (v[2] - v[4]) + (1.0f / 12.0f) * ((v[5] - v[7]) + (v[6] - v[8]));
@@ -278,23 +323,18 @@ __global__ void a_grad_stress(const Params P, const Adj A, const uint8_t* __rest
     A.T[2 * NP + p] = Tyy;
 }
 
-// A4: force F = div T at fluid nodes
-__global__ void a_force(const Params P, const Adj A, const uint8_t* __restrict__ type)
+// force F = div T (Eq.10) at the fluid node (x, y), from the stress of its neighbours
+__device__ __forceinline__ void force_at(const Params& P, const Adj& A, int x, int y, float& Fx, float& Fy)
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    const int i = y * P.nx + x;
-    if (type[i] & 2) return;
     const int NP = P.ny * A.nxp;
-    float Fx = 0.f, Fy = 0.f;
+    Fx = 0.f;
+    Fy = 0.f;
     for (int a = 1; a < kQ; a++) {
         const int q = tpos(P, A, x + ex(a), y + ey(a));
         const float c = 3.0f * wq(a);
         Fx += c * (A.T[q] * ex(a) + A.T[NP + q] * ey(a));
         Fy += c * (A.T[NP + q] * ex(a) + A.T[2 * NP + q] * ey(a));
     }
-    A.F[i] = Fx;
-    A.F[P.N + i] = Fy;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -320,7 +360,8 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     for (int a = 0; a < kQ; a++) f[a] = q[a] + q[9 + a] + q[18 + a];
     const float rho = r[0] + r[1] + r[2];
     const float irho = 1.f / rho;  // one division; every other quotient by rho is a product
-    const float Fx = A.F[i], Fy = A.F[P.N + i];
+    float Fx, Fy;
+    force_at(P, A, x, y, Fx, Fy);
     float g[6];
     for (int j = 0; j < 6; j++) g[j] = A.g[j * NP + p];
     float C[kNF];
@@ -492,36 +533,33 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     A.l_F[i] = lFx;
     A.l_F[P.N + i] = lFy;
     for (int k = 0; k < kNF; k++) {
-        A.l_g[(2 * k) * NP + p] += lg[k][0];
-        A.l_g[(2 * k + 1) * NP + p] += lg[k][1];
+        A.l_g[(2 * k) * NP + p] = lg[k][0];
+        A.l_g[(2 * k + 1) * NP + p] = lg[k][1];
     }
 }
 
-// B2: adjoint of the divergence: lambda_T at fluid / C_SB / ghost positions
-__global__ void b_div(const Params P, const Adj A, const uint8_t* __restrict__ type)
+// adjoint of the divergence: lambda_T at the fluid / C_SB / ghost position (gx, y) with padded
+// index p, gathered from the fluid nodes whose force read T there
+__device__ __forceinline__ void div_adjoint(const Params& P, const Adj& A, const uint8_t* type, int gx,
+                                            int y, int p, float lT[3])
 {
-    const int gx = blockIdx.x * blockDim.x + threadIdx.x - 1, y = blockIdx.y;
-    if (gx > P.nx || y >= P.ny) return;
-    int cls;
-    if (!is_active(P, A, type, gx, y, cls)) return;
-    const int NP = P.ny * A.nxp;
-    const int p = pad(A, gx, y);
     float lxx = 0.f, lxy = 0.f, lyy = 0.f;
     for (int a = 1; a < kQ; a++) {
         // the fluid node q = p - e_a looked up T at p in direction a
-        const Loc L = locate(P, gx - ex(a), y - ey(a));
-        if (L.kind != 0 || (type[L.idx] & 2)) continue;
-        const int qx = L.idx % P.nx, qy = L.idx / P.nx;
+        int qx = gx - ex(a), qy = y - ey(a);
+        if (wrap_xy(P, qx, qy) != 0) continue;
+        const int qi = qy * P.nx + qx;
+        if (type[qi] & 2) continue;
         if (tpos(P, A, qx + ex(a), qy + ey(a)) != p) continue;
         const float c = 3.0f * wq(a);
-        const float lFx = A.l_F[L.idx], lFy = A.l_F[P.N + L.idx];
+        const float lFx = A.l_F[qi], lFy = A.l_F[P.N + qi];
         lxx += c * ex(a) * lFx;
         lxy += c * (ey(a) * lFx + ex(a) * lFy);
         lyy += c * ey(a) * lFy;
     }
-    A.l_T[p] = lxx;
-    A.l_T[NP + p] = lxy;
-    A.l_T[2 * NP + p] = lyy;
+    lT[0] = lxx;
+    lT[1] = lxy;
+    lT[2] = lyy;
 }
 
 // VJP of one pair's stress sigma A (|G|^2 I - G G)/|G|
@@ -557,7 +595,8 @@ __device__ __forceinline__ void pair_stress_vjp(float sig, float ck, float cl, f
     lck -= glx * lGx + gly * lGy;
 }
 
-// B3: adjoint of the stress (local part) and of the gradient stencil (scatter into lambda_C)
+// B2: adjoint of the divergence, of the stress (local part) and of the gradient stencil (scatter
+// into lambda_C)
 __global__ void b_stress_grad(const Params P, const Adj A, const uint8_t* __restrict__ type,
                               const float sig01, const float sig02, const float sig12)
 {
@@ -577,18 +616,19 @@ __global__ void b_stress_grad(const Params P, const Adj A, const uint8_t* __rest
         lg[k][0] = A.l_g[(2 * k) * NP + p];
         lg[k][1] = A.l_g[(2 * k + 1) * NP + p];
     }
-    const float lT[3] = {A.l_T[p], A.l_T[NP + p], A.l_T[2 * NP + p]};
+    float lT[3];
+    div_adjoint(P, A, type, gx, y, p, lT);
     float lrho = 0.f;
     const float rho = A.rho[pc];
     pair_stress_vjp(sig01, c[0], c[1], g[0][0], g[0][1], g[1][0], g[1][1], rho, lT, lc[0], lc[1], lg[0], lg[1], lrho);
     pair_stress_vjp(sig02, c[0], c[2], g[0][0], g[0][1], g[2][0], g[2][1], rho, lT, lc[0], lc[2], lg[0], lg[2], lrho);
     pair_stress_vjp(sig12, c[1], c[2], g[1][0], g[1][1], g[2][0], g[2][1], rho, lT, lc[1], lc[2], lg[1], lg[2], lrho);
+    float m[kQ];
+    int src[kQ], src2[kQ];
+    stencil_geom(P, A, type, gx, y, cls, src, src2, m);
     for (int k = 0; k < kNF; k++) {
         if (lc[k] != 0.f) atomicAdd(&A.l_C[k * NP + pc], lc[k]);
         // gradient stencil transpose
-        float v[kQ], m[kQ];
-        int src[kQ], src2[kQ];
-        stencil_C(P, A, type, gx, y, cls, k, v, src, src2, m);
         for (int a = 1; a < kQ; a++) {
             const float w = 3.0f * wq(a) * (ex(a) * lg[k][0] + ey(a) * lg[k][1]);
             if (w != 0.f) {
@@ -696,13 +736,10 @@ __global__ void b_wet(const Params P, const Adj A, int nw, const int* __restrict
     A.l_cw2[2 * P.N + i] = (float)lCb;
 }
 
-// B6: adjoint of rho_k, C_k at fluid nodes (and of the ghost copies) into lambda_fpost
-__global__ void b_frac(const Params P, const Adj A, const uint8_t* __restrict__ type)
+// adjoint of rho_k, C_k at the fluid node (x, y) (the ghost-column copies already sent theirs to
+// it): lr[k] is added to lambda of each of the node's nine post-streaming populations of fluid k
+__device__ __forceinline__ void frac_adjoint(const Params& P, const Adj& A, int x, int y, float lr[kNF])
 {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    const int i = y * P.nx + x;
-    if (type[i] & 2) return;
     const int NP = P.ny * A.nxp;
     const int p = pad(A, x, y);
     float lC[kNF], C[kNF];
@@ -710,19 +747,15 @@ __global__ void b_frac(const Params P, const Adj A, const uint8_t* __restrict__ 
         lC[k] = A.l_C[k * NP + p];
         C[k] = A.C[k * NP + p];
     }
-    // (the ghost-column copies already sent their adjoint to this node)
     const float lrho = A.l_rho[p];
     const float rho = A.rho[p];
     float sc = 0.f;
     for (int k = 0; k < kNF; k++) sc += lC[k] * C[k];
-    for (int k = 0; k < kNF; k++) {
-        const float lr = (lC[k] - sc) / rho + lrho;
-        for (int a = 0; a < kQ; a++) A.l_fpost[(long long)(9 * k + a) * P.N + i] += lr;
-    }
+    for (int k = 0; k < kNF; k++) lr[k] = (lC[k] - sc) / rho + lrho;
 }
 
-// B7a: adjoint of the Zou-He completion at the open columns (lambda of the known populations
-// and of the inflow velocity)
+// B6: adjoint of the Zou-He completion at the fluid nodes of the open columns (lambda of the known
+// populations and of the inflow velocity), after adding the adjoint of the fractions there
 __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__ type)
 {
     if (P.bc_x != kZouHe) return;
@@ -731,14 +764,17 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     const bool inlet = t < P.ny;
     const int y = inlet ? t : t - P.ny;
-    const bool valid = y < P.ny;
-    const int i = y * P.nx + (inlet ? 0 : P.nx - 1);
+    const int xb = inlet ? 0 : P.nx - 1;
+    const int i = y * P.nx + xb;
+    const bool valid = y < P.ny && !(type[i] & 2);
     float fk[27], lk[27];
     if (valid) {
+        float lr[kNF];
+        frac_adjoint(P, A, xb, y, lr);
 #pragma unroll
         for (int j = 0; j < 27; j++) {
             fk[j] = A.fpost[(long long)j * P.N + i];
-            lk[j] = A.l_fpost[(long long)j * P.N + i];
+            lk[j] = A.l_fpost[(long long)j * P.N + i] + lr[j / 9];
         }
     }
     float f[kQ];
@@ -827,23 +863,34 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
         }
 }
 
-// B7b: adjoint of the pull: the stored population (s, a) was read by exactly one puller
+// B7: adjoint of the pull: the stored population (s, a) was read by exactly one puller, whose
+// lambda_fpost gets the adjoint of its fractions added here (at the open columns b_zouhe did)
 __global__ void b_pull(const Params P, const Adj A, const uint8_t* __restrict__ type)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     const int i = y * P.nx + x;
     const bool solid = type[i] & 2;
+    const bool zh = P.bc_x == kZouHe;
+    float lr_own[kNF] = {0.f, 0.f, 0.f};
+    if (!solid && !(zh && (x == 0 || x == P.nx - 1))) frac_adjoint(P, A, x, y, lr_own);
     for (int a = 0; a < kQ; a++) {
-        const Loc d = locate(P, x + ex(a), y + ey(a));
-        for (int k = 0; k < kNF; k++) {
-            float v = 0.f;
-            if (!solid) {
-                if (d.kind == 1 || (d.kind == 0 && (type[d.idx] & 2)))
-                    v = A.l_fpost[(long long)(9 * k + opp(a)) * P.N + i];
-                else if (d.kind == 0)
-                    v = A.l_fpost[(long long)(9 * k + a) * P.N + d.idx];
+        int X = x + ex(a), Y = y + ey(a);
+        const int dk = wrap_xy(P, X, Y);
+        int src = -1, dir = a;
+        float lr[kNF] = {0.f, 0.f, 0.f};
+        if (!solid) {
+            if (dk == 1 || (dk == 0 && (type[Y * P.nx + X] & 2))) {
+                src = i;
+                dir = opp(a);
+                for (int k = 0; k < kNF; k++) lr[k] = lr_own[k];
+            } else if (dk == 0) {
+                src = Y * P.nx + X;
+                if (!(zh && (X == 0 || X == P.nx - 1))) frac_adjoint(P, A, X, Y, lr);
             }
+        }
+        for (int k = 0; k < kNF; k++) {
+            const float v = src < 0 ? 0.f : A.l_fpost[(long long)(9 * k + dir) * P.N + src] + lr[k];
             A.l_fs[(long long)(9 * k + a) * P.N + i] = v;
         }
     }
@@ -865,11 +912,20 @@ __global__ void b_seed(const Params P, const Adj A, const uint8_t* __restrict__ 
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// host-side driver of one reverse step and of the seed
+// host-side driver
 // ------------------------------------------------------------------------------------------
+// The forward intermediates of a step depend only on its stored state, not on the adjoint, so
+// they are computed on a stream of their own one step ahead of the reverse chain, into the
+// buffer set of the step's parity: the two views A[0], A[1] share the adjoint arrays that the
+// reverse chain carries from step to step and differ in the intermediates and in lambda_C,
+// lambda_rho (cleared by a_dens).
 struct AdjointWork {
-    Adj A;
+    Adj A[2];
     size_t bytes = 0;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_a[2] = {nullptr, nullptr};  // intermediates of the parity ready
+    cudaEvent_t ev_b[2] = {nullptr, nullptr};  // reverse of the parity done with them
+    cudaEvent_t ev_sync = nullptr;
 };
 
 static cudaError_t amalloc(void** p, size_t b, size_t& tot)
@@ -881,9 +937,8 @@ static cudaError_t amalloc(void** p, size_t b, size_t& tot)
 cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out)
 {
     AdjointWork* W = new AdjointWork();
-    Adj& A = W->A;
-    A.nxp = P.nx + 2;
-    const size_t N = (size_t)P.N, NP = (size_t)P.ny * A.nxp;
+    *out = W;
+    const size_t N = (size_t)P.N, NP = (size_t)P.ny * (P.nx + 2);
     const size_t nwz = nw > 0 ? (size_t)nw : 1;
     size_t& t = W->bytes;
     cudaError_t e = cudaSuccess;
@@ -891,58 +946,78 @@ cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out)
         if (e == cudaSuccess) e = amalloc(p, b, t);
         if (e == cudaSuccess) e = cudaMemset(*p, 0, b ? b : 16);
     };
-    M((void**)&A.fpost, 27 * N * 4);
-    M((void**)&A.C, 3 * NP * 4);
-    M((void**)&A.rho, NP * 4);
-    M((void**)&A.g, 6 * NP * 4);
-    M((void**)&A.T, 3 * NP * 4);
-    M((void**)&A.F, 2 * N * 4);
-    M((void**)&A.wkind, 4 * nwz * 4);
-    M((void**)&A.wa, 4 * nwz * 4);
-    M((void**)&A.wb, 4 * nwz * 4);
-    M((void**)&A.wfr, 4 * nwz * 4);
-    M((void**)&A.wdfr, 4 * nwz * 4);
-    M((void**)&A.wcd, 4 * nwz * 4);
-    M((void**)&A.wth, 2 * nwz * 4);
-    M((void**)&A.wraw, 2 * nwz * 4);
-    M((void**)&A.wsel, 2 * nwz * 4);
-    M((void**)&A.l_fpost, 27 * N * 4);
-    M((void**)&A.l_F, 2 * N * 4);
-    M((void**)&A.l_g, 6 * NP * 4);
-    M((void**)&A.l_T, 3 * NP * 4);
-    M((void**)&A.l_C, 3 * NP * 4);
-    M((void**)&A.l_rho, NP * 4);
-    M((void**)&A.l_fs, 27 * N * 4);
-    M((void**)&A.l_cw, 3 * N * 4);
-    M((void**)&A.l_cw2, 3 * N * 4);
-    M((void**)&A.d_ang, 3 * nwz * 8);
-    M((void**)&A.d_u, 8);
-    *out = W;
+    Adj& S = W->A[0];
+    S.nxp = P.nx + 2;
+    // shared by both views
+    M((void**)&S.wline, 4 * nwz * sizeof(AdjLine));
+    if (e == cudaSuccess) e = cudaMemset(S.wline, 0xff, 4 * nwz * sizeof(AdjLine));  // th = NaN: march
+    M((void**)&S.l_fpost, 27 * N * 4);
+    M((void**)&S.l_F, 2 * N * 4);
+    M((void**)&S.l_g, 6 * NP * 4);
+    M((void**)&S.l_fs, 27 * N * 4);
+    M((void**)&S.l_cw, 3 * N * 4);
+    M((void**)&S.l_cw2, 3 * N * 4);
+    M((void**)&S.d_ang, 3 * nwz * 8);
+    M((void**)&S.d_u, 8);
+    W->A[1] = S;
+    // one set per parity
+    for (Adj& A : W->A) {
+        M((void**)&A.fpost, 27 * N * 4);
+        M((void**)&A.C, 3 * NP * 4);
+        M((void**)&A.rho, NP * 4);
+        M((void**)&A.g, 6 * NP * 4);
+        M((void**)&A.T, 3 * NP * 4);
+        M((void**)&A.wkind, 4 * nwz * 4);
+        M((void**)&A.wa, 4 * nwz * 4);
+        M((void**)&A.wb, 4 * nwz * 4);
+        M((void**)&A.wfr, 4 * nwz * 4);
+        M((void**)&A.wdfr, 4 * nwz * 4);
+        M((void**)&A.wcd, 4 * nwz * 4);
+        M((void**)&A.wth, 2 * nwz * 4);
+        M((void**)&A.wraw, 2 * nwz * 4);
+        M((void**)&A.wsel, 2 * nwz * 4);
+        M((void**)&A.l_C, 3 * NP * 4);
+        M((void**)&A.l_rho, NP * 4);
+    }
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&W->side, cudaStreamNonBlocking);
+    for (int c = 0; c < 2; c++) {
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_a[c], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_b[c], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_sync, cudaEventDisableTiming);
     return e;
 }
 
 void adjoint_free(AdjointWork* W)
 {
     if (!W) return;
-    Adj& A = W->A;
-    void* ptrs[] = {A.fpost, A.C, A.rho, A.g, A.T, A.F, A.wkind, A.wa, A.wb, A.wfr, A.wdfr, A.wcd,
-                    A.wth, A.wraw, A.wsel, A.l_fpost, A.l_F, A.l_g, A.l_T, A.l_C, A.l_rho, A.l_fs,
-                    A.l_cw, A.l_cw2, A.d_ang, A.d_u};
-    for (void* p : ptrs)
+    const Adj& S = W->A[0];
+    void* shared[] = {S.wline, S.l_fpost, S.l_F, S.l_g, S.l_fs, S.l_cw, S.l_cw2, S.d_ang, S.d_u};
+    for (void* p : shared)
         if (p) cudaFree(p);
+    for (const Adj& A : W->A) {
+        void* own[] = {A.fpost, A.C, A.rho, A.g, A.T, A.wkind, A.wa, A.wb, A.wfr, A.wdfr, A.wcd,
+                       A.wth, A.wraw, A.wsel, A.l_C, A.l_rho};
+        for (void* p : own)
+            if (p) cudaFree(p);
+    }
+    if (W->side) cudaStreamDestroy(W->side);
+    cudaEvent_t evs[] = {W->ev_a[0], W->ev_a[1], W->ev_b[0], W->ev_b[1], W->ev_sync};
+    for (cudaEvent_t ev : evs)
+        if (ev) cudaEventDestroy(ev);
     delete W;
 }
 
 size_t adjoint_bytes(const AdjointWork* W) { return W ? W->bytes : 0; }
 
-double* adjoint_dang(AdjointWork* W) { return W->A.d_ang; }
-double* adjoint_du(AdjointWork* W) { return W->A.d_u; }
+double* adjoint_dang(AdjointWork* W) { return W->A[0].d_ang; }
+double* adjoint_du(AdjointWork* W) { return W->A[0].d_u; }
 
 // seed the adjoint from the final stored populations: lambda_fs = pull^T (dJ/dfpost)
 void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, double J,
                   double M0, cudaStream_t s)
 {
-    Adj& A = W->A;
+    Adj& A = W->A[0];
     const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
     a_dens<<<gp, 128, 0, s>>>(P, A, fs, type);
     b_seed<<<gn, 128, 0, s>>>(P, A, type, J, M0);
@@ -951,35 +1026,50 @@ void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_
     cudaMemsetAsync(A.l_cw, 0, sizeof(float) * 3 * (size_t)P.N, s);
 }
 
-// one reverse step: fs / cw_lag are the stored populations and lagged wall values at the start
-// of the step; on entry A.l_fs, A.l_cw hold the adjoint of the step's outputs, on exit of its inputs
-void adjoint_step(const Params& P, AdjointWork* W, int nw, const int* widx, const double* wnrm,
-                  const float* wang, const float* fs, const double* cw_lag, const uint8_t* type,
-                  cudaStream_t s)
+cudaError_t adjoint_sync(AdjointWork* W, cudaStream_t s)
 {
-    Adj& A = W->A;
-    const size_t NP = (size_t)P.ny * A.nxp;
-    const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
-    // forward intermediates
+    cudaError_t e = cudaEventRecord(W->ev_sync, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(W->side, W->ev_sync, 0);
+    return e;
+}
+
+// forward intermediates of step t from its stored populations fs and lagged wall values cw_lag,
+// on the side stream; wait_reverse: first wait until the reverse of step t + 2 (the same buffer
+// set) is done with them
+cudaError_t adjoint_prepare(const Params& P, AdjointWork* W, int t, bool wait_reverse, int nw,
+                            const int* widx, const double* wnrm, const float* wang, const float* fs,
+                            const double* cw_lag, const uint8_t* type)
+{
+    const int c = t & 1;
+    const Adj& A = W->A[c];
+    cudaStream_t s = W->side;
+    cudaError_t e = wait_reverse ? cudaStreamWaitEvent(s, W->ev_b[c], 0) : cudaSuccess;
+    if (e != cudaSuccess) return e;
+    const dim3 gp((P.nx + 2 + 127) / 128, P.ny);
     a_dens<<<gp, 128, 0, s>>>(P, A, fs, type);
     if (nw > 0)
         a_wet<<<(unsigned)((4LL * nw + 127) / 128), 128, 0, s>>>(P, A, nw, widx, wnrm, wang, fs, type, cw_lag);
     a_grad_stress<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
-    a_force<<<gn, 128, 0, s>>>(P, A, type);
-    // reverse
-    cudaMemsetAsync(A.l_g, 0, sizeof(float) * 6 * NP, s);
-    cudaMemsetAsync(A.l_C, 0, sizeof(float) * 3 * NP, s);
-    cudaMemsetAsync(A.l_rho, 0, sizeof(float) * NP, s);
-    cudaMemsetAsync(A.l_fpost, 0, sizeof(float) * 27 * (size_t)P.N, s);
+    return cudaEventRecord(W->ev_a[c], s);
+}
+
+// the reverse of step t on s, once its intermediates are ready: on entry lambda_fs and
+// lambda_cw hold the adjoint of the step's outputs, on exit of its inputs
+cudaError_t adjoint_reverse(const Params& P, AdjointWork* W, int t, int nw, const int* widx,
+                            const float* wang, const double* cw_lag, const uint8_t* type, cudaStream_t s)
+{
+    const int c = t & 1;
+    const Adj& A = W->A[c];
+    cudaError_t e = cudaStreamWaitEvent(s, W->ev_a[c], 0);
+    if (e != cudaSuccess) return e;
+    const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
     b_collide<<<gn, 128, 0, s>>>(P, A, type);
-    b_div<<<gp, 128, 0, s>>>(P, A, type);
     b_stress_grad<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
-    cudaMemsetAsync(A.l_cw2, 0, sizeof(float) * 3 * (size_t)P.N, s);
     if (nw > 0) b_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, A, nw, widx, wang, cw_lag, type);
-    b_frac<<<gn, 128, 0, s>>>(P, A, type);
     b_zouhe<<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
-    std::swap(A.l_cw, A.l_cw2);
+    for (Adj& V : W->A) std::swap(V.l_cw, V.l_cw2);
+    return cudaEventRecord(W->ev_b[c], s);
 }
 
 }  // namespace lbm3k

@@ -866,8 +866,8 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
         adjoint_free(W);
     };
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_f, fb * nseg);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_c, cb * nseg);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_f, fb * std::max(nseg - 1, 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_c, cb * std::max(nseg - 1, 1));
     if (e == cudaSuccess) e = cudaMalloc((void**)&sg_f, fb * seglen);
     if (e == cudaSuccess) e = cudaMalloc((void**)&sg_c, cb * seglen);
     if (e == cudaSuccess) e = cudaMalloc((void**)&fin_f, fb);
@@ -888,9 +888,14 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
         cudaMemcpyAsync(h->pop[0].f, df, fb, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(h->Cw, dc, cb, cudaMemcpyDeviceToDevice, s);
     };
-    // forward with checkpoints
+    // forward with checkpoints; the states of the last segment go straight to the segment store,
+    // so that segment is not recomputed (with K >= nsteps: every state, no recompute at all)
+    const int t_last = (nseg - 1) * K;
     for (int t = 0; t < nsteps; t++) {
-        if (t % K == 0) save(ck_f + (size_t)(t / K) * 27 * N, ck_c + (size_t)(t / K) * 3 * N);
+        if (t >= t_last)
+            save(sg_f + (size_t)(t - t_last) * 27 * N, sg_c + (size_t)(t - t_last) * 3 * N);
+        else if (t % K == 0)
+            save(ck_f + (size_t)(t / K) * 27 * N, ck_c + (size_t)(t / K) * 3 * N);
         if ((e = enqueue_step(h, t == nsteps - 1, nullptr)) != cudaSuccess) break;
     }
     double d[8];
@@ -911,15 +916,26 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
     // backward over the segments, each recomputed from its checkpoint
     for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; seg--) {
         const int t0 = seg * K, t1 = std::min(nsteps, t0 + K);
-        restore(ck_f + (size_t)seg * 27 * N, ck_c + (size_t)seg * 3 * N);
-        for (int t = t0; t < t1; t++) {
-            save(sg_f + (size_t)(t - t0) * 27 * N, sg_c + (size_t)(t - t0) * 3 * N);
-            if (t < t1 - 1 && (e = enqueue_step(h, false, nullptr)) != cudaSuccess) break;
+        if (seg < nseg - 1) {
+            restore(ck_f + (size_t)seg * 27 * N, ck_c + (size_t)seg * 3 * N);
+            for (int t = t0; t < t1; t++) {
+                save(sg_f + (size_t)(t - t0) * 27 * N, sg_c + (size_t)(t - t0) * 3 * N);
+                if (t < t1 - 1 && (e = enqueue_step(h, false, nullptr)) != cudaSuccess) break;
+            }
         }
+        // the intermediates of step t - 1 are prepared on the adjoint's side stream while the
+        // reverse of step t runs
+        auto prepare = [&](int t, bool wait) {
+            return adjoint_prepare(h->P, W, t, wait, h->nw, h->widx, h->wnrm, h->wang,
+                                   sg_f + (size_t)(t - t0) * 27 * N, sg_c + (size_t)(t - t0) * 3 * N, h->type);
+        };
+        if (e == cudaSuccess) e = adjoint_sync(W, s);
+        if (e == cudaSuccess) e = prepare(t1 - 1, false);
         for (int t = t1 - 1; t >= t0 && e == cudaSuccess; t--) {
-            adjoint_step(h->P, W, h->nw, h->widx, h->wnrm, h->wang, sg_f + (size_t)(t - t0) * 27 * N,
-                         sg_c + (size_t)(t - t0) * 3 * N, h->type, s);
-            e = cudaGetLastError();
+            if (t > t0) e = prepare(t - 1, t + 1 < t1);
+            if (e == cudaSuccess)
+                e = adjoint_reverse(h->P, W, t, h->nw, h->widx, h->wang, sg_c + (size_t)(t - t0) * 3 * N, h->type, s);
+            if (e == cudaSuccess) e = cudaGetLastError();
         }
     }
     std::vector<double> dang(3 * (size_t)std::max(h->nw, 1));

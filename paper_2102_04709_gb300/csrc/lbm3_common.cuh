@@ -364,9 +364,15 @@ double* adjoint_dang(AdjointWork* W);
 double* adjoint_du(AdjointWork* W);
 void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, double J,
                   double M0, cudaStream_t s);
-void adjoint_step(const Params& P, AdjointWork* W, int nw, const int* widx, const double* wnrm,
-                  const float* wang, const float* fs, const double* cw_lag, const uint8_t* type,
-                  cudaStream_t s);
+// the side stream waits for the work enqueued on s so far
+cudaError_t adjoint_sync(AdjointWork* W, cudaStream_t s);
+// forward intermediates of step t (stored state fs, lagged wall values cw_lag) on the side stream
+cudaError_t adjoint_prepare(const Params& P, AdjointWork* W, int t, bool wait_reverse, int nw,
+                            const int* widx, const double* wnrm, const float* wang, const float* fs,
+                            const double* cw_lag, const uint8_t* type);
+// reverse of step t on s, after its intermediates
+cudaError_t adjoint_reverse(const Params& P, AdjointWork* W, int t, int nw, const int* widx,
+                            const float* wang, const double* cw_lag, const uint8_t* type, cudaStream_t s);
 void launch_diag(int store, const Params& P, const Pop& f, const uint8_t* type, const float* u,
                  double* partials, double* out, cudaStream_t s);
 
