@@ -38,6 +38,7 @@ struct Adj {
     float* rho;    // [NP]
     float* g;      // [6][NP]   (dC0/dx, dC0/dy, dC1/dx, ...)
     float* T;      // [3][NP]
+    float* F;      // [2][N]
     AdjLine* wline;  // [4 Nw] by lane 4 w + 2 k + side
     // wetting decisions, lane = 2 k + side
     int* wkind;    // [4][Nw]
@@ -323,18 +324,23 @@ __global__ void a_grad_stress(const Params P, const Adj A, const uint8_t* __rest
     A.T[2 * NP + p] = Tyy;
 }
 
-// force F = div T (Eq.10) at the fluid node (x, y), from the stress of its neighbours
-__device__ __forceinline__ void force_at(const Params& P, const Adj& A, int x, int y, float& Fx, float& Fy)
+// A4: force F = div T (Eq.10) at the fluid nodes, from the stress of their neighbours
+__global__ void a_force(const Params P, const Adj A, const uint8_t* __restrict__ type)
 {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int i = y * P.nx + x;
+    if (type[i] & 2) return;
     const int NP = P.ny * A.nxp;
-    Fx = 0.f;
-    Fy = 0.f;
+    float Fx = 0.f, Fy = 0.f;
     for (int a = 1; a < kQ; a++) {
         const int q = tpos(P, A, x + ex(a), y + ey(a));
         const float c = 3.0f * wq(a);
         Fx += c * (A.T[q] * ex(a) + A.T[NP + q] * ey(a));
         Fy += c * (A.T[NP + q] * ex(a) + A.T[2 * NP + q] * ey(a));
     }
+    A.F[i] = Fx;
+    A.F[P.N + i] = Fy;
 }
 
 // ------------------------------------------------------------------------------------------
@@ -360,8 +366,7 @@ __global__ void b_collide(const Params P, const Adj A, const uint8_t* __restrict
     for (int a = 0; a < kQ; a++) f[a] = q[a] + q[9 + a] + q[18 + a];
     const float rho = r[0] + r[1] + r[2];
     const float irho = 1.f / rho;  // one division; every other quotient by rho is a product
-    float Fx, Fy;
-    force_at(P, A, x, y, Fx, Fy);
+    const float Fx = A.F[i], Fy = A.F[P.N + i];
     float g[6];
     for (int j = 0; j < 6; j++) g[j] = A.g[j * NP + p];
     float C[kNF];
@@ -641,7 +646,7 @@ __global__ void b_stress_grad(const Params P, const Adj A, const uint8_t* __rest
     if (cls != kSB && lrho != 0.f) atomicAdd(&A.l_rho[pc], lrho);
 }
 
-// B5: adjoint of the wetting pass, one thread per C_SB node
+// B3: adjoint of the wetting pass, one thread per C_SB node
 __global__ void b_wet(const Params P, const Adj A, int nw, const int* __restrict__ widx,
                       const float* __restrict__ wang, const double* __restrict__ cw_lag,
                       const uint8_t* __restrict__ type)
@@ -754,36 +759,20 @@ __device__ __forceinline__ void frac_adjoint(const Params& P, const Adj& A, int 
     for (int k = 0; k < kNF; k++) lr[k] = (lC[k] - sc) / rho + lrho;
 }
 
-// B6: adjoint of the Zou-He completion at the fluid nodes of the open columns (lambda of the known
-// populations and of the inflow velocity), after adding the adjoint of the fractions there
-__global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__ type)
+// adjoint of the Zou-He completion at the fluid node i of an open column: lk (lambda of the
+// node's post-streaming populations, fractions included) becomes lambda of the populations before
+// the completion (the unknown ones end there: 0); returns this node's share of dJ/dU
+__device__ __forceinline__ double zouhe_adjoint(const Params& P, const Adj& A, bool inlet, int i, float lk[27])
 {
-    if (P.bc_x != kZouHe) return;
-    // threads [0, ny): inlet rows; [ny, 2 ny): outlet rows.  Every value is loaded before any is
-    // written, so that the loads go out together instead of one round trip at a time.
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool inlet = t < P.ny;
-    const int y = inlet ? t : t - P.ny;
-    const int xb = inlet ? 0 : P.nx - 1;
-    const int i = y * P.nx + xb;
-    const bool valid = y < P.ny && !(type[i] & 2);
-    float fk[27], lk[27];
-    if (valid) {
-        float lr[kNF];
-        frac_adjoint(P, A, xb, y, lr);
+    float fk[27];
 #pragma unroll
-        for (int j = 0; j < 27; j++) {
-            fk[j] = A.fpost[(long long)j * P.N + i];
-            lk[j] = A.l_fpost[(long long)j * P.N + i] + lr[j / 9];
-        }
-    }
+    for (int j = 0; j < 27; j++) fk[j] = A.fpost[(long long)j * P.N + i];
     float f[kQ];
 #pragma unroll
-    for (int a = 0; a < kQ; a++) f[a] = valid ? fk[a] + fk[9 + a] + fk[18 + a] : 0.f;
+    for (int a = 0; a < kQ; a++) f[a] = fk[a] + fk[9 + a] + fk[18 + a];
     float lf[kQ] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, lpart[kNF] = {0, 0, 0};
-    // dJ/dU of this row, summed over the warp before one atomic
     double lU = 0.0;
-    if (valid && inlet) {
+    if (inlet) {
         // inlet x = 0: unknown a = 1, 5, 8 (fluid 2)
         const float U = P.u_in;
         const float rho = (f[0] + f[2] + f[4] + 2.f * (f[3] + f[6] + f[7])) / (1.f - U);
@@ -802,7 +791,7 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
         lf[6] += 2.f * lrho * ir;
         lf[7] += 2.f * lrho * ir;
         lU = (double)L1 * (2.0 / 3.0) * rho + (double)(L5 + L8) * rho / 6.0 + (double)lrho * rho / (1.0 - U);
-    } else if (valid) {
+    } else {
         // outlet x = nx-1: unknown a = 3, 6, 7, split by the known fractions
         float part[kNF], tot = 0.f;
 #pragma unroll
@@ -849,51 +838,57 @@ __global__ void b_zouhe(const Params P, const Adj A, const uint8_t* __restrict__
         lf[5] += lh6 * (-1.f / 3.f);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) lU += __shfl_xor_sync(0xffffffffu, lU, o);
-    if ((threadIdx.x & 31) == 0 && lU != 0.0) atomicAdd(A.d_u, lU);
-    if (!valid) return;
-    // the unknown populations were set by the boundary, so their adjoint ends here; the known
-    // ones collect the boundary's contribution
-#pragma unroll
     for (int k = 0; k < kNF; k++)
 #pragma unroll
         for (int a = 0; a < kQ; a++) {
             const bool unknown = inlet ? (a == 1 || a == 5 || a == 8) : (a == 3 || a == 6 || a == 7);
-            A.l_fpost[(long long)(9 * k + a) * P.N + i] = unknown ? 0.f : lk[9 * k + a] + (lf[a] + lpart[k]);
+            lk[9 * k + a] = unknown ? 0.f : lk[9 * k + a] + (lf[a] + lpart[k]);
         }
+    return lU;
 }
 
-// B7: adjoint of the pull: the stored population (s, a) was read by exactly one puller, whose
-// lambda_fpost gets the adjoint of its fractions added here (at the open columns b_zouhe did)
+// B4: adjoint of the fractions, of the Zou-He completion and of the pull, pushed back from the
+// puller.  The post-streaming population (d, a) of the fluid node d came from the stored
+// population (d - e_a, a), or, where d - e_a is solid or beyond a wall side, from its own
+// (d, opp a) by the halfway bounce-back; its lambda, with the adjoint of d's fractions added (and,
+// at an open column, taken through the adjoint of the Zou-He completion), goes back there.
+// Every stored population of a fluid node has exactly one puller, except those that leave
+// through an open side, which nobody reads (lambda 0).  Solid nodes' lambda is never read.
 __global__ void b_pull(const Params P, const Adj A, const uint8_t* __restrict__ type)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= P.nx || y >= P.ny) return;
     const int i = y * P.nx + x;
-    const bool solid = type[i] & 2;
+    if (type[i] & 2) return;
     const bool zh = P.bc_x == kZouHe;
-    float lr_own[kNF] = {0.f, 0.f, 0.f};
-    if (!solid && !(zh && (x == 0 || x == P.nx - 1))) frac_adjoint(P, A, x, y, lr_own);
-    for (int a = 0; a < kQ; a++) {
-        int X = x + ex(a), Y = y + ey(a);
-        const int dk = wrap_xy(P, X, Y);
-        int src = -1, dir = a;
-        float lr[kNF] = {0.f, 0.f, 0.f};
-        if (!solid) {
-            if (dk == 1 || (dk == 0 && (type[Y * P.nx + X] & 2))) {
-                src = i;
-                dir = opp(a);
-                for (int k = 0; k < kNF; k++) lr[k] = lr_own[k];
-            } else if (dk == 0) {
-                src = Y * P.nx + X;
-                if (!(zh && (X == 0 || X == P.nx - 1))) frac_adjoint(P, A, X, Y, lr);
-            }
-        }
-        for (int k = 0; k < kNF; k++) {
-            const float v = src < 0 ? 0.f : A.l_fpost[(long long)(9 * k + dir) * P.N + src] + lr[k];
-            A.l_fs[(long long)(9 * k + a) * P.N + i] = v;
-        }
+    const bool zcol = zh && (x == 0 || x == P.nx - 1);
+    float lr[kNF];
+    frac_adjoint(P, A, x, y, lr);
+    float lk[27];
+#pragma unroll
+    for (int j = 0; j < 27; j++) lk[j] = A.l_fpost[(long long)j * P.N + i] + lr[j / 9];
+    if (zcol) {
+        const double lU = zouhe_adjoint(P, A, x == 0, i, lk);
+        if (lU != 0.0) atomicAdd(A.d_u, lU);
     }
+#pragma unroll
+    for (int a = 0; a < kQ; a++) {
+        int X = x - ex(a), Y = y - ey(a);
+        const int sk = wrap_xy(P, X, Y);
+        int dst = i, dir = opp(a);
+        if (sk == 2) continue;  // entered through an open side: a Zou-He unknown, no stored source
+        if (sk == 0 && !(type[Y * P.nx + X] & 2)) {
+            dst = Y * P.nx + X;
+            dir = a;
+        }
+        for (int k = 0; k < kNF; k++) A.l_fs[(long long)(9 * k + dir) * P.N + dst] = lk[9 * k + a];
+    }
+    if (zcol)
+        for (int a = 1; a < kQ; a++) {
+            int X = x + ex(a), Y = y + ey(a);
+            if (wrap_xy(P, X, Y) != 2) continue;
+            for (int k = 0; k < kNF; k++) A.l_fs[(long long)(9 * k + a) * P.N + i] = 0.f;
+        }
 }
 
 // objective: x-centroid of fluid 0, J = sum x rho_0 / sum rho_0 over the post-streaming state;
@@ -967,6 +962,7 @@ cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out)
         M((void**)&A.rho, NP * 4);
         M((void**)&A.g, 6 * NP * 4);
         M((void**)&A.T, 3 * NP * 4);
+        M((void**)&A.F, 2 * N * 4);
         M((void**)&A.wkind, 4 * nwz * 4);
         M((void**)&A.wa, 4 * nwz * 4);
         M((void**)&A.wb, 4 * nwz * 4);
@@ -996,7 +992,7 @@ void adjoint_free(AdjointWork* W)
     for (void* p : shared)
         if (p) cudaFree(p);
     for (const Adj& A : W->A) {
-        void* own[] = {A.fpost, A.C, A.rho, A.g, A.T, A.wkind, A.wa, A.wb, A.wfr, A.wdfr, A.wcd,
+        void* own[] = {A.fpost, A.C, A.rho, A.g, A.T, A.F, A.wkind, A.wa, A.wb, A.wfr, A.wdfr, A.wcd,
                        A.wth, A.wraw, A.wsel, A.l_C, A.l_rho};
         for (void* p : own)
             if (p) cudaFree(p);
@@ -1021,7 +1017,6 @@ void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_
     const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
     a_dens<<<gp, 128, 0, s>>>(P, A, fs, type);
     b_seed<<<gn, 128, 0, s>>>(P, A, type, J, M0);
-    b_zouhe<<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
     cudaMemsetAsync(A.l_cw, 0, sizeof(float) * 3 * (size_t)P.N, s);
 }
@@ -1050,6 +1045,7 @@ cudaError_t adjoint_prepare(const Params& P, AdjointWork* W, int t, bool wait_re
     if (nw > 0)
         a_wet<<<(unsigned)((4LL * nw + 127) / 128), 128, 0, s>>>(P, A, nw, widx, wnrm, wang, fs, type, cw_lag);
     a_grad_stress<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
+    a_force<<<dim3((P.nx + 127) / 128, P.ny), 128, 0, s>>>(P, A, type);
     return cudaEventRecord(W->ev_a[c], s);
 }
 
@@ -1066,7 +1062,6 @@ cudaError_t adjoint_reverse(const Params& P, AdjointWork* W, int t, int nw, cons
     b_collide<<<gn, 128, 0, s>>>(P, A, type);
     b_stress_grad<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
     if (nw > 0) b_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, A, nw, widx, wang, cw_lag, type);
-    b_zouhe<<<(2 * P.ny + 127) / 128, 128, 0, s>>>(P, A, type);
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
     for (Adj& V : W->A) std::swap(V.l_cw, V.l_cw2);
     return cudaEventRecord(W->ev_b[c], s);
