@@ -384,19 +384,23 @@ def run_ours(args):
     if not args.no_adjoint:
         w5 = W.config5()
         s5 = lbm3.Lbm3.from_workload(w5, stream=stream.cuda_stream)
-        s5.adjoint_centroid(200, 100)          # warm-up
-        s5.adjoint_centroid(200, 200)
 
         def timed_adjoint(K):
-            s5.set_fields(w5.rho)
-            barrier()
-            ta = time.perf_counter()
-            out = s5.adjoint_centroid(w5.steps, K)
-            barrier()
-            return out, time.perf_counter() - ta
+            # the first call of a size allocates the store the handle keeps for the next ones
+            # (an optimisation loop's steady state); both are timed, the second is the figure
+            times = []
+            for _ in range(2):
+                s5.set_fields(w5.rho)
+                barrier()
+                ta = time.perf_counter()
+                out = s5.adjoint_centroid(w5.steps, K)
+                barrier()
+                times.append(time.perf_counter() - ta)
+            s5.adjoint_release()
+            return out, times[1], times[0]
 
-        (J, dang, du), t_all = timed_adjoint(w5.steps)
-        _, t_k100 = timed_adjoint(100)
+        (J, dang, du), t_all, t_all_first = timed_adjoint(w5.steps)
+        _, t_k100, t_k100_first = timed_adjoint(100)
         s5.set_fields(w5.rho)
         barrier()
         tc = time.perf_counter()
@@ -408,9 +412,11 @@ def run_ours(args):
                "wall_nodes": int(dang.shape[0]),
                "steps_per_s": w5.steps / t_all, "unit": "adjoint steps/s (forward + reverse, every state kept)",
                "ms_per_step": t_all / w5.steps * 1e3,
+               "first_call_ms_per_step": t_all_first / w5.steps * 1e3,
                "forward_only_ms_per_step": fwd_ms,
                "ratio_to_forward": t_all / w5.steps * 1e3 / fwd_ms,
                "recompute": {"checkpoint_every": 100, "ms_per_step": t_k100 / w5.steps * 1e3,
+                             "first_call_ms_per_step": t_k100_first / w5.steps * 1e3,
                              "unit": "forward + recompute + reverse"},
                "J": J, "dJ_du": du, "grad_angles_norm": float(np.linalg.norm(dang))}
         del s5

@@ -161,10 +161,15 @@ int lbm3_set_inflow(lbm3* h, double u_in);
  * accumulators).  checkpoint_every >= nsteps keeps every state and recomputes nothing.
  * FP32 storage only, not with LBM3_BC_MODPER.  On return the simulation holds its final state.
  * Device memory: about nsteps / checkpoint_every + min(checkpoint_every, nsteps) states (132 B
- * per node each) plus ~300 B per node of work arrays, allocated and released by the call.
- * Synchronises. */
+ * per node each) plus ~300 B per node of work arrays, allocated by the first call that needs
+ * them and kept in the handle for later calls that need no more (an optimisation loop calls it
+ * once per iteration); lbm3_adjoint_release or lbm3_destroy releases it.  Synchronises. */
 int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, double* J_out,
                           double* dJ_dangles, double* dJ_du);
+
+/* Release the device memory that lbm3_adjoint_centroid keeps in the handle (nothing if none).
+ * Synchronises. */
+int lbm3_adjoint_release(lbm3* h);
 
 /* Size facts: out[0] = fluid nodes, out[1] = C_SB nodes, out[2] = algorithmic HBM bytes of the
  * fused step per timestep (216 B per fluid node with FP32 storage, 120 B with 16-bit offsets,

@@ -59,6 +59,7 @@ struct Adj {
     float* l_fs;     // [27][N] adjoint of the stored populations
     float* l_cw;     // [3][N]  adjoint of the lagged wall values (input, from the next step)
     float* l_cw2;    // [3][N]  adjoint of the lagged wall values (output, for the previous step)
+    double* l_th;    // [2][Nw] adjoint of the local angle theta_k of Eq.(21)
     double* d_ang;   // [3][Nw] dJ/d(theta_01, theta_20, theta_12)
     double* d_u;     // [1] dJ/dU
 };
@@ -646,9 +647,9 @@ __global__ void b_stress_grad(const Params P, const Adj A, const uint8_t* __rest
     if (cls != kSB && lrho != 0.f) atomicAdd(&A.l_rho[pc], lrho);
 }
 
-// B3: adjoint of the wetting pass, one thread per C_SB node
+// B3: adjoint of the wetting pass, one thread per C_SB node: the wall values' adjoint goes to the
+// fluid nodes they were read from (lambda_C), and the local angles' adjoint to l_th
 __global__ void b_wet(const Params P, const Adj A, int nw, const int* __restrict__ widx,
-                      const float* __restrict__ wang, const double* __restrict__ cw_lag,
                       const uint8_t* __restrict__ type)
 {
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -675,34 +676,50 @@ __global__ void b_wet(const Params P, const Adj A, int nw, const int* __restrict
     if (!(c0r >= 0.f && c0r <= 1.f)) lc0 = 0.f;
     if (!(c1r >= 0.f && c1r <= 1.f)) lc1 = 0.f;
     const float lk[2] = {lc0, lc1};
+    for (int k = 0; k < 2; k++) {
+        double lth = 0.0;
+        if (lk[k] != 0.f) {
+            const int j = (2 * k + A.wsel[k * nw + w]) * nw + w;
+            const int kind = A.wkind[j];
+            if (kind == 1) {
+                atomicAdd(&A.l_C[k * NP + A.wa[j]], lk[k]);
+            } else if (kind == 2) {
+                const float fr = A.wfr[j];
+                atomicAdd(&A.l_C[k * NP + A.wa[j]], (1.f - fr) * lk[k]);
+                atomicAdd(&A.l_C[k * NP + A.wb[j]], fr * lk[k]);
+                const float ca = A.C[k * NP + A.wa[j]], cb = A.C[k * NP + A.wb[j]];
+                lth = (double)lk[k] * (cb - ca) * A.wdfr[j];
+            } else {
+                // w-weighted mean of the fluid neighbours
+                double ws = 0.0;
+                for (int a = 1; a < kQ; a++)
+                    if (node_is_fluid<Store<kStoreF32>>(P, type, px + ex(a), py + ey(a))) ws += a < 5 ? 1.0 / 9.0 : 1.0 / 36.0;
+                for (int a = 1; a < kQ; a++) {
+                    if (!node_is_fluid<Store<kStoreF32>>(P, type, px + ex(a), py + ey(a))) continue;
+                    int kd;
+                    const int q = cpos(P, A, px + ex(a), py + ey(a), kd);
+                    atomicAdd(&A.l_C[k * NP + q], (float)((a < 5 ? 1.0 / 9.0 : 1.0 / 36.0) / ws * lk[k]));
+                }
+            }
+        }
+        A.l_th[k * nw + w] = lth;
+    }
+}
+
+// B3b: adjoint of Eq.(21), one thread per C_SB node: from the local angles' adjoint to the
+// wall-angle triple (accumulated over the steps) and to the lagged wall values of the previous
+// step.  Nothing in the reverse chain of this step needs it, so it runs beside it.
+__global__ void b_wet_angles(const Params P, const Adj A, int nw, const int* __restrict__ widx,
+                             const float* __restrict__ wang, const double* __restrict__ cw_lag)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= nw) return;
+    const int i = widx[w];
     const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
     const double Cr = cw_lag[i], Cg = cw_lag[P.N + i], Cb = cw_lag[2 * P.N + i];
     double l_rg = 0.0, l_br = 0.0, l_gb = 0.0, lCr = 0.0, lCg = 0.0, lCb = 0.0;
     for (int k = 0; k < 2; k++) {
-        if (lk[k] == 0.f) continue;
-        const int j = (2 * k + A.wsel[k * nw + w]) * nw + w;
-        const int kind = A.wkind[j];
-        double lth = 0.0;
-        if (kind == 1) {
-            atomicAdd(&A.l_C[k * NP + A.wa[j]], lk[k]);
-        } else if (kind == 2) {
-            const float fr = A.wfr[j];
-            atomicAdd(&A.l_C[k * NP + A.wa[j]], (1.f - fr) * lk[k]);
-            atomicAdd(&A.l_C[k * NP + A.wb[j]], fr * lk[k]);
-            const float ca = A.C[k * NP + A.wa[j]], cb = A.C[k * NP + A.wb[j]];
-            lth = (double)lk[k] * (cb - ca) * A.wdfr[j];
-        } else {
-            // w-weighted mean of the fluid neighbours
-            double ws = 0.0;
-            for (int a = 1; a < kQ; a++)
-                if (node_is_fluid<Store<kStoreF32>>(P, type, px + ex(a), py + ey(a))) ws += a < 5 ? 1.0 / 9.0 : 1.0 / 36.0;
-            for (int a = 1; a < kQ; a++) {
-                if (!node_is_fluid<Store<kStoreF32>>(P, type, px + ex(a), py + ey(a))) continue;
-                int kd;
-                const int q = cpos(P, A, px + ex(a), py + ey(a), kd);
-                atomicAdd(&A.l_C[k * NP + q], (float)((a < 5 ? 1.0 / 9.0 : 1.0 / 36.0) / ws * lk[k]));
-            }
-        }
+        const double lth = A.l_th[k * nw + w];
         if (lth == 0.0) continue;
         // Eq.(21) in the convex-combination form
         if (k == 0) {
@@ -913,14 +930,15 @@ __global__ void b_seed(const Params P, const Adj A, const uint8_t* __restrict__ 
 // they are computed on a stream of their own one step ahead of the reverse chain, into the
 // buffer set of the step's parity: the two views A[0], A[1] share the adjoint arrays that the
 // reverse chain carries from step to step and differ in the intermediates and in lambda_C,
-// lambda_rho (cleared by a_dens).
+// lambda_rho (cleared by a_dens).  The adjoint of Eq.(21) (b_wet_angles) runs on a third stream
+// beside the rest of the step's reverse chain; the next step's b_wet waits for it.
 struct AdjointWork {
     Adj A[2];
     size_t bytes = 0;
-    cudaStream_t side = nullptr;
+    cudaStream_t side = nullptr, side_w = nullptr;
     cudaEvent_t ev_a[2] = {nullptr, nullptr};  // intermediates of the parity ready
     cudaEvent_t ev_b[2] = {nullptr, nullptr};  // reverse of the parity done with them
-    cudaEvent_t ev_sync = nullptr;
+    cudaEvent_t ev_sync = nullptr, ev_wet = nullptr, ev_ang = nullptr;
 };
 
 static cudaError_t amalloc(void** p, size_t b, size_t& tot)
@@ -952,6 +970,7 @@ cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out)
     M((void**)&S.l_fs, 27 * N * 4);
     M((void**)&S.l_cw, 3 * N * 4);
     M((void**)&S.l_cw2, 3 * N * 4);
+    M((void**)&S.l_th, 2 * nwz * 8);
     M((void**)&S.d_ang, 3 * nwz * 8);
     M((void**)&S.d_u, 8);
     W->A[1] = S;
@@ -976,11 +995,14 @@ cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out)
         M((void**)&A.l_rho, NP * 4);
     }
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&W->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&W->side_w, cudaStreamNonBlocking);
     for (int c = 0; c < 2; c++) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_a[c], cudaEventDisableTiming);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_b[c], cudaEventDisableTiming);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_sync, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_wet, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&W->ev_ang, cudaEventDisableTiming);
     return e;
 }
 
@@ -988,7 +1010,7 @@ void adjoint_free(AdjointWork* W)
 {
     if (!W) return;
     const Adj& S = W->A[0];
-    void* shared[] = {S.wline, S.l_fpost, S.l_F, S.l_g, S.l_fs, S.l_cw, S.l_cw2, S.d_ang, S.d_u};
+    void* shared[] = {S.wline, S.l_fpost, S.l_F, S.l_g, S.l_fs, S.l_cw, S.l_cw2, S.l_th, S.d_ang, S.d_u};
     for (void* p : shared)
         if (p) cudaFree(p);
     for (const Adj& A : W->A) {
@@ -998,7 +1020,8 @@ void adjoint_free(AdjointWork* W)
             if (p) cudaFree(p);
     }
     if (W->side) cudaStreamDestroy(W->side);
-    cudaEvent_t evs[] = {W->ev_a[0], W->ev_a[1], W->ev_b[0], W->ev_b[1], W->ev_sync};
+    if (W->side_w) cudaStreamDestroy(W->side_w);
+    cudaEvent_t evs[] = {W->ev_a[0], W->ev_a[1], W->ev_b[0], W->ev_b[1], W->ev_sync, W->ev_wet, W->ev_ang};
     for (cudaEvent_t ev : evs)
         if (ev) cudaEventDestroy(ev);
     delete W;
@@ -1027,6 +1050,10 @@ cudaError_t adjoint_sync(AdjointWork* W, cudaStream_t s)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(W->side, W->ev_sync, 0);
     return e;
 }
+
+cudaError_t adjoint_join(AdjointWork* W, cudaStream_t s) { return cudaStreamWaitEvent(s, W->ev_ang, 0); }
+
+cudaStream_t adjoint_side_stream(AdjointWork* W) { return W->side; }
 
 // forward intermediates of step t from its stored populations fs and lagged wall values cw_lag,
 // on the side stream; wait_reverse: first wait until the reverse of step t + 2 (the same buffer
@@ -1061,7 +1088,15 @@ cudaError_t adjoint_reverse(const Params& P, AdjointWork* W, int t, int nw, cons
     const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
     b_collide<<<gn, 128, 0, s>>>(P, A, type);
     b_stress_grad<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
-    if (nw > 0) b_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, A, nw, widx, wang, cw_lag, type);
+    if (nw > 0) {
+        // lambda_cw and l_th: b_wet_angles of the step after this one is done with them
+        if ((e = cudaStreamWaitEvent(s, W->ev_ang, 0)) != cudaSuccess) return e;
+        b_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, A, nw, widx, type);
+        if ((e = cudaEventRecord(W->ev_wet, s)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(W->side_w, W->ev_wet, 0)) != cudaSuccess) return e;
+        b_wet_angles<<<(nw + 127) / 128, 128, 0, W->side_w>>>(P, A, nw, widx, wang, cw_lag);
+        if ((e = cudaEventRecord(W->ev_ang, W->side_w)) != cudaSuccess) return e;
+    }
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
     for (Adj& V : W->A) std::swap(V.l_cw, V.l_cw2);
     return cudaEventRecord(W->ev_b[c], s);

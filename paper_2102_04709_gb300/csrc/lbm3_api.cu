@@ -44,6 +44,13 @@ struct lbm3 {
     double* wnrm = nullptr;
     float* wang = nullptr;
     WetCache* wcache = nullptr;  // [4 nw] characteristic-line crossings of the wetting lanes
+    double* cw_keep = nullptr;   // set by the adjoint for one step: the wetting pass stores there
+                                 // the lagged wall values it reads
+    // set by the adjoint for one step: the step reads io_in (through the tensor map io_box on the
+    // ring path) and writes io_out instead of the two population buffers, whose turn is kept
+    const Pop* io_in = nullptr;
+    const Pop* io_out = nullptr;
+    const CUtensorMap* io_box = nullptr;
     int nw = 0;
     long long n_fluid = 0;
     // tiles of the fused step kernel: pure tiles (no solid within 3 nodes, away from the domain
@@ -73,6 +80,18 @@ struct lbm3 {
     bool ready = false;
     std::vector<int> wall_host;
     std::string err;
+    // device memory of lbm3_adjoint_centroid, kept for later calls that need no more of it: the
+    // checkpoints (nck states), the segment's states (nsg), the final state, the work arrays,
+    // and two events that order the state copies; released by lbm3_adjoint_release or
+    // lbm3_destroy
+    struct AdjStore {
+        float *ck_f = nullptr, *sg_f = nullptr, *fin_f = nullptr;
+        double *ck_c = nullptr, *sg_c = nullptr, *fin_c = nullptr;
+        int nck = 0, nsg = 0;
+        AdjointWork* W = nullptr;
+        cudaEvent_t ev_in = nullptr, ev_saved = nullptr;
+        std::vector<CUtensorMap> box;  // ring path: the tensor map of every segment slot
+    } adj;
 };
 
 namespace {
@@ -134,8 +153,21 @@ size_t tally(lbm3* h, size_t b)
     return b;
 }
 
+void adj_release(lbm3* h)
+{
+    lbm3::AdjStore& a = h->adj;
+    void* ptrs[] = {a.ck_f, a.sg_f, a.fin_f, a.ck_c, a.sg_c, a.fin_c};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    adjoint_free(a.W);
+    if (a.ev_in) cudaEventDestroy(a.ev_in);
+    if (a.ev_saved) cudaEventDestroy(a.ev_saved);
+    a = lbm3::AdjStore{};
+}
+
 void release(lbm3* h)
 {
+    adj_release(h);
     void* ptrs[] = {h->pop[0].f, h->pop[1].f, h->pop[0].rho, h->pop[1].rho, h->pop[0].off,
                     h->pop[1].off, h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
                     h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag, h->wcache};
@@ -235,14 +267,16 @@ bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtens
 cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 {
     cudaError_t e;
-    const Pop& fin = h->pop[h->cur];
-    const Pop& fo = h->pop[1 - h->cur];
+    const bool io = h->io_in != nullptr;
+    const Pop& fin = io ? *h->io_in : h->pop[h->cur];
+    const Pop& fo = io ? *h->io_out : h->pop[1 - h->cur];
     float* u = last ? h->u : nullptr;
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->ring)
-        launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, h->tm_box[h->cur], h->stream);
+        launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, io ? *h->io_box : h->tm_box[h->cur],
+                         h->stream);
     else if (h->tma && h->precision == LBM3_FP32)
         launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
                         h->tm_in_b[h->cur], h->tm_out[1 - h->cur], h->stream);
@@ -254,7 +288,8 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
                     h->stream);
     if (ev) cudaEventRecord(ev[1], h->stream);
     if (ev) cudaEventRecord(ev[2], h->side);
-    launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side);
+    launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side,
+               h->cw_keep);
     if (ev) cudaEventRecord(ev[3], h->side);
     const bool edges = h->n_gen > h->n_walltiles;
     if (edges) {
@@ -277,7 +312,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     }
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
-    h->cur = 1 - h->cur;
+    if (!io) h->cur = 1 - h->cur;
     return cudaGetLastError();
 }
 
@@ -856,34 +891,87 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
     const size_t fb = 27 * N * sizeof(float), cb = 3 * N * sizeof(double);
     const int nseg = (nsteps + K - 1) / K;
     const int seglen = std::min(K, nsteps);
-    float *ck_f = nullptr, *sg_f = nullptr, *fin_f = nullptr;
-    double *ck_c = nullptr, *sg_c = nullptr, *fin_c = nullptr;
-    AdjointWork* W = nullptr;
-    auto cleanup = [&]() {
-        void* ptrs[] = {ck_f, sg_f, fin_f, ck_c, sg_c, fin_c};
-        for (void* p : ptrs)
-            if (p) cudaFree(p);
-        adjoint_free(W);
-    };
-    cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_f, fb * std::max(nseg - 1, 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&ck_c, cb * std::max(nseg - 1, 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&sg_f, fb * seglen);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&sg_c, cb * seglen);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&fin_f, fb);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&fin_c, cb);
-    if (e == cudaSuccess) e = adjoint_alloc(h->P, h->nw, &W);
+    const int nck = std::max(nseg - 1, 1);
+    lbm3::AdjStore& st = h->adj;
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess && st.W && (st.nck < nck || st.nsg < seglen)) adj_release(h);
+    if (e == cudaSuccess && !st.W) {
+        if (e == cudaSuccess) e = cudaMalloc((void**)&st.ck_f, fb * nck);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&st.ck_c, cb * nck);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&st.sg_f, fb * seglen);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&st.sg_c, cb * seglen);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&st.fin_f, fb);
+        if (e == cudaSuccess) e = cudaMalloc((void**)&st.fin_c, cb);
+        // the wetting pass stores only the C_SB nodes' wall values into a state's slot; the rest
+        // stays 0, as in the handle's own array
+        if (e == cudaSuccess) e = cudaMemset(st.ck_c, 0, cb * nck);
+        if (e == cudaSuccess) e = cudaMemset(st.sg_c, 0, cb * seglen);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev_in, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&st.ev_saved, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = adjoint_alloc(h->P, h->nw, &st.W);
+        if (e == cudaSuccess && h->ring) {
+            st.box.resize(seglen);
+            for (int j = 0; j < seglen && e == cudaSuccess; j++)
+                if (!make_box_map(h->P, st.sg_f + (size_t)j * 27 * N, &st.box[j])) e = cudaErrorInvalidValue;
+        }
+        st.nck = nck;
+        st.nsg = seglen;
+    }
     if (e != cudaSuccess) {
-        cleanup();
+        adj_release(h);
         return fail(h, e == cudaErrorMemoryAllocation ? LBM3_ERR_OOM : LBM3_ERR_CUDA,
                     std::string("adjoint set-up: ") + cudaGetErrorString(e));
     }
+    float *ck_f = st.ck_f, *sg_f = st.sg_f, *fin_f = st.fin_f;
+    double *ck_c = st.ck_c, *sg_c = st.sg_c, *fin_c = st.fin_c;
+    AdjointWork* W = st.W;
+    auto cleanup = [&]() {
+        if (e != cudaSuccess) adj_release(h);
+    };
     cudaStream_t s = h->stream;
-    auto save = [&](float* df, double* dc) {
-        cudaMemcpyAsync(df, h->pop[h->cur].f, fb, cudaMemcpyDeviceToDevice, s);
-        cudaMemcpyAsync(dc, h->Cw, cb, cudaMemcpyDeviceToDevice, s);
+    // A state is saved while the next step runs, which only reads its populations: they are
+    // copied on the adjoint's side stream, which the step after next waits for, as it overwrites
+    // them; that step's wetting pass stores the wall values it starts from (saved_step).  A save
+    // that no step follows (the final state) copies the wall values itself.
+    cudaStream_t cs = adjoint_side_stream(W);
+    bool copying = false;
+    auto save_wait = [&]() {
+        if (copying) cudaStreamWaitEvent(s, st.ev_saved, 0);
+        copying = false;
+    };
+    auto save = [&](float* df, double* dc, bool stepped) {
+        save_wait();
+        cudaEventRecord(st.ev_in, s);
+        cudaStreamWaitEvent(cs, st.ev_in, 0);
+        cudaMemcpyAsync(df, h->pop[h->cur].f, fb, cudaMemcpyDeviceToDevice, cs);
+        cudaEventRecord(st.ev_saved, cs);
+        copying = true;
+        if (!stepped || h->nw == 0) cudaMemcpyAsync(dc, h->Cw, cb, cudaMemcpyDeviceToDevice, s);
+    };
+    // one step whose lagged wall values go to dc (or nowhere)
+    auto saved_step = [&](double* dc, bool last) {
+        h->cw_keep = h->nw > 0 ? dc : nullptr;
+        const cudaError_t r = enqueue_step(h, last, nullptr);
+        h->cw_keep = nullptr;
+        return r;
+    };
+    // Where the step kernels can read any buffer (the ring path, through the slot's tensor map, or
+    // the plain kernels), a segment's steps go from slot to slot of the store and its states need
+    // no copy: one step from slot j to `out`, its lagged wall values to slot j's
+    const bool direct = h->ring || !h->tma;
+    auto slot = [&](int j) { return Pop{sg_f + (size_t)j * 27 * N, nullptr, nullptr}; };
+    auto slot_step = [&](int j, const Pop& out, bool last) {
+        const Pop in = slot(j);
+        h->io_in = &in;
+        h->io_out = &out;
+        h->io_box = h->ring ? &st.box[j] : nullptr;
+        const cudaError_t r = saved_step(sg_c + (size_t)j * 3 * N, last);
+        h->io_in = h->io_out = nullptr;
+        h->io_box = nullptr;
+        return r;
     };
     auto restore = [&](const float* df, const double* dc) {
+        save_wait();
         h->cur = 0;
         cudaMemcpyAsync(h->pop[0].f, df, fb, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(h->Cw, dc, cb, cudaMemcpyDeviceToDevice, s);
@@ -892,12 +980,34 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
     // so that segment is not recomputed (with K >= nsteps: every state, no recompute at all)
     const int t_last = (nseg - 1) * K;
     for (int t = 0; t < nsteps; t++) {
-        if (t >= t_last)
-            save(sg_f + (size_t)(t - t_last) * 27 * N, sg_c + (size_t)(t - t_last) * 3 * N);
-        else if (t % K == 0)
-            save(ck_f + (size_t)(t / K) * 27 * N, ck_c + (size_t)(t / K) * 3 * N);
-        if ((e = enqueue_step(h, t == nsteps - 1, nullptr)) != cudaSuccess) break;
+        double* dc = nullptr;
+        if (t >= t_last && direct) {
+            if (t == t_last) {
+                save_wait();
+                cudaMemcpyAsync(sg_f, h->pop[h->cur].f, fb, cudaMemcpyDeviceToDevice, s);
+            }
+            const int j = t - t_last;
+            if (t + 1 < nsteps) {
+                e = slot_step(j, slot(j + 1), false);
+            } else {
+                e = slot_step(j, h->pop[1 - h->cur], true);  // the final state in the handle's buffer
+                h->cur = 1 - h->cur;
+            }
+            if (e != cudaSuccess) break;
+            continue;
+        }
+        if (t >= t_last) {
+            dc = sg_c + (size_t)(t - t_last) * 3 * N;
+            save(sg_f + (size_t)(t - t_last) * 27 * N, dc, true);
+        } else if (t % K == 0) {
+            dc = ck_c + (size_t)(t / K) * 3 * N;
+            save(ck_f + (size_t)(t / K) * 27 * N, dc, true);
+        } else {
+            save_wait();  // the copy of the previous state is done before this step overwrites it
+        }
+        if ((e = saved_step(dc, t == nsteps - 1)) != cudaSuccess) break;
     }
+    save_wait();
     double d[8];
     if (e == cudaSuccess) {
         launch_diag(h->precision, h->P, h->pop[h->cur], h->type, h->u, h->partials, h->dout, s);
@@ -909,19 +1019,28 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
         return fail(h, LBM3_ERR_CUDA, std::string("adjoint forward: ") + cudaGetErrorString(e));
     }
     const double M0 = d[0], J = d[3] / d[0];
-    save(fin_f, fin_c);
+    save(fin_f, fin_c, false);
+    save_wait();
     cudaMemsetAsync(adjoint_dang(W), 0, sizeof(double) * 3 * (size_t)std::max(h->nw, 1), s);
     cudaMemsetAsync(adjoint_du(W), 0, sizeof(double), s);
     adjoint_seed(h->P, W, h->pop[h->cur].f, h->type, J, M0, s);
     // backward over the segments, each recomputed from its checkpoint
     for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; seg--) {
         const int t0 = seg * K, t1 = std::min(nsteps, t0 + K);
-        if (seg < nseg - 1) {
+        if (seg < nseg - 1 && direct) {
+            // the checkpoint into slot 0 and the wall values into the handle, then slot to slot
+            cudaMemcpyAsync(sg_f, ck_f + (size_t)seg * 27 * N, fb, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(h->Cw, ck_c + (size_t)seg * 3 * N, cb, cudaMemcpyDeviceToDevice, s);
+            for (int t = t0; t < t1 - 1 && e == cudaSuccess; t++) e = slot_step(t - t0, slot(t - t0 + 1), false);
+            cudaMemcpyAsync(sg_c + (size_t)(t1 - 1 - t0) * 3 * N, h->Cw, cb, cudaMemcpyDeviceToDevice, s);
+        } else if (seg < nseg - 1) {
             restore(ck_f + (size_t)seg * 27 * N, ck_c + (size_t)seg * 3 * N);
             for (int t = t0; t < t1; t++) {
-                save(sg_f + (size_t)(t - t0) * 27 * N, sg_c + (size_t)(t - t0) * 3 * N);
-                if (t < t1 - 1 && (e = enqueue_step(h, false, nullptr)) != cudaSuccess) break;
+                double* dc = sg_c + (size_t)(t - t0) * 3 * N;
+                save(sg_f + (size_t)(t - t0) * 27 * N, dc, t < t1 - 1);
+                if (t < t1 - 1 && (e = saved_step(dc, false)) != cudaSuccess) break;
             }
+            save_wait();
         }
         // the intermediates of step t - 1 are prepared on the adjoint's side stream while the
         // reverse of step t runs
@@ -937,6 +1056,11 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
                 e = adjoint_reverse(h->P, W, t, h->nw, h->widx, h->wang, sg_c + (size_t)(t - t0) * 3 * N, h->type, s);
             if (e == cudaSuccess) e = cudaGetLastError();
         }
+        // the segment's stored states are recomputed for the next segment; the host waits for
+        // this segment's reverse before it enqueues that (running further ahead made the sweep
+        // slower)
+        if (e == cudaSuccess) e = adjoint_join(W, s);
+        if (e == cudaSuccess && seg > 0) e = cudaStreamSynchronize(s);
     }
     std::vector<double> dang(3 * (size_t)std::max(h->nw, 1));
     double du = 0.0;
@@ -1003,6 +1127,14 @@ int lbm3_sync(lbm3* h)
     if (!h) return LBM3_ERR_INVALID;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM3_OK;
+}
+
+int lbm3_adjoint_release(lbm3* h)
+{
+    if (!h) return fail(h, LBM3_ERR_INVALID, "NULL handle");
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    adj_release(h);
+    return e == cudaSuccess ? LBM3_OK : fail(h, LBM3_ERR_CUDA, std::string("adjoint release: ") + cudaGetErrorString(e));
 }
 
 void lbm3_destroy(lbm3* h)

@@ -305,9 +305,10 @@ struct WetCache {
 };
 
 // ---- kernel launchers (lbm3_step.cu); `store` is kStoreF32 / kStoreF16 / kStoreBF16 ----
+// Cw_prev (or nullptr): where the wetting pass also stores the lagged wall values it reads
 void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
                 const float* wang, const Pop& f, const uint8_t* type, double* Cw, WetCache* cache,
-                cudaStream_t s);
+                cudaStream_t s, double* Cw_prev = nullptr);
 void reset_wet_cache(WetCache* cache, int nw, cudaStream_t s);
 void launch_wet_init(int store, const Params& P, int nw, const int* widx, const Pop& f,
                      const uint8_t* type, double* Cw, cudaStream_t s);
@@ -364,12 +365,17 @@ double* adjoint_dang(AdjointWork* W);
 double* adjoint_du(AdjointWork* W);
 void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, double J,
                   double M0, cudaStream_t s);
+// the stream of the forward intermediates (idle outside the reverse sweep)
+cudaStream_t adjoint_side_stream(AdjointWork* W);
 // the side stream waits for the work enqueued on s so far
 cudaError_t adjoint_sync(AdjointWork* W, cudaStream_t s);
 // forward intermediates of step t (stored state fs, lagged wall values cw_lag) on the side stream
 cudaError_t adjoint_prepare(const Params& P, AdjointWork* W, int t, bool wait_reverse, int nw,
                             const int* widx, const double* wnrm, const float* wang, const float* fs,
                             const double* cw_lag, const uint8_t* type);
+// s waits for the adjoint of Eq.(21) of the last reversed step (before its lagged wall values
+// are overwritten, and before the angle gradient is read)
+cudaError_t adjoint_join(AdjointWork* W, cudaStream_t s);
 // reverse of step t on s, after its intermediates
 cudaError_t adjoint_reverse(const Params& P, AdjointWork* W, int t, int nw, const int* widx,
                             const float* wang, const double* cw_lag, const uint8_t* type, cudaStream_t s);

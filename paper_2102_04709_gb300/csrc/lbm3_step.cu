@@ -24,13 +24,14 @@ namespace {
 // Four lanes per C_SB node: lane = 2 * k + side, for the wetted fluids k = 0, 1 and the two
 // characteristic lines (rotated by +phi and -phi from n_s).  Each lane marches its line over the
 // class bytes, then gathers C at the one or two nodes it found; Eq.(22) combines the two lines
-// of a fluid with a shuffle, and lane 0 writes the wall values.
+// of a fluid with a shuffle, and lane 0 writes the wall values (and, when Cw_prev is given, the
+// lagged ones it started from, which the adjoint keeps for every step).
 template <class S>
 __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const int* __restrict__ widx,
                                              const double* __restrict__ wnrm,
                                              const float* __restrict__ wang, const S st,
                                              const uint8_t* __restrict__ type, double* __restrict__ Cw,
-                                             WetCache* __restrict__ cache)
+                                             WetCache* __restrict__ cache, double* __restrict__ Cw_prev)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     const int w = g >> 2;
@@ -45,6 +46,11 @@ __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const
         py = i / P.nx;
         // Eq.(21) with the wall values of the previous step
         const double Cr = Cw[i], Cg = Cw[P.N + i], Cb = Cw[2 * P.N + i];
+        if (Cw_prev && (g & 3) == 0) {
+            Cw_prev[i] = Cr;
+            Cw_prev[P.N + i] = Cg;
+            Cw_prev[2 * P.N + i] = Cb;
+        }
         const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
         th = k == 0 ? local_angle(Cb, 180.0 - t_br, Cg, t_rg) : local_angle(Cb, t_gb, Cr, 180.0 - t_rg);
         WetCache c = cache[g];
@@ -1469,12 +1475,12 @@ void with_store(int store, const Pop& p, long long N, Fn fn)
 
 void launch_wet(int store, const Params& P, int nw, const int* widx, const double* wnrm,
                 const float* wang, const Pop& f, const uint8_t* type, double* Cw, WetCache* cache,
-                cudaStream_t s)
+                cudaStream_t s, double* Cw_prev)
 {
     if (nw <= 0) return;
     const long long threads = 4LL * nw;
     with_store(store, f, P.N, [&](auto st) {
-        k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw, cache);
+        k_wet<<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(P, nw, widx, wnrm, wang, st, type, Cw, cache, Cw_prev);
     });
 }
 

@@ -29,7 +29,7 @@ EXPORTS = ("lbm3_create", "lbm3_set_fields", "lbm3_step", "lbm3_step_timed",
            "lbm3_step_timed_detail", "lbm3_fields",
            "lbm3_diag", "lbm3_n_wall", "lbm3_wall_nodes", "lbm3_wall_values", "lbm3_get_state",
            "lbm3_set_state", "lbm3_set_wall_angles", "lbm3_set_inflow", "lbm3_adjoint_centroid",
-           "lbm3_info", "lbm3_set_stream", "lbm3_set_copy_wait_limit", "lbm3_sync",
+           "lbm3_adjoint_release", "lbm3_info", "lbm3_set_stream", "lbm3_set_copy_wait_limit", "lbm3_sync",
            "lbm3_destroy", "lbm3_last_error", "lbm3_diag_fields")
 
 
@@ -77,6 +77,7 @@ def load(path: str | None = None):
     L.lbm3_set_wall_angles.argtypes = [vp, _D]
     L.lbm3_set_inflow.argtypes = [vp, ctypes.c_double]
     L.lbm3_adjoint_centroid.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, _D, _D, _D]
+    L.lbm3_adjoint_release.argtypes = [vp]
     L.lbm3_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     L.lbm3_set_stream.argtypes = [vp, vp]
     L.lbm3_set_copy_wait_limit.argtypes = [vp, ctypes.c_int32]
@@ -250,6 +251,10 @@ class Lbm3:
         _check(self._h, load().lbm3_adjoint_centroid(self._h, int(nsteps), int(checkpoint_every),
                                                      _dp(J), _dp(dang), _dp(du)))
         return float(J[0]), dang[:3 * n].reshape(n, 3), float(du[0])
+
+    def adjoint_release(self):
+        """Release the device memory adjoint_centroid keeps for its next call."""
+        _check(self._h, load().lbm3_adjoint_release(self._h))
 
     def info(self):
         out = np.zeros(9, np.int64)
