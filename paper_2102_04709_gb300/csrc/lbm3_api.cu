@@ -60,6 +60,8 @@ struct lbm3 {
     int* tiles_gen = nullptr;
     int n_pure = 0, n_gen = 0;
     int n_walltiles = 0;  // tiles_gen lists the inner wall tiles first, then the edge tiles
+    int n_edgewall = 0;   // of the edge tiles, those with a solid node within 3 nodes come first;
+                          // the others read no wall value and need not wait for the wetting pass
     long long pure_fluid = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -260,10 +262,11 @@ bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtens
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// One timestep: fork the side stream off the main stream, run the pure tiles on the main stream
-// while the side stream runs the wetting pass and then the remaining tiles, join.  With ev != NULL
-// the launches are bracketed by the events ev[0..6] (main: 0-1 pure tiles; side: 2-3 wetting pass,
-// 3-4 wall tiles; second side stream: 5-6 edge tiles).
+// One timestep: fork the side streams off the main stream, run the pure tiles on the main stream
+// while the side stream runs the wetting pass and then the wall tiles, and the second side stream
+// the edge tiles (at once those without a solid node near them, after the wetting pass the
+// others), join.  With ev != NULL the launches are bracketed by the events ev[0..6] (main: 0-1
+// pure tiles; side: 2-3 wetting pass, 3-4 wall tiles; second side stream: 5-6 edge tiles).
 cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 {
     cudaError_t e;
@@ -291,18 +294,27 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side,
                h->cw_keep);
     if (ev) cudaEventRecord(ev[3], h->side);
-    const bool edges = h->n_gen > h->n_walltiles;
+    // edge tiles: those without a solid node near them start at once, the others after the
+    // wetting pass
+    const int n_edge = h->n_gen - h->n_walltiles, n_edge_free = n_edge - h->n_edgewall;
+    const int* tiles_edge = h->tiles_gen + h->n_walltiles;
+    const bool edges = n_edge > 0;
     if (edges) {
-        if ((e = cudaEventRecord(h->ev_wet, h->side)) != cudaSuccess) return e;
-        if ((e = cudaStreamWaitEvent(h->side2, h->ev_wet, 0)) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(h->side2, h->ev_fork, 0)) != cudaSuccess) return e;
+        if (ev) cudaEventRecord(ev[5], h->side2);
+        launch_step(h->precision, h->P, tiles_edge + h->n_edgewall, n_edge_free, kTilesEdge, fin, fo, h->type,
+                    h->Cw, u, h->side2);
+        if (h->n_edgewall > 0) {
+            if ((e = cudaEventRecord(h->ev_wet, h->side)) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(h->side2, h->ev_wet, 0)) != cudaSuccess) return e;
+        }
     }
     launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
                 h->side);
     if (ev) cudaEventRecord(ev[4], h->side);
     if (edges) {
-        if (ev) cudaEventRecord(ev[5], h->side2);
-        launch_step(h->precision, h->P, h->tiles_gen + h->n_walltiles, h->n_gen - h->n_walltiles, kTilesEdge,
-                    fin, fo, h->type, h->Cw, u, h->side2);
+        launch_step(h->precision, h->P, tiles_edge, h->n_edgewall, kTilesEdge, fin, fo, h->type, h->Cw, u,
+                    h->side2);
         if (ev) cudaEventRecord(ev[6], h->side2);
         if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(h->stream, h->ev_join2, 0)) != cudaSuccess) return e;
@@ -489,7 +501,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     }
 
     // ---- tiles of the fused step kernel (2-D prefix sums of the solid mask)
-    std::vector<int> tp, tg, te;
+    std::vector<int> tp, tg, te, tf;
     long long pure_fluid = 0;
     {
         std::vector<long long> ps((size_t)(nx + 1) * (ny + 1), 0);
@@ -518,12 +530,34 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
                 } else if (inner) {
                     tg.push_back(ty * ntx + tx);
                 } else {
-                    te.push_back(ty * ntx + tx);
+                    // an edge tile: any solid node within 3 nodes, across a periodic side too?
+                    bool near_solid = false;
+                    for (int y = y0 - 3; y < y0 + kTY + 3 && !near_solid; y++) {
+                        int yy = y;
+                        if (yy < 0 || yy >= ny) {
+                            if (!g->periodic_y) continue;
+                            yy = (yy % ny + ny) % ny;
+                        }
+                        for (int x = x0 - 3; x < x0 + kTX + 3; x++) {
+                            int xx = x;
+                            if (xx < 0 || xx >= nx) {
+                                if (g->bc_x != kPeriodic && g->bc_x != kModPer) continue;
+                                xx = (xx % nx + nx) % nx;
+                            }
+                            if (solid[(size_t)yy * nx + xx]) {
+                                near_solid = true;
+                                break;
+                            }
+                        }
+                    }
+                    (near_solid ? te : tf).push_back(ty * ntx + tx);
                 }
             }
     }
     const int n_wall_tiles = (int)tg.size();
+    const int n_edge_wall = (int)te.size();
     tg.insert(tg.end(), te.begin(), te.end());
+    tg.insert(tg.end(), tf.begin(), tf.end());
 
     // ---- parameters
     lbm3* h = new lbm3();
@@ -561,6 +595,7 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
     h->n_pure = (int)tp.size();
     h->n_gen = (int)tg.size();
     h->n_walltiles = n_wall_tiles;
+    h->n_edgewall = n_edge_wall;
     h->pure_fluid = pure_fluid;
     h->wall_host = widx;
 

@@ -64,8 +64,9 @@ __device__ __forceinline__ bool node_is_fluid(const Params& P, const uint8_t* __
 }
 
 // C_k at the fluid node at unwrapped (X, Y), in the frame of the home domain.  The populations
-// are summed with error-free transformations and divided with the FMA residual, so the value is
-// the FP64 fraction of the stored FP32 populations (a node holding one fluid gives exactly 0 or 1).
+// are summed with error-free transformations and divided in float-float arithmetic (div_df), so
+// the value is the fraction of the stored FP32 populations to about 44 bits (a node holding one
+// fluid gives exactly 0 or 1) without a double-precision division, which is slow on this GPU.
 // (kept out of line: the wetting pass calls it up to ten times per lane, and inlining each call
 // made that kernel wait on its instruction cache)
 template <class S>
@@ -84,8 +85,9 @@ __device__ __noinline__ double node_C(const Params& P, const S& st, const uint8_
     two_sum(sh, dl, dh, sl);
     const float nh = k == 0 ? rh[0] : (k == 1 ? rh[1] : rh[2]);
     const float nl = k == 0 ? rl[0] : (k == 1 ? rl[1] : rl[2]);
-    const double num = (double)nh + (double)nl, den = (double)dh + (double)sl;
-    return num / den;
+    float qh, ql;
+    div_df(nh, nl, dh, sl, qh, ql);
+    return (double)qh + (double)ql;
 }
 
 template <class S>

@@ -157,16 +157,46 @@ def test_adjoint_full_gradient_small_case(gpu):
     assert abs(u.grad.item() - fd_u) <= 1e-3 * abs(fd_u)
 
 
-def test_adjoint_leaves_final_state(gpu):
-    """After lbm3_adjoint_centroid the simulation holds the same state as after lbm3_step."""
+@pytest.mark.parametrize("K", [25, 60, 1])
+def test_adjoint_leaves_final_state(gpu, K):
+    """After lbm3_adjoint_centroid the simulation holds the same state (populations and wall
+    values) as after lbm3_step, whether the forward pass kept every state (K = 60), some
+    segments (25) or checkpoints only (1)."""
     w = pillar_case()
     a = gpu.Lbm3.from_workload(w)
-    a.adjoint_centroid(60, 25)
+    a.adjoint_centroid(60, K)
     b = gpu.Lbm3.from_workload(w)
     b.step(60)
-    ra, _ = a.fields()
-    rb, _ = b.fields()
-    assert np.array_equal(ra, rb)
+    fa, ca = a.get_state()
+    fb, cb = b.get_state()
+    assert np.array_equal(fa, fb)
+    assert np.array_equal(ca, cb)
+    a.close()
+    b.close()
+
+
+def test_adjoint_checkpoint_schedules_agree(gpu):
+    """The same gradient (to the rounding of the adjoint's atomic sums) with every state kept
+    (K = n), with segments recomputed from checkpoints (K = 25, 7, 1), from a second call that
+    reuses the device memory the first one kept, and after that memory was released."""
+    w = pillar_case()
+    n = 60
+    sim = gpu.Lbm3.from_workload(w)
+    runs = []
+    for K in (n, n, 25, 7, 1):
+        sim.set_fields(w.rho)
+        runs.append(sim.adjoint_centroid(n, K))
+    sim.adjoint_release()
+    sim.set_fields(w.rho)
+    runs.append(sim.adjoint_centroid(n, n))
+    J0, g0, u0 = runs[0]
+    scale = np.abs(g0).max()
+    assert scale > 0
+    for J, g, u in runs[1:]:
+        assert J == J0
+        assert np.abs(g - g0).max() <= 1e-4 * scale
+        assert abs(u - u0) <= 1e-5 * abs(u0)
+    sim.close()
 
 
 def test_adjoint_gradients_follow_input_device(gpu):
