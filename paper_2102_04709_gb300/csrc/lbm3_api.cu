@@ -63,6 +63,14 @@ struct lbm3 {
     int n_edgewall = 0;   // of the edge tiles, those with a solid node within 3 nodes come first;
                           // the others read no wall value and need not wait for the wetting pass
     long long pure_fluid = 0;
+    // fluids present per tile (one byte per warp of the ring kernel's group, so no byte needs an
+    // atomic or a clearing): pres[pp] describes the current state, the ring kernel writes the
+    // next one's for the pure tiles; every other tile keeps 0x07 (all fluids), and so does every
+    // tile after the state is replaced from outside.  pp turns with cur (and alone in the
+    // adjoint's slot-to-slot steps).
+    uint64_t* pres[2] = {nullptr, nullptr};
+    size_t pres_bytes = 0;
+    int pp = 0;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // the edge tiles run on a second side stream once the wetting pass is done, concurrently with
@@ -172,7 +180,8 @@ void release(lbm3* h)
     adj_release(h);
     void* ptrs[] = {h->pop[0].f, h->pop[1].f, h->pop[0].rho, h->pop[1].rho, h->pop[0].off,
                     h->pop[1].off, h->type, h->Cw, h->u, h->scratch, h->partials, h->dout,
-                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag, h->wcache};
+                    h->widx, h->wnrm, h->wang, h->tiles_pure, h->tiles_gen, h->err_flag, h->wcache,
+                    h->pres[0], h->pres[1]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     h->pop[0] = h->pop[1] = Pop{nullptr, nullptr, nullptr};
@@ -279,7 +288,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if (ev) cudaEventRecord(ev[0], h->stream);
     if (h->ring)
         launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, io ? *h->io_box : h->tm_box[h->cur],
-                         h->stream);
+                         h->pres[h->pp], h->pres[1 - h->pp], h->stream);
     else if (h->tma && h->precision == LBM3_FP32)
         launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
                         h->tm_in_b[h->cur], h->tm_out[1 - h->cur], h->stream);
@@ -325,6 +334,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
     if (!io) h->cur = 1 - h->cur;
+    h->pp = 1 - h->pp;
     return cudaGetLastError();
 }
 
@@ -344,6 +354,15 @@ int take_kernel_error(lbm3* h, int* bits)
     return e == cudaSuccess ? LBM3_OK : fail(h, LBM3_ERR_CUDA, std::string("error bits: ") + cudaGetErrorString(e));
 }
 
+// the state was replaced from outside: every tile may hold every fluid
+cudaError_t pres_reset(lbm3* h)
+{
+    h->pp = h->cur;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < 2 && e == cudaSuccess; b++) e = cudaMemsetAsync(h->pres[b], 0x07, h->pres_bytes, h->stream);
+    return e;
+}
+
 void drop_graphs(lbm3* h)
 {
     for (int c = 0; c < 2; c++) {
@@ -358,7 +377,7 @@ void drop_graphs(lbm3* h)
 // stream, the legacy default one included.
 cudaError_t graph_block(lbm3* h)
 {
-    const int c = h->cur;
+    const int c = h->cur, pc = h->pp;
     if (!h->gexec[c] && !h->graph_off) {
         cudaStream_t user = h->stream;
         h->stream = h->gcap;
@@ -372,6 +391,7 @@ cudaError_t graph_block(lbm3* h)
         }
         h->stream = user;
         h->cur = c;
+        h->pp = pc;
         if (e == cudaSuccess) e = cudaGraphInstantiate(&h->gexec[c], g, 0);
         if (g) cudaGraphDestroy(g);
         if (e != cudaSuccess) {
@@ -632,6 +652,11 @@ int lbm3_create(lbm3** out, const lbm3_grid* g, const uint8_t* solid, const doub
         reset_wet_cache(h->wcache, (int)widx.size(), nullptr);
         e = cudaGetLastError();
     }
+    h->pres_bytes = (size_t)((nx + kTX - 1) / kTX) * ((ny + kTY - 1) / kTY) * sizeof(uint64_t);
+    for (int b = 0; b < 2; b++) {
+        if (e == cudaSuccess) e = dmalloc((void**)&h->pres[b], h->pres_bytes);
+        if (e == cudaSuccess) e = cudaMemset(h->pres[b], 0x07, h->pres_bytes);
+    }
     if (e == cudaSuccess) e = dmalloc((void**)&h->tiles_pure, tp.size() * sizeof(int));
     if (e == cudaSuccess) e = dmalloc((void**)&h->tiles_gen, tg.size() * sizeof(int));
     if (e == cudaSuccess && !tp.empty()) e = cudaMemcpy(h->tiles_pure, tp.data(), tp.size() * sizeof(int), cudaMemcpyHostToDevice);
@@ -725,6 +750,7 @@ int lbm3_set_fields(lbm3* h, const double* rho)
     CUDA_TRY(h, cudaMallocAsync((void**)&drho, 3 * N * sizeof(double), h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(drho, rho, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->cur = 0;
+    CUDA_TRY(h, pres_reset(h));
     CUDA_TRY(h, cudaMemsetAsync(h->err_flag, 0, sizeof(int), h->stream));
     launch_init(h->precision, h->P, drho, h->type, h->pop[0], h->stream);
     launch_wet_init(h->precision, h->P, h->nw, h->widx, h->pop[0], h->type, h->Cw, h->stream);
@@ -878,6 +904,7 @@ int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c)
     CUDA_TRY(h, cudaMallocAsync((void**)&dpost, 27 * N * sizeof(double), h->stream));
     CUDA_TRY(h, cudaMemcpyAsync(dpost, f_post, 27 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
     h->cur = 0;
+    CUDA_TRY(h, pres_reset(h));
     CUDA_TRY(h, cudaMemsetAsync(h->err_flag, 0, sizeof(int), h->stream));
     launch_set_state(h->precision, h->P, dpost, h->type, h->pop[0], h->stream);
     CUDA_TRY(h, cudaMemcpyAsync(h->Cw, wall_c, 3 * N * sizeof(double), cudaMemcpyHostToDevice, h->stream));
@@ -1008,6 +1035,7 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
     auto restore = [&](const float* df, const double* dc) {
         save_wait();
         h->cur = 0;
+        pres_reset(h);
         cudaMemcpyAsync(h->pop[0].f, df, fb, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(h->Cw, dc, cb, cudaMemcpyDeviceToDevice, s);
     };
@@ -1027,6 +1055,7 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
             } else {
                 e = slot_step(j, h->pop[1 - h->cur], true);  // the final state in the handle's buffer
                 h->cur = 1 - h->cur;
+                if (h->pp != h->cur) pres_reset(h);
             }
             if (e != cudaSuccess) break;
             continue;
@@ -1064,6 +1093,7 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
         const int t0 = seg * K, t1 = std::min(nsteps, t0 + K);
         if (seg < nseg - 1 && direct) {
             // the checkpoint into slot 0 and the wall values into the handle, then slot to slot
+            pres_reset(h);
             cudaMemcpyAsync(sg_f, ck_f + (size_t)seg * 27 * N, fb, cudaMemcpyDeviceToDevice, s);
             cudaMemcpyAsync(h->Cw, ck_c + (size_t)seg * 3 * N, cb, cudaMemcpyDeviceToDevice, s);
             for (int t = t0; t < t1 - 1 && e == cudaSuccess; t++) e = slot_step(t - t0, slot(t - t0 + 1), false);

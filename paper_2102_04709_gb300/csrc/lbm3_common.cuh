@@ -333,8 +333,9 @@ void launch_step_tma(const Params& P, const int* tiles, int ntiles, int nblocks,
 // (kTX + 8, kTY + 6, 27) over the [27][ny][nx] buffer
 size_t step_ring_smem_bytes();
 cudaError_t step_ring_prepare();
+// pres_in / pres_out: fluids present per tile in the step's input / output (see k_step_ring)
 void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
-                      const CUtensorMap& tin, cudaStream_t s);
+                      const CUtensorMap& tin, const uint64_t* pres_in, uint64_t* pres_out, cudaStream_t s);
 // pure tiles of the 16-bit storage through bulk tensor copies (persistent, nblocks blocks): tensor
 // maps of the densities (box (kTX + 8, kTY + 6, 3) of [3][ny][nx] FP32) and of the offset planes
 // (box (kTX + 16, kTY + 6, 24) of [24][ny][nx] 16-bit words)

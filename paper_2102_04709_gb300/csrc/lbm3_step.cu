@@ -1090,12 +1090,18 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar)
 // up on a buffer that is never released, and before exiting it waits (full limit) for every copy
 // it issued, so no copy lands in the shared memory of a later block.  The arithmetic is that of
 // k_step_tma and k_step<PURE>, so the results are identical.
+// Each warp also records the fluids its nodes hold (one byte of pres_out[tile] per warp); when
+// the 3 x 3 tiles around a tile held one fluid in the step's input (pres_in, read by the
+// producer), the tile is single-fluid after the pull, and its consumers skip the halo's phase
+// fields and the presence barrier, which only decide that (same results, fewer instructions).
 constexpr int kRingBufs = 3;
 template <int TX, int TY>
 __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params P, const int* __restrict__ tiles,
                                                                     const int ntiles, float* __restrict__ fout,
                                                                     float* __restrict__ uout,
-                                                                    const __grid_constant__ CUtensorMap tm_in)
+                                                                    const __grid_constant__ CUtensorMap tm_in,
+                                                                    const uint64_t* __restrict__ pres_in,
+                                                                    uint64_t* __restrict__ pres_out)
 {
     constexpr int NT = TX * TY;               // threads of a consumer group
     constexpr int NW = NT / 32;               // warps of a consumer group
@@ -1112,6 +1118,8 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
     __shared__ float s_txx[2][RY][RX], s_txy[2][RY][RX], s_tyy[2][RY][RX];
     __shared__ __align__(8) uint64_t s_full[2 * kRingBufs], s_empty[kRingBufs];
     __shared__ int s_flags[2][2];
+    __shared__ int s_single[2 * kRingBufs];  // by full-barrier slot: the tile's 3 x 3 tiles hold one fluid
+    __shared__ int s_tile[2 * kRingBufs];    // by full-barrier slot: the tile
     extern __shared__ unsigned char dsm[];
     float* ring = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [3][27][BY][BX]
 
@@ -1130,6 +1138,24 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
     // ---------------- producer warp ----------------
     if (warp == 2 * NW) {
         if (lane != 0) return;
+        // fluids stored in the 3 x 3 tiles around a tile (a pure tile is inner, so they exist)
+        auto around = [&](int t) {
+            uint64_t nb = 0;
+#pragma unroll
+            for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+                for (int dx = -1; dx <= 1; dx++) nb |= pres_in[t + dy * ntx + dx];
+            nb |= nb >> 32;
+            nb |= nb >> 16;
+            nb |= nb >> 8;
+            return (int)(nb & 7u);
+        };
+        // tile indices are loaded two tiles ahead and the fluids around a tile one tile ahead, so
+        // that no load waits on another within a tile and their latency passes while the
+        // producer waits for a free buffer
+        auto tile_at = [&](int jj) { return jj < njobs ? tiles[blockIdx.x + jj * gridDim.x] : 0; };
+        int tile_n = tile_at(0), tile_nn = tile_at(1);
+        int around_n = around(tile_n);
         int issued = 0;
         for (int j = 0; j < njobs; j++) {
             const int b = j % kRingBufs;
@@ -1143,12 +1169,18 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
                     break;
                 }
             }
-            const int tile = tiles[blockIdx.x + j * gridDim.x];
+            const int tile = tile_n;
             const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+            // written before the arrive, whose release the consumers' wait acquires
+            s_single[j % (2 * kRingBufs)] = __popc((unsigned)around_n) == 1;
+            s_tile[j % (2 * kRingBufs)] = tile;
             const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
             mbar_arrive_expect_tx(full, (uint32_t)NBOX * 4u);
             tma_load_3d(smem_u32(ring + b * NBOXP), &tm_in, x0 - 4, y0 - 3, 0, full);
             issued = j + 1;
+            tile_n = tile_nn;
+            tile_nn = tile_at(j + 2);
+            if (j + 1 < njobs) around_n = around(tile_n);
         }
         // every copy issued has landed before the block may exit
         for (int m = 0; m < 2 * kRingBufs; m++) {
@@ -1202,8 +1234,6 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
 
     for (int j = g, jj = 0; j < njobs; j += 2, jj++) {
         const float* box = ring + (j % kRingBufs) * NBOXP;
-        const int tile = tiles[blockIdx.x + j * gridDim.x];
-        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
         {
             bool ok = false;
             const uint32_t full = smem_u32(&s_full[j % (2 * kRingBufs)]);
@@ -1214,6 +1244,13 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
                 return;
             }
         }
+        const int tile = s_tile[j % (2 * kRingBufs)];
+        const int x0 = (tile % ntx) * TX, y0 = (tile / ntx) * TY;
+        // One fluid in the 3 x 3 tiles around: every node of the halo-2 region holds that fluid
+        // alone after the pull (a fluid absent from a node's sources stays absent), so the tile
+        // is not mixed, and its phase fields, which only the mixed path reads, are skipped.
+        const bool single = s_single[j % (2 * kRingBufs)];
+        if (single && tid == 0) flags[(jj + 1) & 1] = 0;  // all threads are past the last tile
         // ---- phase 1: pulls, densities and phase fields of the halo-2 region ----
         auto pull = [&](int cx, int cy, float q[27]) {
 #pragma unroll
@@ -1224,7 +1261,7 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
         };
         int present = 0;
         float q[27];
-        if (ring_node) {
+        if (ring_node && !single) {
             pull(rcx, rcy, q);
             const float a0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
             const float a1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
@@ -1241,22 +1278,31 @@ __global__ void __launch_bounds__(2 * TX * TY + 32, 1) k_step_ring(const Params 
         r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
         r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
         r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
-        present |= store_phase(lx + 2, ly + 2, r0, r1, r2);
-        // fluids present in the group's phase-field region (one barrier; see fluids_present)
-        int cnt;
+        // the fluids this warp's nodes hold, for the tiles around this one in the next step
         {
-            const int w = __reduce_or_sync(0xffffffffu, present);
-            if (lane == 0 && w) atomicOr(&flags[jj & 1], w);
-            group_sync(bar_id, NT);
-            const int v = flags[jj & 1];
-            if (tid == 0) flags[(jj + 1) & 1] = 0;
-            cnt = __popc(v & 7);
+            const int own = (r0 != 0.0f ? 1 : 0) | (r1 != 0.0f ? 2 : 0) | (r2 != 0.0f ? 4 : 0);
+            const int w = __reduce_or_sync(0xffffffffu, own);
+            if (lane == 0) reinterpret_cast<uint8_t*>(pres_out + tile)[tid >> 5] = (uint8_t)w;
         }
-        const bool mixed = cnt != 1;
+        bool mixed = false;
+        if (!single) {
+            present |= store_phase(lx + 2, ly + 2, r0, r1, r2);
+            // fluids present in the group's phase-field region (one barrier; see fluids_present)
+            int cnt;
+            {
+                const int w = __reduce_or_sync(0xffffffffu, present);
+                if (lane == 0 && w) atomicOr(&flags[jj & 1], w);
+                group_sync(bar_id, NT);
+                const int v = flags[jj & 1];
+                if (tid == 0) flags[(jj + 1) & 1] = 0;
+                cnt = __popc(v & 7);
+            }
+            mixed = cnt != 1;
 
-        // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
-        if (mixed) stress_halo1<TX, TY>(P, ch, rh, s_txx[g], s_txy[g], s_tyy[g], tid);
-        group_sync(bar_id, NT);
+            // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
+            if (mixed) stress_halo1<TX, TY>(P, ch, rh, s_txx[g], s_txy[g], s_tyy[g], tid);
+            group_sync(bar_id, NT);
+        }
 
         // ---- phase 3: force, collision, recolouring, 27 stores per node ----
         float Fx = 0.0f, Fy = 0.0f, gr[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -1744,11 +1790,12 @@ cudaError_t step_ring_prepare()
 }
 
 void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout, float* u,
-                      const CUtensorMap& tin, cudaStream_t s)
+                      const CUtensorMap& tin, const uint64_t* pres_in, uint64_t* pres_out, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     const int nb = nblocks < ntiles ? nblocks : ntiles;
-    k_step_ring<kTX, kTY><<<nb, 2 * kTX * kTY + 32, step_ring_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin);
+    k_step_ring<kTX, kTY><<<nb, 2 * kTX * kTY + 32, step_ring_smem_bytes(), s>>>(P, tiles, ntiles, fout.f, u, tin,
+                                                                                 pres_in, pres_out);
 }
 
 size_t step_tma16_smem_bytes()
