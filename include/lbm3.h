@@ -163,7 +163,10 @@ int lbm3_set_inflow(lbm3* h, double u_in);
  * Device memory: about nsteps / checkpoint_every + min(checkpoint_every, nsteps) states (132 B
  * per node each) plus ~300 B per node of work arrays, allocated by the first call that needs
  * them and kept in the handle for later calls that need no more (an optimisation loop calls it
- * once per iteration); lbm3_adjoint_release or lbm3_destroy releases it.  Synchronises. */
+ * once per iteration); lbm3_adjoint_release or lbm3_destroy releases it.  The first call of a
+ * given nsteps / checkpoint_every also records the whole sweep as a CUDA graph, which later such
+ * calls replay (dropped with the store, or when lbm3_set_inflow / lbm3_set_copy_wait_limit
+ * change a captured parameter).  Synchronises. */
 int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t checkpoint_every, double* J_out,
                           double* dJ_dangles, double* dJ_du);
 

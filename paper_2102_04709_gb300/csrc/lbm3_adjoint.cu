@@ -908,12 +908,15 @@ __global__ void b_pull(const Params P, const Adj A, const uint8_t* __restrict__ 
         }
 }
 
-// objective: x-centroid of fluid 0, J = sum x rho_0 / sum rho_0 over the post-streaming state;
-// seed lambda_fpost = dJ/dfpost
-__global__ void b_seed(const Params P, const Adj A, const uint8_t* __restrict__ type, double J, double M0)
+// objective: x-centroid of fluid 0, J = sum x rho_0 / sum rho_0 over the post-streaming state,
+// from the diagnostics of the final state (diag[0] = sum rho_0, diag[3] = sum x rho_0, so that
+// no value passes through the host); seed lambda_fpost = dJ/dfpost
+__global__ void b_seed(const Params P, const Adj A, const uint8_t* __restrict__ type,
+                       const double* __restrict__ diag)
 {
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y;
     if (x >= P.nx || y >= P.ny) return;
+    const double M0 = diag[0], J = diag[3] / M0;
     const int i = y * P.nx + x;
     const bool fluid = !(type[i] & 2);
     for (int k = 0; k < kNF; k++)
@@ -939,6 +942,7 @@ struct AdjointWork {
     cudaEvent_t ev_a[2] = {nullptr, nullptr};  // intermediates of the parity ready
     cudaEvent_t ev_b[2] = {nullptr, nullptr};  // reverse of the parity done with them
     cudaEvent_t ev_sync = nullptr, ev_wet = nullptr, ev_ang = nullptr;
+    bool ang_recorded = false;  // ev_ang was recorded in this sweep (no wait on an older record)
 };
 
 static cudaError_t amalloc(void** p, size_t b, size_t& tot)
@@ -1033,15 +1037,16 @@ double* adjoint_dang(AdjointWork* W) { return W->A[0].d_ang; }
 double* adjoint_du(AdjointWork* W) { return W->A[0].d_u; }
 
 // seed the adjoint from the final stored populations: lambda_fs = pull^T (dJ/dfpost)
-void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, double J,
-                  double M0, cudaStream_t s)
+void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, const double* diag,
+                  cudaStream_t s)
 {
     Adj& A = W->A[0];
     const dim3 gn((P.nx + 127) / 128, P.ny), gp((P.nx + 2 + 127) / 128, P.ny);
     a_dens<<<gp, 128, 0, s>>>(P, A, fs, type);
-    b_seed<<<gn, 128, 0, s>>>(P, A, type, J, M0);
+    b_seed<<<gn, 128, 0, s>>>(P, A, type, diag);
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
     cudaMemsetAsync(A.l_cw, 0, sizeof(float) * 3 * (size_t)P.N, s);
+    W->ang_recorded = false;
 }
 
 cudaError_t adjoint_sync(AdjointWork* W, cudaStream_t s)
@@ -1051,7 +1056,10 @@ cudaError_t adjoint_sync(AdjointWork* W, cudaStream_t s)
     return e;
 }
 
-cudaError_t adjoint_join(AdjointWork* W, cudaStream_t s) { return cudaStreamWaitEvent(s, W->ev_ang, 0); }
+cudaError_t adjoint_join(AdjointWork* W, cudaStream_t s)
+{
+    return W->ang_recorded ? cudaStreamWaitEvent(s, W->ev_ang, 0) : cudaSuccess;
+}
 
 cudaStream_t adjoint_side_stream(AdjointWork* W) { return W->side; }
 
@@ -1090,12 +1098,13 @@ cudaError_t adjoint_reverse(const Params& P, AdjointWork* W, int t, int nw, cons
     b_stress_grad<<<gp, 128, 0, s>>>(P, A, type, P.sig01, P.sig02, P.sig12);
     if (nw > 0) {
         // lambda_cw and l_th: b_wet_angles of the step after this one is done with them
-        if ((e = cudaStreamWaitEvent(s, W->ev_ang, 0)) != cudaSuccess) return e;
+        if (W->ang_recorded && (e = cudaStreamWaitEvent(s, W->ev_ang, 0)) != cudaSuccess) return e;
         b_wet<<<(nw + 127) / 128, 128, 0, s>>>(P, A, nw, widx, type);
         if ((e = cudaEventRecord(W->ev_wet, s)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(W->side_w, W->ev_wet, 0)) != cudaSuccess) return e;
         b_wet_angles<<<(nw + 127) / 128, 128, 0, W->side_w>>>(P, A, nw, widx, wang, cw_lag);
         if ((e = cudaEventRecord(W->ev_ang, W->side_w)) != cudaSuccess) return e;
+        W->ang_recorded = true;
     }
     b_pull<<<gn, 128, 0, s>>>(P, A, type);
     for (Adj& V : W->A) std::swap(V.l_cw, V.l_cw2);

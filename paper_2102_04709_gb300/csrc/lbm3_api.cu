@@ -101,6 +101,9 @@ struct lbm3 {
         AdjointWork* W = nullptr;
         cudaEvent_t ev_in = nullptr, ev_saved = nullptr;
         std::vector<CUtensorMap> box;  // ring path: the tensor map of every segment slot
+        // the sweep as a graph, for nsteps / K from state buffer g_cur
+        cudaGraphExec_t gexec = nullptr;
+        int g_nsteps = 0, g_K = 0, g_cur = 0;
     } adj;
 };
 
@@ -169,6 +172,7 @@ void adj_release(lbm3* h)
     void* ptrs[] = {a.ck_f, a.sg_f, a.fin_f, a.ck_c, a.sg_c, a.fin_c};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (a.gexec) cudaGraphExecDestroy(a.gexec);
     adjoint_free(a.W);
     if (a.ev_in) cudaEventDestroy(a.ev_in);
     if (a.ev_saved) cudaEventDestroy(a.ev_saved);
@@ -369,6 +373,8 @@ void drop_graphs(lbm3* h)
         if (h->gexec[c]) cudaGraphExecDestroy(h->gexec[c]);
         h->gexec[c] = nullptr;
     }
+    if (h->adj.gexec) cudaGraphExecDestroy(h->adj.gexec);
+    h->adj.gexec = nullptr;
 }
 
 // kGraphSteps steps from the current buffer, none of them the last of an lbm3_step call (no
@@ -1039,106 +1045,146 @@ int lbm3_adjoint_centroid(lbm3* h, int32_t nsteps, int32_t K, double* J_out, dou
         cudaMemcpyAsync(h->pop[0].f, df, fb, cudaMemcpyDeviceToDevice, s);
         cudaMemcpyAsync(h->Cw, dc, cb, cudaMemcpyDeviceToDevice, s);
     };
-    // forward with checkpoints; the states of the last segment go straight to the segment store,
-    // so that segment is not recomputed (with K >= nsteps: every state, no recompute at all)
-    const int t_last = (nseg - 1) * K;
-    for (int t = 0; t < nsteps; t++) {
-        double* dc = nullptr;
-        if (t >= t_last && direct) {
-            if (t == t_last) {
-                save_wait();
-                cudaMemcpyAsync(sg_f, h->pop[h->cur].f, fb, cudaMemcpyDeviceToDevice, s);
+    // The whole sweep, enqueued without a host round trip (the seed reads J from the device
+    // diagnostics): the forward pass with checkpoints, whose last segment's states go straight to
+    // the segment store (with K >= nsteps: every state, no recompute at all), then the reverse
+    // over the segments, each other segment recomputed from its checkpoint, then the final state
+    // back into the handle.  capturing: recorded into a graph (no host waits allowed).
+    auto enqueue_all = [&](bool capturing) -> cudaError_t {
+        cudaError_t r = cudaSuccess;
+        const int t_last = (nseg - 1) * K;
+        for (int t = 0; t < nsteps && r == cudaSuccess; t++) {
+            double* dc = nullptr;
+            if (t >= t_last && direct) {
+                if (t == t_last) {
+                    save_wait();
+                    cudaMemcpyAsync(sg_f, h->pop[h->cur].f, fb, cudaMemcpyDeviceToDevice, s);
+                }
+                const int j = t - t_last;
+                if (t + 1 < nsteps) {
+                    r = slot_step(j, slot(j + 1), false);
+                } else {
+                    r = slot_step(j, h->pop[1 - h->cur], true);  // the final state in the handle's buffer
+                    h->cur = 1 - h->cur;
+                    if (h->pp != h->cur) pres_reset(h);
+                }
+                continue;
             }
-            const int j = t - t_last;
-            if (t + 1 < nsteps) {
-                e = slot_step(j, slot(j + 1), false);
+            if (t >= t_last) {
+                dc = sg_c + (size_t)(t - t_last) * 3 * N;
+                save(sg_f + (size_t)(t - t_last) * 27 * N, dc, true);
+            } else if (t % K == 0) {
+                dc = ck_c + (size_t)(t / K) * 3 * N;
+                save(ck_f + (size_t)(t / K) * 27 * N, dc, true);
             } else {
-                e = slot_step(j, h->pop[1 - h->cur], true);  // the final state in the handle's buffer
-                h->cur = 1 - h->cur;
-                if (h->pp != h->cur) pres_reset(h);
+                save_wait();  // the copy of the previous state is done before this step overwrites it
             }
-            if (e != cudaSuccess) break;
-            continue;
+            r = saved_step(dc, t == nsteps - 1);
         }
-        if (t >= t_last) {
-            dc = sg_c + (size_t)(t - t_last) * 3 * N;
-            save(sg_f + (size_t)(t - t_last) * 27 * N, dc, true);
-        } else if (t % K == 0) {
-            dc = ck_c + (size_t)(t / K) * 3 * N;
-            save(ck_f + (size_t)(t / K) * 27 * N, dc, true);
-        } else {
-            save_wait();  // the copy of the previous state is done before this step overwrites it
-        }
-        if ((e = saved_step(dc, t == nsteps - 1)) != cudaSuccess) break;
-    }
-    save_wait();
-    double d[8];
-    if (e == cudaSuccess) {
+        save_wait();
+        if (r != cudaSuccess) return r;
         launch_diag(h->precision, h->P, h->pop[h->cur], h->type, h->u, h->partials, h->dout, s);
-        e = cudaMemcpyAsync(d, h->dout, sizeof d, cudaMemcpyDeviceToHost, s);
-    }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-        cleanup();
-        return fail(h, LBM3_ERR_CUDA, std::string("adjoint forward: ") + cudaGetErrorString(e));
-    }
-    const double M0 = d[0], J = d[3] / d[0];
-    save(fin_f, fin_c, false);
-    save_wait();
-    cudaMemsetAsync(adjoint_dang(W), 0, sizeof(double) * 3 * (size_t)std::max(h->nw, 1), s);
-    cudaMemsetAsync(adjoint_du(W), 0, sizeof(double), s);
-    adjoint_seed(h->P, W, h->pop[h->cur].f, h->type, J, M0, s);
-    // backward over the segments, each recomputed from its checkpoint
-    for (int seg = nseg - 1; seg >= 0 && e == cudaSuccess; seg--) {
-        const int t0 = seg * K, t1 = std::min(nsteps, t0 + K);
-        if (seg < nseg - 1 && direct) {
-            // the checkpoint into slot 0 and the wall values into the handle, then slot to slot
-            pres_reset(h);
-            cudaMemcpyAsync(sg_f, ck_f + (size_t)seg * 27 * N, fb, cudaMemcpyDeviceToDevice, s);
-            cudaMemcpyAsync(h->Cw, ck_c + (size_t)seg * 3 * N, cb, cudaMemcpyDeviceToDevice, s);
-            for (int t = t0; t < t1 - 1 && e == cudaSuccess; t++) e = slot_step(t - t0, slot(t - t0 + 1), false);
-            cudaMemcpyAsync(sg_c + (size_t)(t1 - 1 - t0) * 3 * N, h->Cw, cb, cudaMemcpyDeviceToDevice, s);
-        } else if (seg < nseg - 1) {
-            restore(ck_f + (size_t)seg * 27 * N, ck_c + (size_t)seg * 3 * N);
-            for (int t = t0; t < t1; t++) {
-                double* dc = sg_c + (size_t)(t - t0) * 3 * N;
-                save(sg_f + (size_t)(t - t0) * 27 * N, dc, t < t1 - 1);
-                if (t < t1 - 1 && (e = saved_step(dc, false)) != cudaSuccess) break;
+        save(fin_f, fin_c, false);
+        save_wait();
+        cudaMemsetAsync(adjoint_dang(W), 0, sizeof(double) * 3 * (size_t)std::max(h->nw, 1), s);
+        cudaMemsetAsync(adjoint_du(W), 0, sizeof(double), s);
+        adjoint_seed(h->P, W, h->pop[h->cur].f, h->type, h->dout, s);
+        for (int seg = nseg - 1; seg >= 0 && r == cudaSuccess; seg--) {
+            const int t0 = seg * K, t1 = std::min(nsteps, t0 + K);
+            if (seg < nseg - 1 && direct) {
+                // the checkpoint into slot 0 and the wall values into the handle, then slot to slot
+                pres_reset(h);
+                cudaMemcpyAsync(sg_f, ck_f + (size_t)seg * 27 * N, fb, cudaMemcpyDeviceToDevice, s);
+                cudaMemcpyAsync(h->Cw, ck_c + (size_t)seg * 3 * N, cb, cudaMemcpyDeviceToDevice, s);
+                for (int t = t0; t < t1 - 1 && r == cudaSuccess; t++) r = slot_step(t - t0, slot(t - t0 + 1), false);
+                cudaMemcpyAsync(sg_c + (size_t)(t1 - 1 - t0) * 3 * N, h->Cw, cb, cudaMemcpyDeviceToDevice, s);
+            } else if (seg < nseg - 1) {
+                restore(ck_f + (size_t)seg * 27 * N, ck_c + (size_t)seg * 3 * N);
+                for (int t = t0; t < t1; t++) {
+                    double* dc = sg_c + (size_t)(t - t0) * 3 * N;
+                    save(sg_f + (size_t)(t - t0) * 27 * N, dc, t < t1 - 1);
+                    if (t < t1 - 1 && (r = saved_step(dc, false)) != cudaSuccess) break;
+                }
+                save_wait();
             }
-            save_wait();
+            // the intermediates of step t - 1 are prepared on the adjoint's side stream while the
+            // reverse of step t runs
+            auto prepare = [&](int t, bool wait) {
+                return adjoint_prepare(h->P, W, t, wait, h->nw, h->widx, h->wnrm, h->wang,
+                                       sg_f + (size_t)(t - t0) * 27 * N, sg_c + (size_t)(t - t0) * 3 * N, h->type);
+            };
+            if (r == cudaSuccess) r = adjoint_sync(W, s);
+            if (r == cudaSuccess) r = prepare(t1 - 1, false);
+            for (int t = t1 - 1; t >= t0 && r == cudaSuccess; t--) {
+                if (t > t0) r = prepare(t - 1, t + 1 < t1);
+                if (r == cudaSuccess)
+                    r = adjoint_reverse(h->P, W, t, h->nw, h->widx, h->wang, sg_c + (size_t)(t - t0) * 3 * N, h->type, s);
+                if (r == cudaSuccess) r = cudaGetLastError();
+            }
+            // the segment's stored states are recomputed for the next segment; launched one by
+            // one, the host waits for this segment's reverse before it enqueues that (running
+            // further ahead made the sweep slower)
+            if (r == cudaSuccess) r = adjoint_join(W, s);
+            if (r == cudaSuccess && seg > 0 && !capturing) r = cudaStreamSynchronize(s);
         }
-        // the intermediates of step t - 1 are prepared on the adjoint's side stream while the
-        // reverse of step t runs
-        auto prepare = [&](int t, bool wait) {
-            return adjoint_prepare(h->P, W, t, wait, h->nw, h->widx, h->wnrm, h->wang,
-                                   sg_f + (size_t)(t - t0) * 27 * N, sg_c + (size_t)(t - t0) * 3 * N, h->type);
-        };
-        if (e == cudaSuccess) e = adjoint_sync(W, s);
-        if (e == cudaSuccess) e = prepare(t1 - 1, false);
-        for (int t = t1 - 1; t >= t0 && e == cudaSuccess; t--) {
-            if (t > t0) e = prepare(t - 1, t + 1 < t1);
-            if (e == cudaSuccess)
-                e = adjoint_reverse(h->P, W, t, h->nw, h->widx, h->wang, sg_c + (size_t)(t - t0) * 3 * N, h->type, s);
-            if (e == cudaSuccess) e = cudaGetLastError();
-        }
-        // the segment's stored states are recomputed for the next segment; the host waits for
-        // this segment's reverse before it enqueues that (running further ahead made the sweep
-        // slower)
-        if (e == cudaSuccess) e = adjoint_join(W, s);
-        if (e == cudaSuccess && seg > 0) e = cudaStreamSynchronize(s);
+        restore(fin_f, fin_c);
+        return r;
+    };
+    // Replayed as one CUDA graph, captured by the first call of a size (the graph holds the
+    // store's addresses, so it lives as long as the store) and dropped with the handle's other
+    // graphs when a captured parameter changes; launched one by one if the capture fails.
+    if (st.gexec && (st.g_nsteps != nsteps || st.g_K != K || st.g_cur != h->cur)) {
+        cudaGraphExecDestroy(st.gexec);
+        st.gexec = nullptr;
     }
+    if (!st.gexec && !h->graph_off) {
+        const int cur0 = h->cur;
+        cudaStream_t user = h->stream;
+        h->stream = h->gcap;
+        s = h->gcap;
+        cudaGraph_t g = nullptr;
+        cudaError_t ec = cudaStreamBeginCapture(h->gcap, cudaStreamCaptureModeThreadLocal);
+        if (ec == cudaSuccess) {
+            const cudaError_t el = enqueue_all(true);
+            ec = cudaStreamEndCapture(h->gcap, &g);
+            if (el != cudaSuccess) ec = el;
+        }
+        if (ec == cudaSuccess) ec = cudaGraphInstantiate(&st.gexec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        h->stream = user;
+        s = user;
+        if (ec == cudaSuccess) {
+            st.g_nsteps = nsteps;
+            st.g_K = K;
+            st.g_cur = cur0;
+        } else {
+            st.gexec = nullptr;
+            cudaGetLastError();  // a failed capture leaves no sticky error; clear the last one
+        }
+        h->cur = cur0;  // the capture ran nothing
+        h->pp = cur0;
+        copying = false;
+    }
+    if (st.gexec) {
+        e = cudaGraphLaunch(st.gexec, s);
+        h->cur = 0;  // where the sweep leaves the state (restore of the final state)
+        h->pp = 0;
+    } else {
+        e = enqueue_all(false);
+    }
+    double d[8];
     std::vector<double> dang(3 * (size_t)std::max(h->nw, 1));
     double du = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d, h->dout, sizeof d, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dang.data(), adjoint_dang(W), sizeof(double) * dang.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(&du, adjoint_du(W), sizeof(double), cudaMemcpyDeviceToHost, s);
-    restore(fin_f, fin_c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cleanup();
     if (e != cudaSuccess) return fail(h, LBM3_ERR_CUDA, std::string("adjoint: ") + cudaGetErrorString(e));
     int bits = 0;
     if (int rc = take_kernel_error(h, &bits)) return rc;
     if (bits & 1) return fail(h, LBM3_ERR_CUDA, "a bulk tensor copy of the step kernel did not complete in time");
-    *J_out = J;
+    *J_out = d[3] / d[0];
     for (int w = 0; w < h->nw; w++)
         for (int j = 0; j < 3; j++) dJ_dangles[3 * w + j] = dang[(size_t)j * h->nw + w];
     *dJ_du = h->P.bc_x == kZouHe ? du : 0.0;

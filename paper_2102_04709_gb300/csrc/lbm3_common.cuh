@@ -364,8 +364,9 @@ void adjoint_free(AdjointWork* W);
 size_t adjoint_bytes(const AdjointWork* W);
 double* adjoint_dang(AdjointWork* W);
 double* adjoint_du(AdjointWork* W);
-void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, double J,
-                  double M0, cudaStream_t s);
+// diag: the device diagnostics of the final state (sum rho_0 and sum x rho_0 give J)
+void adjoint_seed(const Params& P, AdjointWork* W, const float* fs, const uint8_t* type, const double* diag,
+                  cudaStream_t s);
 // the stream of the forward intermediates (idle outside the reverse sweep)
 cudaStream_t adjoint_side_stream(AdjointWork* W);
 // the side stream waits for the work enqueued on s so far
