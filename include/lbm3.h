@@ -107,10 +107,13 @@ int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3]);
 
 /* lbm3_step_timed with the other tiles split by kind: ms_out[0] = wetting pass, ms_out[1] = pure
  * tiles, ms_out[2] = wall tiles (solids within 3 nodes, halo inside the domain), ms_out[3] = edge
- * tiles (halo crossing the domain edge; on a second internal stream, concurrently with the wall
- * tiles once the wetting pass is done), summed over the steps in ms.  Synchronises.  lbm3_step_timed's
- * ms_out[2] is the sum of the last two. */
-int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[4]);
+ * tiles (halo crossing the domain edge; on a second internal stream, those with no solid within
+ * 3 nodes from the start of the step, the others once the wetting pass is done), summed over the
+ * steps in ms, and ms_out[4] = the device time of the whole run, from the event before the first
+ * step's first launch to one recorded after the last step (the host's read-back of the events
+ * after the run is outside it).  Synchronises.  lbm3_step_timed's ms_out[2] is the sum of
+ * ms_out[2] and ms_out[3]. */
+int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[5]);
 
 /* Copy the current post-streaming densities rho_k (host [3][ny][nx], 0 at solid nodes) and the
  * velocity of the most recent collision, Eq.(11) (host [2][ny][nx], may be NULL).  Synchronises.

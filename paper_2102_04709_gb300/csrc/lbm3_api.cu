@@ -780,16 +780,22 @@ int lbm3_step(lbm3* h, int32_t nsteps)
     return LBM3_OK;
 }
 
-int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[4])
+int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[5])
 {
     if (!h || !ms_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
     if (nsteps < 0) return fail(h, LBM3_ERR_INVALID, "nsteps < 0");
     if (!h->ready) return fail(h, LBM3_ERR_STATE, "lbm3_set_fields has not been called");
-    for (int j = 0; j < 4; j++) ms_out[j] = 0.0;
-    std::vector<cudaEvent_t> ev(7 * (size_t)nsteps);
+    for (int j = 0; j < 5; j++) ms_out[j] = 0.0;
+    std::vector<cudaEvent_t> ev(7 * (size_t)nsteps + 1);  // 7 per step, and the end of the run
     for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
     for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[7 * (size_t)s]));
+    CUDA_TRY(h, cudaEventRecord(ev.back(), h->stream));  // after the last step's joins
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    if (nsteps > 0) {
+        float t = 0.f;
+        CUDA_TRY(h, cudaEventElapsedTime(&t, ev[0], ev.back()));
+        ms_out[4] = t;
+    }
     for (int s = 0; s < nsteps; s++) {
         const cudaEvent_t* E = &ev[7 * (size_t)s];
         const int from[4] = {2, 0, 3, 5}, to[4] = {3, 1, 4, 6};
@@ -806,7 +812,7 @@ int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[4])
 int lbm3_step_timed(lbm3* h, int32_t nsteps, double ms_out[3])
 {
     if (!ms_out) return fail(h, LBM3_ERR_INVALID, "NULL argument");
-    double d[4];
+    double d[5];
     const int rc = lbm3_step_timed_detail(h, nsteps, d);
     if (rc != LBM3_OK) return rc;
     ms_out[0] = d[0];
@@ -1201,7 +1207,8 @@ int lbm3_info(const lbm3* h, int64_t out[9])
     // and 8 16-bit offsets (120 B); plus one class byte per node
     const long long per = h->precision == LBM3_FP32 ? 216 : 120;
     out[2] = h->n_fluid * per + h->P.N;
-    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_gen > h->n_walltiles);
+    out[3] = (h->n_pure > 0) + (h->n_walltiles > 0) + (h->n_edgewall > 0) +
+             (h->n_gen - h->n_walltiles - h->n_edgewall > 0);
     out[4] = h->nw > 0 ? 1 : 0;
     out[5] = (int64_t)h->bytes;
     // the pure-tile launch reads and writes 27 FP32 populations per node and no class bytes

@@ -189,8 +189,8 @@ class Lbm3:
 
     def step_timed_detail(self, n):
         """Advance n steps; return CUDA-event times in ms summed over the steps: (wetting pass,
-        pure tiles, wall tiles, edge tiles)."""
-        out = np.zeros(4)
+        pure tiles, wall tiles, edge tiles, the whole run on the device)."""
+        out = np.zeros(5)
         _check(self._h, load().lbm3_step_timed_detail(self._h, int(n), _dp(out)))
         return tuple(float(v) for v in out)
 
