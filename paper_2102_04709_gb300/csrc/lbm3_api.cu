@@ -51,6 +51,9 @@ struct lbm3 {
     const Pop* io_in = nullptr;
     const Pop* io_out = nullptr;
     const CUtensorMap* io_box = nullptr;
+    // the timing events of enqueue_step are recorded into a graph being captured (as nodes that
+    // record them when the graph runs)
+    bool ev_external = false;
     int nw = 0;
     long long n_fluid = 0;
     // tiles of the fused step kernel: pure tiles (no solid within 3 nodes, away from the domain
@@ -280,6 +283,15 @@ bool make_tensor_maps16(const Params& P, const Pop& p, CUtensorMap* trho, CUtens
 // the edge tiles (at once those without a solid node near them, after the wetting pass the
 // others), join.  With ev != NULL the launches are bracketed by the events ev[0..6] (main: 0-1
 // pure tiles; side: 2-3 wetting pass, 3-4 wall tiles; second side stream: 5-6 edge tiles).
+// a timing event of enqueue_step (a record node when captured into a graph)
+void record_timing(lbm3* h, cudaEvent_t ev, cudaStream_t s)
+{
+    if (h->ev_external)
+        cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+    else
+        cudaEventRecord(ev, s);
+}
+
 cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
 {
     cudaError_t e;
@@ -289,7 +301,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     float* u = last ? h->u : nullptr;
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
-    if (ev) cudaEventRecord(ev[0], h->stream);
+    if (ev) record_timing(h, ev[0], h->stream);
     if (h->ring)
         launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, io ? *h->io_box : h->tm_box[h->cur],
                          h->pres[h->pp], h->pres[1 - h->pp], h->stream);
@@ -302,11 +314,11 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     else
         launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, kTilesPure, fin, fo, h->type, h->Cw, u,
                     h->stream);
-    if (ev) cudaEventRecord(ev[1], h->stream);
-    if (ev) cudaEventRecord(ev[2], h->side);
+    if (ev) record_timing(h, ev[1], h->stream);
+    if (ev) record_timing(h, ev[2], h->side);
     launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side,
                h->cw_keep);
-    if (ev) cudaEventRecord(ev[3], h->side);
+    if (ev) record_timing(h, ev[3], h->side);
     // edge tiles: those without a solid node near them start at once, the others after the
     // wetting pass
     const int n_edge = h->n_gen - h->n_walltiles, n_edge_free = n_edge - h->n_edgewall;
@@ -314,7 +326,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     const bool edges = n_edge > 0;
     if (edges) {
         if ((e = cudaStreamWaitEvent(h->side2, h->ev_fork, 0)) != cudaSuccess) return e;
-        if (ev) cudaEventRecord(ev[5], h->side2);
+        if (ev) record_timing(h, ev[5], h->side2);
         launch_step(h->precision, h->P, tiles_edge + h->n_edgewall, n_edge_free, kTilesEdge, fin, fo, h->type,
                     h->Cw, u, h->side2);
         if (h->n_edgewall > 0) {
@@ -324,16 +336,16 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     }
     launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
                 h->side);
-    if (ev) cudaEventRecord(ev[4], h->side);
+    if (ev) record_timing(h, ev[4], h->side);
     if (edges) {
         launch_step(h->precision, h->P, tiles_edge, h->n_edgewall, kTilesEdge, fin, fo, h->type, h->Cw, u,
                     h->side2);
-        if (ev) cudaEventRecord(ev[6], h->side2);
+        if (ev) record_timing(h, ev[6], h->side2);
         if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(h->stream, h->ev_join2, 0)) != cudaSuccess) return e;
     } else if (ev) {
-        cudaEventRecord(ev[5], h->side);
-        cudaEventRecord(ev[6], h->side);
+        record_timing(h, ev[5], h->side);
+        record_timing(h, ev[6], h->side);
     }
     if ((e = cudaEventRecord(h->ev_join, h->side)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->stream, h->ev_join, 0)) != cudaSuccess) return e;
@@ -788,9 +800,47 @@ int lbm3_step_timed_detail(lbm3* h, int32_t nsteps, double ms_out[5])
     for (int j = 0; j < 5; j++) ms_out[j] = 0.0;
     std::vector<cudaEvent_t> ev(7 * (size_t)nsteps + 1);  // 7 per step, and the end of the run
     for (auto& e : ev) CUDA_TRY(h, cudaEventCreate(&e));
-    for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[7 * (size_t)s]));
-    CUDA_TRY(h, cudaEventRecord(ev.back(), h->stream));  // after the last step's joins
-    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    // The steps are captured into one graph with the events as record nodes, so that they run
+    // as lbm3_step runs them (replayed graphs) rather than launched one by one; launched one by
+    // one if the capture fails.
+    bool ran = false;
+    if (nsteps > 0 && !h->graph_off) {
+        const int c0 = h->cur, p0 = h->pp;
+        cudaStream_t user = h->stream;
+        h->stream = h->gcap;
+        h->ev_external = true;
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t x = nullptr;
+        cudaError_t ec = cudaStreamBeginCapture(h->gcap, cudaStreamCaptureModeThreadLocal);
+        if (ec == cudaSuccess) {
+            cudaError_t el = cudaSuccess;
+            for (int s = 0; s < nsteps && el == cudaSuccess; s++) el = enqueue_step(h, s == nsteps - 1, &ev[7 * (size_t)s]);
+            if (el == cudaSuccess) el = cudaEventRecordWithFlags(ev.back(), h->gcap, cudaEventRecordExternal);
+            ec = cudaStreamEndCapture(h->gcap, &g);
+            if (el != cudaSuccess) ec = el;
+        }
+        h->ev_external = false;
+        h->stream = user;
+        if (ec == cudaSuccess) ec = cudaGraphInstantiate(&x, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (ec == cudaSuccess) {
+            // cur and pp turned during the capture as the steps turn them
+            cudaError_t er = cudaGraphLaunch(x, h->stream);
+            if (er == cudaSuccess) er = cudaStreamSynchronize(h->stream);
+            cudaGraphExecDestroy(x);
+            CUDA_TRY(h, er);
+            ran = true;
+        } else {
+            h->cur = c0;
+            h->pp = p0;
+            cudaGetLastError();  // a failed capture leaves no sticky error; clear the last one
+        }
+    }
+    if (!ran) {
+        for (int s = 0; s < nsteps; s++) CUDA_TRY(h, enqueue_step(h, s == nsteps - 1, &ev[7 * (size_t)s]));
+        CUDA_TRY(h, cudaEventRecord(ev.back(), h->stream));  // after the last step's joins
+        CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+    }
     if (nsteps > 0) {
         float t = 0.f;
         CUDA_TRY(h, cudaEventElapsedTime(&t, ev[0], ev.back()));

@@ -180,6 +180,36 @@ def test_graph_replay_matches_single_launches(gpu, precision):
     b.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp32", "fp16"])
+def test_timed_steps_match_lbm3_step(gpu, precision):
+    """lbm3_step_timed_detail (the steps captured into one graph with the timing events as record
+    nodes) leaves the state lbm3_step leaves, bit for bit, velocity included, and its times are
+    consistent: every kernel's sum is positive and below the run's span, and the pure tiles
+    overlap the rest (their sum exceeds neither the span nor the others' by more than the span)."""
+    w = small_pillars()
+    a = gpu.Lbm3.from_workload(w, precision=precision)
+    b = gpu.Lbm3.from_workload(w, precision=precision)
+    a.step(5)
+    b.step(5)
+    t = a.step_timed_detail(23)
+    b.step(23)
+    fa, ca = a.get_state()
+    fb, cb = b.get_state()
+    ra, ua = a.fields()
+    rb, ub = b.fields()
+    assert np.array_equal(fa, fb) and np.array_equal(ca, cb)
+    assert np.array_equal(ra, rb) and np.array_equal(ua, ub)
+    wet, pure, wall, edge, run = t
+    assert run > 0 and all(v >= 0 for v in t)
+    assert pure <= run and wet + wall <= run and edge <= run
+    # the same call continues from where it left off: 3 more timed steps equal 3 more steps
+    a.step_timed_detail(3)
+    b.step(3)
+    assert np.array_equal(a.get_state()[0], b.get_state()[0])
+    a.close()
+    b.close()
+
+
 def test_inflow_change_drops_captured_graphs(gpu):
     """The graphs hold the launch arguments; lbm3_set_inflow must make the next call capture
     anew: 20 steps, U -> 0.03, 20 steps equals the same sequence of single steps."""
