@@ -989,6 +989,9 @@ int lbm3_set_wall_angles(lbm3* h, const double* angles)
     }
     if (!a.empty())
         CUDA_TRY(h, cudaMemcpyAsync(h->wang, a.data(), a.size() * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+    // the wetting pass keeps each lane's angle with the wall values it came from: forget them
+    reset_wet_cache(h->wcache, h->nw, h->stream);
+    CUDA_TRY(h, cudaGetLastError());
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
     return LBM3_OK;
 }

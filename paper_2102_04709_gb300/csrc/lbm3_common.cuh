@@ -298,9 +298,12 @@ __device__ void pull_global(const Params& P, const S& st, const uint8_t* __restr
 // Where the characteristic line of one lane of the wetting pass (C_SB node, wetted fluid, side)
 // met the fluid for the local contact angle th of Eq.(21) it was marched with: the line depends
 // on th and the fixed geometry only, so while a node's th repeats bit for bit (every node away
-// from a moving contact line) the march is skipped and its crossing reused.  th = NaN: none yet.
+// from a moving contact line) the march is skipped and its crossing reused.  th itself is kept
+// with the two wall values (wm, wl) of Eq.(21) it came from, so that while those repeat it is
+// not recomputed either (the wall angles are fixed between resets of the cache).  th, wm, wl =
+// NaN: none yet.
 struct WetCache {
-    double th, fr;
+    double th, fr, wm, wl;
     int kind, ax, ay, bx, by, pad;
 };
 

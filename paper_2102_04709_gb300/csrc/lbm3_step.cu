@@ -51,22 +51,29 @@ __global__ void __launch_bounds__(128) k_wet(const Params P, const int nw, const
             Cw_prev[P.N + i] = Cg;
             Cw_prev[2 * P.N + i] = Cb;
         }
-        const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
-        th = k == 0 ? local_angle(Cb, 180.0 - t_br, Cg, t_rg) : local_angle(Cb, t_gb, Cr, 180.0 - t_rg);
-        WetCache c = cache[g];
-        if (c.th == th) {
-            // the same angle as when this lane last marched: the same line, the same crossing
+        const double wm = Cb, wl = k == 0 ? Cg : Cr;  // the weights of Eq.(21) for fluid k
+        const WetCache c = cache[g];
+        if (c.wm == wm && c.wl == wl) {
+            // the same wall values as last time: the same angle, line and crossing
+            th = c.th;
             cr = Crossing{c.kind, c.ax, c.ay, c.bx, c.by, c.fr};
         } else {
-            const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
-            const double dev = fabs(90.0 - th);
-            const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
-            double sn, cs;
-            sincos(phi, &sn, &cs);
-            if (side) sn = -sn;
-            // the line makes the angle phi with n_s (tangent (-n_y, n_x))
-            cr = characteristic_line<S>(P, type, px, py, cs * nx_ - sn * ny_, cs * ny_ + sn * nx_);
-            cache[g] = WetCache{th, cr.fr, cr.kind, cr.ax, cr.ay, cr.bx, cr.by, 0};
+            const double t_rg = wang[3 * w], t_br = wang[3 * w + 1], t_gb = wang[3 * w + 2];
+            th = k == 0 ? local_angle(wm, 180.0 - t_br, wl, t_rg) : local_angle(wm, t_gb, wl, 180.0 - t_rg);
+            if (c.th == th) {
+                // the same angle as when this lane last marched: the same line, the same crossing
+                cr = Crossing{c.kind, c.ax, c.ay, c.bx, c.by, c.fr};
+            } else {
+                const double nx_ = wnrm[2 * w], ny_ = wnrm[2 * w + 1];
+                const double dev = fabs(90.0 - th);
+                const double phi = dev < kPhiSnap ? 0.0 : dev * (M_PI / 180.0);
+                double sn, cs;
+                sincos(phi, &sn, &cs);
+                if (side) sn = -sn;
+                // the line makes the angle phi with n_s (tangent (-n_y, n_x))
+                cr = characteristic_line<S>(P, type, px, py, cs * nx_ - sn * ny_, cs * ny_ + sn * nx_);
+            }
+            cache[g] = WetCache{th, cr.fr, wm, wl, cr.kind, cr.ax, cr.ay, cr.bx, cr.by, 0};
         }
     }
     double ca = 0.0, cb = 0.0;
@@ -1533,7 +1540,12 @@ void launch_wet(int store, const Params& P, int nw, const int* widx, const doubl
 __global__ void k_wet_cache_reset(WetCache* cache, int n)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) cache[i].th = __longlong_as_double(0x7ff8000000000000LL);  // NaN: never equal
+    if (i < n) {
+        const double nan = __longlong_as_double(0x7ff8000000000000LL);  // never equal
+        cache[i].th = nan;
+        cache[i].wm = nan;
+        cache[i].wl = nan;
+    }
 }
 
 void reset_wet_cache(WetCache* cache, int nw, cudaStream_t s)
