@@ -310,7 +310,7 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
                         h->tm_in_b[h->cur], h->tm_out[1 - h->cur], h->stream);
     else if (h->tma)
         launch_step_tma16(h->precision, h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
-                          h->tm_in_b[h->cur], h->stream);
+                          h->tm_in_b[h->cur], h->pres[h->pp], h->pres[1 - h->pp], h->stream);
     else
         launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, kTilesPure, fin, fo, h->type, h->Cw, u,
                     h->stream);

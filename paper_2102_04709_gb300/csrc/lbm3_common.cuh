@@ -344,7 +344,8 @@ void launch_step_ring(const Params& P, const int* tiles, int ntiles, int nblocks
 // (box (kTX + 16, kTY + 6, 24) of [24][ny][nx] 16-bit words)
 size_t step_tma16_smem_bytes();
 void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
-                       float* u, const CUtensorMap& trho, const CUtensorMap& toff, cudaStream_t s);
+                       float* u, const CUtensorMap& trho, const CUtensorMap& toff, const uint64_t* pres_in,
+                       uint64_t* pres_out, cudaStream_t s);
 // tile lists of the fused step: pure tiles (no solid within 3 nodes, away from the domain
 // edge), wall tiles (solids near, halo inside the domain) and edge tiles (halo crossing the
 // domain edge: wrap, ghost columns, seam)

@@ -1601,7 +1601,9 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
                                                             const int ntiles, const Pop fout,
                                                             float* __restrict__ uout,
                                                             const __grid_constant__ CUtensorMap tm_rho,
-                                                            const __grid_constant__ CUtensorMap tm_off)
+                                                            const __grid_constant__ CUtensorMap tm_off,
+                                                            const uint64_t* __restrict__ pres_in,
+                                                            uint64_t* __restrict__ pres_out)
 {
     constexpr int NT = TX * TY;
     constexpr int CX = TX + 4, CY = TY + 4;
@@ -1616,7 +1618,8 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
     __shared__ float s_rho[CY][CX];
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
     __shared__ __align__(8) uint64_t s_bar;
-    __shared__ int s_flags[2];  // fluids present in the tile, by iteration parity
+    __shared__ int s_flags[2];   // fluids present in the tile, by iteration parity
+    __shared__ int s_single[2];  // by iteration parity: the tile's 3 x 3 tiles hold one fluid
     extern __shared__ unsigned char dsm[];
     float* rbox = reinterpret_cast<float*>(dsm + ((128u - (smem_u32(dsm) & 127u)) & 127u));  // [3][BY][BX]
     const unsigned short* obox = reinterpret_cast<const unsigned short*>(rbox + NRP);          // [24][BY][OX]
@@ -1632,6 +1635,19 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
         tma_load_3d(smem_u32(rbox), &tm_rho, x0 - 4, y0 - 3, 0, bar);
         tma_load_3d(smem_u32(obox), &tm_off, x0 - 8, y0 - 3, 0, bar);
     };
+    // fluids stored in the 3 x 3 tiles around a tile (a pure tile is inner, so they exist): one
+    // fluid means the tile holds it alone after the pull (as in k_step_ring)
+    auto single_around = [&](int t) {
+        uint64_t nb = 0;
+#pragma unroll
+        for (int dy = -1; dy <= 1; dy++)
+#pragma unroll
+            for (int dx = -1; dx <= 1; dx++) nb |= pres_in[t + dy * ntx + dx];
+        nb |= nb >> 32;
+        nb |= nb >> 16;
+        nb |= nb >> 8;
+        return __popc((unsigned)(nb & 7u)) == 1 ? 1 : 0;
+    };
     int tile = tiles[blockIdx.x];
     int last = 0;
     if (tid == 0) {
@@ -1639,6 +1655,7 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
         fence_mbar_init();
         issue(tile);
         s_flags[0] = s_flags[1] = 0;
+        s_single[0] = single_around(tile);
     }
     __syncthreads();
 
@@ -1693,9 +1710,11 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
             return;
         }
 
+        const bool single = s_single[j & 1];
+        int single_next = 0;  // thread 0: for the next tile, written once this one is computed
         // ---- phase 1: pulls, densities and phase fields of the halo-2 region ----
         int present = 0;
-        {
+        if (!single) {
             constexpr int NRING = CX * CY - TX * TY;
             for (int r = tid; r < NRING; r += NT) {
                 int cx, cy;
@@ -1720,23 +1739,38 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
         {
             float q[27];
             pull(lx + 2, ly + 2, q);
-            present |= store_phase(lx + 2, ly + 2, q);
+            if (!single) present |= store_phase(lx + 2, ly + 2, q);
 #pragma unroll
             for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
             r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
             r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
             r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
         }
-        const bool mixed = fluids_present(present, s_flags, j, tid) != 1;
+        // the fluids this warp's nodes hold, for the tiles around this one in the next step
+        {
+            const int own = (r0 != 0.0f ? 1 : 0) | (r1 != 0.0f ? 2 : 0) | (r2 != 0.0f ? 4 : 0);
+            const int w = __reduce_or_sync(0xffffffffu, own);
+            if ((tid & 31) == 0) reinterpret_cast<uint8_t*>(pres_out + tile)[tid >> 5] = (uint8_t)w;
+        }
+        bool mixed = false;
+        if (single) {
+            __syncthreads();  // every pull is done before the boxes are refilled
+            if (tid == 0) s_flags[(j + 1) & 1] = 0;
+        } else {
+            mixed = fluids_present(present, s_flags, j, tid) != 1;
+        }
         // the boxes are free: fetch the next tile's while this one computes
         if (tid == 0 && more) {
             issue(next);
             last = j + 1;
+            single_next = single_around(next);
         }
 
         // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
-        if (mixed) stress_halo1<TX, TY>(P, s_ch, s_rho, s_txx, s_txy, s_tyy, tid);
-        __syncthreads();
+        if (!single) {
+            if (mixed) stress_halo1<TX, TY>(P, s_ch, s_rho, s_txx, s_txy, s_tyy, tid);
+            __syncthreads();
+        }
 
         // ---- phase 3: force, collision, recolouring, 16-bit stores ----
         float Fx = 0.0f, Fy = 0.0f, g[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
@@ -1760,6 +1794,8 @@ __global__ void __launch_bounds__(TX* TY, kTma16BlocksPerSm) k_step_tma16(const 
             for (int a = 0; a < kQ; a++)
                 v[9 * k + a] = rc.C[k] * f[a] + wq(a) * (rc.Vx[k] * (float)ex(a) + rc.Vy[k] * (float)ey(a));
         store_node<STORE>(fout, P.N, i, v);
+        // read by every thread after the next tile's first barrier
+        if (tid == 0) s_single[(j + 1) & 1] = single_next;
     }
 }
 
@@ -1829,16 +1865,17 @@ cudaError_t step_tma16_prepare()
 }
 
 void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles, int nblocks, const Pop& fout,
-                       float* u, const CUtensorMap& trho, const CUtensorMap& toff, cudaStream_t s)
+                       float* u, const CUtensorMap& trho, const CUtensorMap& toff, const uint64_t* pres_in,
+                       uint64_t* pres_out, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     const int nb = nblocks < ntiles ? nblocks : ntiles;
     if (store == kStoreF16)
-        k_step_tma16<kTX, kTY, kStoreF16>
-            <<<nb, dim3(kTX, kTY), step_tma16_smem_bytes(), s>>>(P, tiles, ntiles, fout, u, trho, toff);
+        k_step_tma16<kTX, kTY, kStoreF16><<<nb, dim3(kTX, kTY), step_tma16_smem_bytes(), s>>>(
+            P, tiles, ntiles, fout, u, trho, toff, pres_in, pres_out);
     else
-        k_step_tma16<kTX, kTY, kStoreBF16>
-            <<<nb, dim3(kTX, kTY), step_tma16_smem_bytes(), s>>>(P, tiles, ntiles, fout, u, trho, toff);
+        k_step_tma16<kTX, kTY, kStoreBF16><<<nb, dim3(kTX, kTY), step_tma16_smem_bytes(), s>>>(
+            P, tiles, ntiles, fout, u, trho, toff, pres_in, pres_out);
 }
 
 void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,

@@ -305,15 +305,15 @@ def test_state_roundtrip(gpu):
 
 @pytest.mark.parametrize("precision,kernel,nx,ny", [(0, "ring", 200, 100), (0, "ring", 512, 260),
                                                    (0, "tma", 200, 100), (1, "", 200, 100),
-                                                   (2, "", 200, 100)],
-                         ids=["fp32-ring", "fp32-ring-wide", "fp32-tma", "fp16", "bf16"])
+                                                   (1, "", 512, 264), (2, "", 200, 100)],
+                         ids=["fp32-ring", "fp32-ring-wide", "fp32-tma", "fp16", "fp16-wide", "bf16"])
 def test_tma_path_matches_plain_kernel(gpu, monkeypatch, precision, kernel, nx, ny):
     """The bulk-tensor-copy paths move the same stored values through shared memory, so they give
     bit-identical results to the plain kernels (LBM3_DISABLE_TMA=1), for every storage and both
     FP32 pure-tile kernels (the warp-specialised ring, and LBM3_PURE_KERNEL=tma), on a grid with
     pure tiles, walls, Zou-He and a ragged last tile row.  The wide case leaves most of the grid
-    to the carrier fluid alone, so that most pure tiles have single-fluid neighbours and the ring
-    kernel skips their halo phase fields: the results must not change."""
+    to the carrier fluid alone, so that most pure tiles have single-fluid neighbours and the pure-tile
+    kernels skip their halo phase fields: the results must not change."""
     w = W.pillars(nx=nx, ny=ny, count=4, r_lo=8.0, r_hi=14.0, x_lo=90.0, x_hi=180.0, gap=6.0,
                   seed=11, drop=(50.0, 48.0), r_core=12.0, r_shell=22.0, theta_range=(60.0, 120.0),
                   u_in=0.02)
