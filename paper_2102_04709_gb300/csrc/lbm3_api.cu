@@ -299,21 +299,23 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
     const Pop& fin = io ? *h->io_in : h->pop[h->cur];
     const Pop& fo = io ? *h->io_out : h->pop[1 - h->cur];
     float* u = last ? h->u : nullptr;
+    const uint64_t* pin = h->pres[h->pp];
+    uint64_t* pout = h->pres[1 - h->pp];
     if ((e = cudaEventRecord(h->ev_fork, h->stream)) != cudaSuccess) return e;
     if ((e = cudaStreamWaitEvent(h->side, h->ev_fork, 0)) != cudaSuccess) return e;
     if (ev) record_timing(h, ev[0], h->stream);
     if (h->ring)
         launch_step_ring(h->P, h->tiles_pure, h->n_pure, h->ring_blocks, fo, u, io ? *h->io_box : h->tm_box[h->cur],
-                         h->pres[h->pp], h->pres[1 - h->pp], h->stream);
+                         pin, pout, h->stream);
     else if (h->tma && h->precision == LBM3_FP32)
         launch_step_tma(h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
                         h->tm_in_b[h->cur], h->tm_out[1 - h->cur], h->stream);
     else if (h->tma)
         launch_step_tma16(h->precision, h->P, h->tiles_pure, h->n_pure, h->tma_blocks, fo, u, h->tm_in_a[h->cur],
-                          h->tm_in_b[h->cur], h->pres[h->pp], h->pres[1 - h->pp], h->stream);
+                          h->tm_in_b[h->cur], pin, pout, h->stream);
     else
         launch_step(h->precision, h->P, h->tiles_pure, h->n_pure, kTilesPure, fin, fo, h->type, h->Cw, u,
-                    h->stream);
+                    pin, pout, h->stream);
     if (ev) record_timing(h, ev[1], h->stream);
     if (ev) record_timing(h, ev[2], h->side);
     launch_wet(h->precision, h->P, h->nw, h->widx, h->wnrm, h->wang, fin, h->type, h->Cw, h->wcache, h->side,
@@ -328,18 +330,18 @@ cudaError_t enqueue_step(lbm3* h, bool last, cudaEvent_t* ev)
         if ((e = cudaStreamWaitEvent(h->side2, h->ev_fork, 0)) != cudaSuccess) return e;
         if (ev) record_timing(h, ev[5], h->side2);
         launch_step(h->precision, h->P, tiles_edge + h->n_edgewall, n_edge_free, kTilesEdge, fin, fo, h->type,
-                    h->Cw, u, h->side2);
+                    h->Cw, u, pin, pout, h->side2);
         if (h->n_edgewall > 0) {
             if ((e = cudaEventRecord(h->ev_wet, h->side)) != cudaSuccess) return e;
             if ((e = cudaStreamWaitEvent(h->side2, h->ev_wet, 0)) != cudaSuccess) return e;
         }
     }
-    launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u,
-                h->side);
+    launch_step(h->precision, h->P, h->tiles_gen, h->n_walltiles, kTilesWall, fin, fo, h->type, h->Cw, u, pin,
+                pout, h->side);
     if (ev) record_timing(h, ev[4], h->side);
     if (edges) {
-        launch_step(h->precision, h->P, tiles_edge, h->n_edgewall, kTilesEdge, fin, fo, h->type, h->Cw, u,
-                    h->side2);
+        launch_step(h->precision, h->P, tiles_edge, h->n_edgewall, kTilesEdge, fin, fo, h->type, h->Cw, u, pin,
+                    pout, h->side2);
         if (ev) record_timing(h, ev[6], h->side2);
         if ((e = cudaEventRecord(h->ev_join2, h->side2)) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(h->stream, h->ev_join2, 0)) != cudaSuccess) return e;

@@ -350,8 +350,11 @@ void launch_step_tma16(int store, const Params& P, const int* tiles, int ntiles,
 // edge), wall tiles (solids near, halo inside the domain) and edge tiles (halo crossing the
 // domain edge: wrap, ghost columns, seam)
 constexpr int kTilesPure = 0, kTilesWall = 1, kTilesEdge = 2;
+// pres_in / pres_out: fluids present per tile in the step's input / output; the wall tiles read
+// and write them (see k_step), the other kinds ignore them
 void launch_step(int store, const Params& P, const int* tiles, int ntiles, int kind, const Pop& fin,
-                 const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s);
+                 const Pop& fout, const uint8_t* type, const double* Cw, float* u, const uint64_t* pres_in,
+                 uint64_t* pres_out, cudaStream_t s);
 void launch_init(int store, const Params& P, const double* rho, const uint8_t* type, const Pop& f,
                  cudaStream_t s);
 void launch_fields(int store, const Params& P, const Pop& f, const uint8_t* type, float* rho_out,

@@ -534,7 +534,9 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
                                                   const Pop fin, const Pop fout,
                                                   const uint8_t* __restrict__ type,
                                                   const double* __restrict__ Cw,
-                                                  float* __restrict__ uout)
+                                                  float* __restrict__ uout,
+                                                  const uint64_t* __restrict__ pres_in,
+                                                  uint64_t* __restrict__ pres_out)
 {
     constexpr int NT = TX * TY;
     constexpr int HX = TX + 6, HY = TY + 6;  // geometry region (halo 3)
@@ -548,6 +550,10 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
     __shared__ float s_txx[RY][RX], s_txy[RY][RX], s_tyy[RY][RX];
     __shared__ float s_g[2 * kNF][TY][TX];   // colour gradients of the tile's own nodes
     __shared__ int s_flags[2];                // fluids present (wall and edge tiles)
+    // wall tiles: fluids stored in the 3 x 3 tiles around (one word each), and the fluids with a
+    // nonzero wall value at the C_SB nodes of the phase-field region (one word per warp)
+    __shared__ uint64_t s_nb[9];
+    __shared__ int s_wp[TX * TY / 32];
 
     const int tid = threadIdx.x + TX * threadIdx.y;
     if (!PURE && tid == 0) s_flags[0] = 0;  // published by the phase-0 barrier
@@ -561,16 +567,26 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
     const bool inner = PURE || INNER || (x0 >= 3 && y0 >= 3 && x0 + TX + 3 <= P.nx && y0 + TY + 3 <= P.ny);
 
     // ---- phase 0: geometry of the halo-3 region ----
-    int wall = 0;
+    int wall = 0, wp = 0;
     if (PURE) {
     } else if (inner) {
+        if constexpr (INNER) {
+            if (tid < 9) s_nb[tid] = pres_in[tile + (tid / 3 - 1) * ntx + (tid % 3 - 1)];
+        }
         for (int j = tid; j < HX * HY; j += NT) {
             const int hx = j % HX, hy = j / HX;
             const uint8_t t = __ldg(type + (y0 + hy - 3) * nx + (x0 + hx - 3));
             s_t[hy][hx] = t;
-            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY &&
-                mixed_wall(Cw, P.N, (y0 + hy - 3) * nx + (x0 + hx - 3)))
-                wall = 1;
+            if ((t & 3) == kSB && hx >= 1 && hx <= CX && hy >= 1 && hy <= CY) {
+                const long long in = (long long)(y0 + hy - 3) * nx + (x0 + hx - 3);
+                const double c0 = Cw[in], c1 = Cw[P.N + in], c2 = Cw[2 * P.N + in];
+                if (fmax(fmax(c0, c1), c2) < 1.0 - kMixEps) wall = 1;  // mixed_wall
+                wp |= (c0 != 0.0 ? 1 : 0) | (c1 != 0.0 ? 2 : 0) | (c2 != 0.0 ? 4 : 0);
+            }
+        }
+        if constexpr (INNER) {
+            const int w = __reduce_or_sync(0xffffffffu, wp);
+            if ((tid & 31) == 0) s_wp[tid >> 5] = w;
         }
     } else {
         for (int j = tid; j < HX * HY; j += NT) {
@@ -590,6 +606,25 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
         }
     }
     const bool df = PURE ? false : __syncthreads_or(wall);
+    // A wall tile whose 3 x 3 tiles stored one fluid, and whose C_SB nodes in the phase-field
+    // region have wall values of that fluid only, holds that fluid alone in the region after
+    // the pull: it is not mixed, and its halo's phase fields, which only the mixed path reads,
+    // are skipped (same results).  The plain float path only (no float-float words).
+    bool single = false;
+    if constexpr (INNER && !PURE) {
+        if (!df) {
+            uint64_t nb = 0;
+#pragma unroll
+            for (int t = 0; t < 9; t++) nb |= s_nb[t];
+            nb |= nb >> 32;
+            nb |= nb >> 16;
+            nb |= nb >> 8;
+            int bits = (int)(nb & 7u);
+#pragma unroll
+            for (int w = 0; w < TX * TY / 32; w++) bits |= s_wp[w];
+            single = __popc(bits) == 1;
+        }
+    }
 
     // ---- phase 1: post-streaming populations, densities and phase fields ----
     // pull of the fluid node at (hx, hy) of the geometry region into q[27]
@@ -698,7 +733,7 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
         return false;
     };
 
-    {
+    if (!single) {
         // ring of the halo-2 region: rows 0, 1, CY-2, CY-1 and columns 0, 1, CX-2, CX-1
         constexpr int NRING = CX * CY - TX * TY;
         for (int j = tid; j < NRING; j += NT) {
@@ -726,16 +761,28 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
     bool own_fluid;
     {
         float q[27];
-        own_fluid = fill(lx + 2, ly + 2, q);
+        if (single) {
+            own_fluid = !(s_t[ly + 3][lx + 3] & 2);
+            if (own_fluid) pull(lx + 3, ly + 3, q);
+        } else {
+            own_fluid = fill(lx + 2, ly + 2, q);
+        }
 #pragma unroll
         for (int a = 0; a < kQ; a++) f[a] = (q[a] + q[9 + a]) + q[18 + a];
         r0 = ((q[0] + (q[1] + q[3])) + (q[2] + q[4])) + ((q[5] + q[7]) + (q[6] + q[8]));
         r1 = ((q[9] + (q[10] + q[12])) + (q[11] + q[13])) + ((q[14] + q[16]) + (q[15] + q[17]));
         r2 = ((q[18] + (q[19] + q[21])) + (q[20] + q[22])) + ((q[23] + q[25]) + (q[24] + q[26]));
     }
+    if constexpr (INNER && !PURE) {
+        // the fluids this warp's fluid nodes hold, for the tiles around this one in the next step
+        const int own = own_fluid ? (r0 != 0.0f ? 1 : 0) | (r1 != 0.0f ? 2 : 0) | (r2 != 0.0f ? 4 : 0) : 0;
+        const int w = __reduce_or_sync(0xffffffffu, own);
+        if ((tid & 31) == 0) reinterpret_cast<uint8_t*>(pres_out + tile)[tid >> 5] = (uint8_t)w;
+    }
     // fluids present in the phase-field region: one barrier for tiles that had one already (the
     // word was cleared before the phase-0 barrier), three for the pure tiles of the plain path
-    const bool mixed = (PURE ? single_fluid_or(present) : fluids_present(present, s_flags, 0, tid)) != 1;
+    const bool mixed =
+        single ? false : (PURE ? single_fluid_or(present) : fluids_present(present, s_flags, 0, tid)) != 1;
 
     // ---- phase 2: stress tensor of Eq.(10) on the halo-1 region ----
     for (int j = mixed ? tid : RX * RY; j < RX * RY; j += NT) {
@@ -768,7 +815,7 @@ __global__ void __launch_bounds__(TX* TY, (INNER && !PURE) ? kStepBlocksPerSm : 
         s_txy[ry][rx] = Txy;
         s_tyy[ry][rx] = Tyy;
     }
-    __syncthreads();
+    if (!single) __syncthreads();
 
     if (!own_fluid || gx >= P.nx || gy >= P.ny) return;
 
@@ -1566,26 +1613,31 @@ void launch_wet_init(int store, const Params& P, int nw, const int* widx, const 
 
 template <int STORE>
 static void launch_step_t(const Params& P, const int* tiles, int ntiles, int kind, const Pop& fin,
-                          const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
+                          const Pop& fout, const uint8_t* type, const double* Cw, float* u,
+                          const uint64_t* pres_in, uint64_t* pres_out, cudaStream_t s)
 {
     if (kind == kTilesPure)
-        k_step<kTX, kTY, true, true, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+        k_step<kTX, kTY, true, true, STORE>
+            <<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u, pres_in, pres_out);
     else if (kind == kTilesWall)
-        k_step<kTX, kTY, false, true, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+        k_step<kTX, kTY, false, true, STORE>
+            <<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u, pres_in, pres_out);
     else
-        k_step<kTX, kTY, false, false, STORE><<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u);
+        k_step<kTX, kTY, false, false, STORE>
+            <<<ntiles, dim3(kTX, kTY), 0, s>>>(P, tiles, fin, fout, type, Cw, u, pres_in, pres_out);
 }
 
 void launch_step(int store, const Params& P, const int* tiles, int ntiles, int kind, const Pop& fin,
-                 const Pop& fout, const uint8_t* type, const double* Cw, float* u, cudaStream_t s)
+                 const Pop& fout, const uint8_t* type, const double* Cw, float* u, const uint64_t* pres_in,
+                 uint64_t* pres_out, cudaStream_t s)
 {
     if (ntiles <= 0) return;
     if (store == kStoreF32)
-        launch_step_t<kStoreF32>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, s);
+        launch_step_t<kStoreF32>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, pres_in, pres_out, s);
     else if (store == kStoreF16)
-        launch_step_t<kStoreF16>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, s);
+        launch_step_t<kStoreF16>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, pres_in, pres_out, s);
     else
-        launch_step_t<kStoreBF16>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, s);
+        launch_step_t<kStoreBF16>(P, tiles, ntiles, kind, fin, fout, type, Cw, u, pres_in, pres_out, s);
 }
 
 // Pure tiles of the 16-bit storage through the tensor memory accelerator, persistent, with the
