@@ -4,7 +4,9 @@ J(angles, u_in) = x-centroid of fluid 0 after `nsteps` timesteps from the rest s
 `angles` are the wall-angle triples (theta_01, theta_20, theta_12) of every solid boundary node
 (degrees, [n_wall, 3], the order of Lbm3.wall_nodes()), `u_in` the Zou-He inflow velocity.  The
 forward call runs the checkpointed forward pass and the adjoint kernels on the GPU and keeps the
-gradient for backward.
+gradient for backward.  The simulation keeps the adjoint's device memory and its recorded sweep
+between calls of the same size (an optimisation loop's steady state); Lbm3.adjoint_release()
+frees them.
 """
 from __future__ import annotations
 

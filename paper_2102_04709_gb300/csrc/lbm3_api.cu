@@ -1003,6 +1003,7 @@ int lbm3_set_inflow(lbm3* h, double u_in)
     if (!h) return fail(h, LBM3_ERR_INVALID, "NULL handle");
     if (h->P.bc_x != kZouHe) return fail(h, LBM3_ERR_INVALID, "no Zou-He inlet");
     if (!(std::fabs(u_in) < 0.3)) return fail(h, LBM3_ERR_INVALID, "|u_in| must be < 0.3");
+    if ((float)u_in == h->P.u_in) return LBM3_OK;  // the captured graphs stay valid
     h->P.u_in = (float)u_in;
     drop_graphs(h);  // the graphs hold the old Params
     return LBM3_OK;
