@@ -150,7 +150,8 @@ int lbm3_set_state(lbm3* h, const double* f_post, const double* wall_c);
  * host [n_wall][3] in lbm3_wall_nodes order (each in (0, 180)). */
 int lbm3_set_wall_angles(lbm3* h, const double* angles_deg);
 
-/* Replace the Zou-He inlet velocity (|u_in| < 0.3; LBM3_BC_ZOUHE only). */
+/* Replace the Zou-He inlet velocity (|u_in| < 0.3; LBM3_BC_ZOUHE only).  A new value drops the
+ * captured CUDA graphs of lbm3_step and of the adjoint (they hold it); the same value keeps them. */
 int lbm3_set_inflow(lbm3* h, double u_in);
 
 /* Adjoint (reverse-mode) gradient.  Runs nsteps timesteps from the current state, evaluates
