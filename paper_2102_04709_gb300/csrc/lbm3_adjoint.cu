@@ -46,8 +46,6 @@ struct Adj {
     int* wb;       // [4][Nw]
     float* wfr;    // [4][Nw]
     float* wdfr;   // [4][Nw] d fr / d theta_k (deg)
-    float* wcd;    // [4][Nw]
-    float* wth;    // [2][Nw] theta_k
     float* wraw;   // [2][Nw] C_P of fluid k before the normalisation
     int* wsel;     // [2][Nw] side chosen by Eq.(22)
     // adjoint fields
@@ -216,9 +214,7 @@ __global__ void a_wet(const Params P, const Adj A, int nw, const int* __restrict
         A.wb[j] = cr.kind == 2 ? cpos(P, A, cr.bx, cr.by, kk) : 0;
         A.wfr[j] = (float)cr.fr;
         A.wdfr[j] = (float)dfr;
-        A.wcd[j] = (float)cd;
         if (side == 0) {
-            A.wth[k * nw + w] = (float)th;
             A.wraw[k * nw + w] = (float)cp;
             A.wsel[k * nw + w] = sel;
         }
@@ -991,8 +987,6 @@ cudaError_t adjoint_alloc(const Params& P, int nw, AdjointWork** out)
         M((void**)&A.wb, 4 * nwz * 4);
         M((void**)&A.wfr, 4 * nwz * 4);
         M((void**)&A.wdfr, 4 * nwz * 4);
-        M((void**)&A.wcd, 4 * nwz * 4);
-        M((void**)&A.wth, 2 * nwz * 4);
         M((void**)&A.wraw, 2 * nwz * 4);
         M((void**)&A.wsel, 2 * nwz * 4);
         M((void**)&A.l_C, 3 * NP * 4);
@@ -1018,8 +1012,7 @@ void adjoint_free(AdjointWork* W)
     for (void* p : shared)
         if (p) cudaFree(p);
     for (const Adj& A : W->A) {
-        void* own[] = {A.fpost, A.C, A.rho, A.g, A.T, A.F, A.wkind, A.wa, A.wb, A.wfr, A.wdfr, A.wcd,
-                       A.wth, A.wraw, A.wsel, A.l_C, A.l_rho};
+        void* own[] = {A.fpost, A.C, A.rho, A.g, A.T, A.F, A.wkind, A.wa, A.wb, A.wfr, A.wdfr, A.wraw, A.wsel, A.l_C, A.l_rho};
         for (void* p : own)
             if (p) cudaFree(p);
     }
