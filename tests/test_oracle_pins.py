@@ -786,3 +786,42 @@ def test_halfway_walls_in_poiseuille_flow(oracle_mod):
     roots = np.sort(np.roots(c).real)
     assert np.abs(ux - np.polyval(c, yy)).max() < 1e-4 * ux.max()
     assert abs(roots[0] - 0.5) < 0.02 and abs(roots[1] - 15.5) < 0.02, roots
+
+
+def _dilate_periodic_x(mask):
+    """Nodes within one lattice link (D2Q9 neighbourhood) of a True node; periodic in x, the
+    rows beyond y = 0 and y = ny - 1 taken as empty."""
+    out = mask.copy()
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            sh = np.roll(mask, dx, axis=1)
+            if dy == 1:
+                sh = np.vstack([np.zeros_like(sh[:1]), sh[:-1]])
+            elif dy == -1:
+                sh = np.vstack([sh[1:], np.zeros_like(sh[:1])])
+            out |= sh
+    return out
+
+
+def test_absent_fluid_stays_absent_beyond_one_link(oracle_mod):
+    """Eq.1-15 with pull streaming and halfway bounce-back: a fluid whose stored populations are
+    all exactly zero within one link of a fluid node is exactly zero there after the next step
+    (the post-streaming densities come from the node and its neighbours, C_k = 0 makes the
+    recolouring's C_k f and its beta term b_kl ~ rho_k rho_l vanish).  The pure-tile kernels use
+    this, tile by tile, to skip the phase fields of tiles whose neighbourhood holds one fluid.
+    Checked on a Janus droplet on a flat wall (walls, three fluids, contact lines) over 40
+    steps, node by node; the test also requires that the droplet's fluids do spread."""
+    w = W.janus_flat(nx=64, ny=36, R=12.0, triple=(70.0, 60.0, 110.0))
+    o = oracle_mod.Oracle.from_workload(w)
+    o.set_fields(w.rho)
+    fluid = ~w.solid.astype(bool)
+    spread = 0
+    for _ in range(40):
+        held = np.abs(o.get_f()).sum(axis=1) != 0.0   # [3][ny][nx]: fluid k stored at the node
+        o.step(1)
+        after = np.abs(o.get_f()).sum(axis=1) != 0.0
+        for k in range(3):
+            allowed = _dilate_periodic_x(held[k])
+            assert not (after[k] & fluid & ~allowed).any(), f"fluid {k} appeared beyond one link"
+            spread += int((after[k] & ~held[k] & fluid).sum())
+    assert spread > 0
